@@ -1,0 +1,283 @@
+"""FP64 CPU oracle of Big-means (Mussabayev, Mladenovic, Mussabayev, Jarboui,
+"How to Use K-means for Big Data Clustering?", arXiv 2204.07485).
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only ``tests/``,
+``__graft_entry__.smoke()`` and ``bench.py`` (its CPU-baseline leg and its
+reference arm) may import this module.  The CUDA library never calls it and
+it shares no code with the CUDA library.
+
+It is the plain, slow, obviously-correct statement of what the GPU path
+computes, in float64 (inputs are float32 data promoted to float64).  Random
+numbers (chunk indices, K-means++ uniforms) are inputs, drawn by
+``bminputs``.  The one library primitive used as a step is
+``scipy.spatial.distance.cdist(..., 'sqeuclidean')``, i.e. sum_f (x_f - c_f)^2
+evaluated directly in float64.
+
+Readings taken where the paper is silent or ambiguous (each is repeated in the
+design notes):
+  R1  Eq. 1 is printed without min_j; the text says "nearest centre", so
+      f(C, X) = sum_i min_j ||x_i - c_j||^2 over live centroids (Sec. 1).
+  R2  Keep-the-best uses Alg. 1 literally: accept C'' iff f(C'', P) < f_opt
+      (strict, so a tie keeps the incumbent) (Alg. 1, Sec. 3.2).
+  R3  Lloyd stop rule (Sec. 5): stop after an assignment when f == 0, or
+      it > 0 and f_prev - f <= tol * f_prev, or it == max_iter (so at most
+      max_iter update steps); tol = 1e-4, max_iter = 300.
+  R4  f(C'', P) is the objective of the last assignment, computed with the
+      returned centroids C'' themselves, so it is exact for C''.
+  R5  A centroid that loses all members becomes degenerate (the paper's
+      "empty" = "uninitialized" state, Sec. 3.3); it is excluded from later
+      assignments of this chunk and reseeded only at the next chunk (Alg. 1).
+  R6  Degenerate centroids are excluded from every minimum (treated as +inf).
+  R7  K-means++ (Sec. 2, Sec. 3.3, Sec. 5): degenerate slots are filled in
+      ascending order on the sample P; if no centroid is live the first one is
+      P[floor(u_first * s)]; each further centre draws `trials` (= 3)
+      candidates by inverse CDF of D^2 over the inclusive prefix sum in index
+      order (smallest i with prefix_i > u * sum D^2; uniform floor(u * s) when
+      sum D^2 = 0) and keeps the candidate with the lowest potential
+      sum_i min(D^2_i, ||p_i - cand||^2) (lowest trial index on ties).
+  R8  The sample is drawn without replacement (indices are an input here).
+  R9  Argmin ties go to the lowest centroid index.
+"""
+import math
+
+import numpy as np
+from scipy.spatial.distance import cdist
+
+
+# ---------------------------------------------------------------- primitives
+
+def sq_distances(P, C):
+    """||p_i - c_j||^2 for all pairs, float64 (s x k).  Sec. 1, Eq. 1."""
+    P = np.asarray(P, dtype=np.float64)
+    C = np.asarray(C, dtype=np.float64)
+    if P.shape[0] == 0 or C.shape[0] == 0:
+        return np.zeros((P.shape[0], C.shape[0]))
+    return cdist(P, C, "sqeuclidean")
+
+
+def nearest(P, C, live):
+    """Nearest live centroid of every row (R6, R9).
+
+    Returns (labels int64, d1 = squared distance to it, d2 = squared distance
+    to the second-nearest live centroid, +inf if only one is live).
+    """
+    live = np.asarray(live, dtype=bool)
+    D = sq_distances(P, C)
+    D[:, ~live] = np.inf
+    labels = np.argmin(D, axis=1)                 # first minimum: lowest index
+    rows = np.arange(D.shape[0])
+    d1 = D[rows, labels]
+    if live.sum() >= 2:
+        D2 = D.copy()
+        D2[rows, labels] = np.inf
+        d2 = D2.min(axis=1)
+    else:
+        d2 = np.full(D.shape[0], np.inf)
+    return labels, d1, d2
+
+
+def objective(X, C, live):
+    """f(C, X) = sum_i min_{live j} ||x_i - c_j||^2 (Eq. 1 with R1, R6)."""
+    _, d1, _ = nearest(X, C, live)
+    return float(d1.sum())
+
+
+# ------------------------------------------------------------ K-means++ (a2)
+
+class KppPick:
+    """What one reseeded slot decided, for the tests and the margin report."""
+
+    def __init__(self, slot, cands, potentials, chosen, boundary_margin):
+        self.slot = slot
+        self.cands = cands
+        self.potentials = potentials
+        self.chosen = chosen
+        self.boundary_margin = boundary_margin
+
+
+def kmeanspp_reseed(P, C, live, u_first, u, trials=3, picks=None):
+    """Reinitialise every degenerate centroid of (C, live) on sample P (R7).
+
+    P: s x n, C: k x n (rows of degenerate slots are ignored), live: k bools,
+    u_first: float, u: k x trials uniforms.  Returns new (C, live) copies.
+    ``picks`` (optional list) receives one KppPick per reseeded slot.
+    """
+    P = np.asarray(P, dtype=np.float64)
+    C = np.array(C, dtype=np.float64, copy=True)
+    live = np.array(live, dtype=bool, copy=True)
+    s = P.shape[0]
+    k = C.shape[0]
+    if live.all():
+        return C, live
+    if not live.any():
+        j0 = 0
+        C[j0] = P[int(math.floor(u_first * s))]
+        live[j0] = True
+        D2 = sq_distances(P, C[j0:j0 + 1])[:, 0]
+        if picks is not None:
+            picks.append(KppPick(j0, [int(math.floor(u_first * s))], [], 0, math.inf))
+    else:
+        D2 = sq_distances(P, C[live]).min(axis=1)
+    for j in range(k):
+        if live[j]:
+            continue
+        total = float(D2.sum())
+        prefix = np.cumsum(D2)
+        cands, pots, margins = [], [], []
+        for l in range(trials):
+            if total == 0.0:
+                cand = int(math.floor(u[j, l] * s))
+                margins.append(math.inf)
+            else:
+                target = u[j, l] * total
+                cand = int(np.searchsorted(prefix, target, side="right"))
+                if cand >= s:                       # rounding: last positive D^2
+                    cand = int(np.flatnonzero(D2 > 0)[-1])
+                lo = prefix[cand - 1] if cand > 0 else 0.0
+                margins.append(min(target - lo, prefix[cand] - target) / total)
+            dc = sq_distances(P, P[cand:cand + 1])[:, 0]
+            cands.append(cand)
+            pots.append(float(np.minimum(D2, dc).sum()))
+        best = int(np.argmin(pots))                 # lowest trial on ties
+        C[j] = P[cands[best]]
+        live[j] = True
+        D2 = np.minimum(D2, sq_distances(P, C[j:j + 1])[:, 0])
+        if picks is not None:
+            picks.append(KppPick(j, cands, pots, best, min(margins)))
+    return C, live
+
+
+# ------------------------------------------------- Lloyd (a3, a5, a6)
+
+class LloydResult:
+    def __init__(self, C, live, f, iters, f_trace, min_gap, stop_margin, n_d):
+        self.C = C                  # k x n centroids C''
+        self.n_d = n_d              # distance evaluations: s x live per step
+        self.live = live            # k bools
+        self.f = f                  # f(C'', P), R4
+        self.iters = iters          # update steps performed
+        self.f_trace = f_trace      # objective of every assignment step
+        self.min_gap = min_gap      # min over steps/rows of (d2 - d1) / d2
+        self.stop_margin = stop_margin  # min relative distance to the stop threshold
+
+
+def lloyd(P, C, live, tol=1e-4, max_iter=300):
+    """K-means local search on sample P from centroids C (Sec. 2; R3, R4, R5)."""
+    P = np.asarray(P, dtype=np.float64)
+    C = np.array(C, dtype=np.float64, copy=True)
+    live = np.array(live, dtype=bool, copy=True)
+    k = C.shape[0]
+    it = 0
+    f_prev = math.inf
+    f_trace = []
+    min_gap = math.inf
+    stop_margin = math.inf
+    n_d = 0
+    while True:
+        n_d += P.shape[0] * int(live.sum())
+        labels, d1, d2 = nearest(P, C, live)
+        f = float(d1.sum())
+        f_trace.append(f)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            gaps = np.where(np.isfinite(d2), (d2 - d1) / d2, np.inf)
+        if gaps.size:
+            min_gap = min(min_gap, float(np.nanmin(gaps)))
+        if it > 0 and f_prev > 0:
+            stop_margin = min(stop_margin, abs((f_prev - f) - tol * f_prev) / f_prev)
+        if f == 0.0 or (it > 0 and f_prev - f <= tol * f_prev) or it == max_iter:
+            break
+        for j in range(k):
+            if not live[j]:
+                continue
+            members = P[labels == j]
+            if members.shape[0] == 0:
+                live[j] = False
+            else:
+                C[j] = members.mean(axis=0)
+        f_prev = f
+        it += 1
+    counts = np.bincount(labels, minlength=k)
+    live &= counts > 0
+    return LloydResult(C, live, f, it, f_trace, min_gap, stop_margin, n_d)
+
+
+# ------------------------------------------------------- Big-means (Alg. 1)
+
+class ChunkRecord:
+    def __init__(self, t, f_chunk, accepted, iters, picks, lloyd_res, keep_margin,
+                 n_d):
+        self.t = t
+        self.n_d = n_d
+        self.f_chunk = f_chunk
+        self.accepted = accepted
+        self.iters = iters
+        self.picks = picks
+        self.lloyd = lloyd_res
+        self.keep_margin = keep_margin
+
+
+class BigMeansState:
+    """Incumbent of Alg. 1: centroids C, live mask, f_opt."""
+
+    def __init__(self, k, n):
+        self.C = np.zeros((k, n))
+        self.live = np.zeros(k, dtype=bool)
+        self.f_opt = math.inf
+
+    def copy(self):
+        o = BigMeansState(*self.C.shape)
+        o.C = self.C.copy()
+        o.live = self.live.copy()
+        o.f_opt = self.f_opt
+        return o
+
+
+def big_means_chunk(X, state, idx, u_first, u, tol=1e-4, max_iter=300,
+                    trials=3, t=0):
+    """One pass of Alg. 1's loop body on the sample X[idx]; updates ``state``."""
+    P = np.asarray(X, dtype=np.float32)[np.asarray(idx)].astype(np.float64)
+    picks = []
+    s = P.shape[0]
+    live0 = int(state.live.sum())
+    reseeded = state.live.shape[0] - live0
+    # n_d of the reseed (Sec. 5 counter): the D^2 of the first centre or of
+    # the live set, then `trials` candidate distances per further slot.
+    if reseeded == 0:
+        nd_kpp = 0
+    elif live0 == 0:
+        nd_kpp = s + (reseeded - 1) * s * trials
+    else:
+        nd_kpp = s * live0 + reseeded * s * trials
+    C1, live1 = kmeanspp_reseed(P, state.C, state.live, u_first, u, trials, picks)
+    res = lloyd(P, C1, live1, tol, max_iter)
+    accepted = res.f < state.f_opt
+    keep_margin = (abs(res.f - state.f_opt) / state.f_opt
+                   if math.isfinite(state.f_opt) and state.f_opt > 0 else math.inf)
+    if accepted:
+        state.C = res.C
+        state.live = res.live
+        state.f_opt = res.f
+    return ChunkRecord(t, res.f, accepted, res.iters, picks, res, keep_margin,
+                       nd_kpp + res.n_d)
+
+
+def big_means(X, k, draws, tol=1e-4, max_iter=300, trials=3, state=None,
+              t0=0):
+    """Alg. 1 over the given chunk draws [(idx, u_first, u), ...].
+
+    Returns (state, records).  The final assignment is ``final_assignment``.
+    """
+    X = np.asarray(X, dtype=np.float32)
+    if state is None:
+        state = BigMeansState(k, X.shape[1])
+    records = []
+    for q, (idx, u_first, u) in enumerate(draws):
+        records.append(big_means_chunk(X, state, idx, u_first, u, tol,
+                                       max_iter, trials, t=t0 + q))
+    return state, records
+
+
+def final_assignment(X, C, live):
+    """Last step of Alg. 1: A_i = nearest live centroid; returns (A, f(C, X))."""
+    labels, d1, d2 = nearest(X, C, live)
+    return labels, float(d1.sum()), d1, d2
