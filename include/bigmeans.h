@@ -1,0 +1,193 @@
+/*
+ * bigmeans.h -- C ABI of the GB300 Big-means library (libbigmeans.so).
+ *
+ * Big-means (Mussabayev, Mladenovic, Mussabayev, Jarboui, "How to Use
+ * K-means for Big Data Clustering?", arXiv 2204.07485) solves the minimum
+ * sum-of-squares clustering problem (Sec. 1, Eq. 1): given m points X in R^n
+ * and k, find centroids C minimising f(C, X) = sum_i min_j ||x_i - c_j||^2.
+ * Alg. 1 repeatedly draws a uniform sample P of s points (Sec. 3.1, Eq. 2;
+ * Sec. 3.5), reinitialises the degenerate centroids of the incumbent with
+ * K-means++ (Sec. 3.3), runs K-means on P (Sec. 2), keeps the result if its
+ * sample objective beats the incumbent's (Alg. 1, Sec. 3.2), and finally
+ * assigns every point of X to its nearest centroid (Sec. 3.4).
+ *
+ * Conventions for every entry point
+ *   - Matrices are row-major float32: X is m x n, P is s x n, C is k x n.
+ *   - "_dev" pointers are CUDA device pointers, "_host" pointers host memory.
+ *     Device buffers passed in are borrowed: the caller owns them and must
+ *     keep them alive for the duration of the call (X_dev: for the whole
+ *     lifetime of the context that borrows it).
+ *   - A centroid mask holds one byte per centroid: 1 = live, 0 = degenerate
+ *     (empty or uninitialised, Alg. 1 / Sec. 3.3).  The coordinates of a
+ *     degenerate centroid are never read.
+ *   - stream is a cudaStream_t (NULL = legacy default stream).
+ *   - Every call returns a bm_status and never aborts the process.  Invalid
+ *     shapes return BM_EINVAL (k < 1, n < 1, s < 1, s > m, k > s, m or s
+ *     beyond 2^31 - 1); CUDA failures return BM_ECUDA; a device-side wait
+ *     that exceeds its bound returns BM_ETIMEOUT and leaves the context
+ *     usable after bm_reset.
+ *   - Results are a pure function of (X, configuration, seed) on a given
+ *     device: reductions have a fixed shape and order (no float atomics).
+ *   - Random draws follow Philox4x64-10 (Salmon et al., SC'11) with
+ *     key (seed, 0) and counter (i / 4, round, chunk t, purpose), word i % 4.
+ */
+#ifndef BIGMEANS_H
+#define BIGMEANS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum bm_status {
+  BM_OK = 0,
+  BM_EINVAL = 1,        /* invalid argument or shape                         */
+  BM_ENOMEM = 2,        /* device allocation or admission failed              */
+  BM_ECUDA = 3,         /* a CUDA runtime call failed                         */
+  BM_ETIMEOUT = 4,      /* a bounded device-side wait gave up                 */
+  BM_EBUSY = 5,         /* server full / resource in use                      */
+  BM_ECANCELLED = 6,    /* job cancelled before completion                   */
+  BM_EUNSUPPORTED = 7   /* shape outside what this build's kernels cover      */
+} bm_status;
+
+typedef enum bm_precision {
+  BM_FP32 = 0,          /* FP32 distances throughout                          */
+  BM_BF16_RESCORE = 1,  /* BF16 tensor-core distances, FP32 rescore of ties   */
+  BM_FP8_RESCORE = 2    /* FP8 E4M3 tensor-core distances, FP32 rescore       */
+} bm_precision;
+
+/* Parameters of one Big-means job (Alg. 1 inputs X, k, s and the stop rule). */
+typedef struct bm_config {
+  int64_t m;            /* number of points                                    */
+  int32_t n;            /* dimension                                           */
+  int32_t k;            /* number of clusters                                  */
+  int64_t s;            /* sample (chunk) size, 1 <= s <= m, k <= s            */
+  int32_t max_iter;     /* Lloyd update-step cap per chunk (Sec. 5: 300)       */
+  double tol;           /* Lloyd relative-improvement stop (Sec. 5: 1e-4)      */
+  int32_t kpp_trials;   /* K-means++ candidates per new centre (Sec. 5: 3)     */
+  uint64_t seed;        /* Philox key                                          */
+  int32_t precision;    /* bm_precision                                        */
+  double time_budget_s; /* bm_fit_chunk(chunks = 0) runs until this elapses    */
+} bm_config;
+
+/* What one bm_fit_chunk call did. */
+typedef struct bm_fit_report {
+  int64_t chunks;        /* chunks processed by this call                      */
+  int64_t accepted;      /* of which replaced the incumbent (Alg. 1)           */
+  int64_t lloyd_iters;   /* Lloyd update steps summed over those chunks        */
+  int64_t n_d;           /* distance evaluations, cumulative for the context   */
+  int64_t chunk_counter; /* index t of the next chunk                          */
+  double f_opt;          /* incumbent sample objective after the call          */
+  double seconds;        /* host wall time of the call                         */
+} bm_fit_report;
+
+typedef struct bm_ctx bm_ctx;
+
+/* Fills *cfg with the paper's defaults (max_iter 300, tol 1e-4, 3 trials,
+ * FP32, seed 0) and zero sizes. */
+void bm_config_default(bm_config* cfg);
+
+/* Human-readable name of a status code (static string). */
+const char* bm_status_string(int32_t status);
+
+/* Creates a Big-means context for the dataset X_dev (m x n, borrowed) on the
+ * current CUDA device.  Allocates all device state (sample, centroids,
+ * partial sums) once.  The incumbent starts with every centroid degenerate
+ * and f_opt = +inf (Alg. 1).  stream: the stream all work is queued on. */
+bm_status bm_create(const bm_config* cfg, const float* X_dev, void* stream,
+                    bm_ctx** out);
+
+/* Releases the context (synchronises its stream first).  NULL is a no-op. */
+bm_status bm_destroy(bm_ctx* ctx);
+
+/* Resets the incumbent to all-degenerate, f_opt = +inf, chunk counter 0,
+ * n_d = 0, and clears any error left by a failed launch. */
+bm_status bm_reset(bm_ctx* ctx);
+
+/* Runs Alg. 1's loop body for `chunks` consecutive chunks t, t+1, ...:
+ * draw sample t, gather P, K-means++ reseed of degenerate centroids, Lloyd on
+ * P, keep-the-best.  chunks = 0 runs chunks until cfg.time_budget_s of wall
+ * time has elapsed (the paper's CPU-time stop condition, Sec. 5).  Blocks
+ * until the work is done; `out` (may be NULL) receives the report. */
+bm_status bm_fit_chunk(bm_ctx* ctx, int32_t chunks, bm_fit_report* out);
+
+/* Final step of Alg. 1: labels_dev[i] (int32, m entries, caller-owned device
+ * memory; may be NULL to skip labels) = nearest live incumbent centroid of
+ * x_i (lowest index on ties); *sse_out (host, may be NULL) = f(C, X)
+ * accumulated in float64.  Blocks until done. */
+bm_status bm_assign(bm_ctx* ctx, int32_t* labels_dev, double* sse_out);
+
+/* Reads the incumbent: f_opt (its sample objective), C (k x n, host) and the
+ * mask (k bytes, host).  Any output may be NULL. */
+bm_status bm_objective(bm_ctx* ctx, double* f_opt_out, float* C_out_host,
+                       uint8_t* mask_out_host);
+
+/* Checkpoint / resume of the whole Alg. 1 state: incumbent C (k x n host),
+ * mask (k host), f_opt and the next chunk index.  Restoring a saved state
+ * and continuing reproduces an uninterrupted run bit for bit. */
+bm_status bm_get_state(bm_ctx* ctx, float* C_host, uint8_t* mask_host,
+                       double* f_opt, int64_t* chunk_counter);
+bm_status bm_set_state(bm_ctx* ctx, const float* C_host,
+                       const uint8_t* mask_host, double f_opt,
+                       int64_t chunk_counter);
+
+/* One-call job on HOST memory: copies X_host (m x n) to the device, runs
+ * `chunks` chunks and the final assignment, and copies back C (k x n),
+ * mask (k), labels (m) and f(C, X).  Outputs may be NULL.  Uses and frees
+ * its own device memory and stream. */
+bm_status bm_fit_host(const bm_config* cfg, const float* X_host,
+                      int32_t chunks, float* C_out_host,
+                      uint8_t* mask_out_host, int32_t* labels_out_host,
+                      double* sse_out, bm_fit_report* report);
+
+/* ---------------------------------------------------------------------
+ * Step-level entry points: each runs one step of the hot path on caller
+ * buffers, on `stream`, and blocks until done.  Each call allocates its
+ * scratch (partial sums, barrier counters) on the current device and frees
+ * it before returning; calls from several host threads serialise on a lock.
+ * ------------------------------------------------------------------- */
+
+/* Sample draw of chunk t (Sec. 3.1, Eq. 2; Sec. 3.5): writes the s sorted,
+ * distinct row indices of the uniform sample to idx_dev (int32, s entries).
+ * Round r draws (count - |S|) Philox values (purpose 0) mapped to [0, m) by
+ * the high word of a 64x64 product and adds them to S; for 2s > m the m - s
+ * rows to leave out are drawn instead and the sample is their complement. */
+bm_status bm_draw_chunk(int64_t m, int64_t s, uint64_t seed, int64_t t,
+                        int32_t* idx_dev, void* stream);
+
+/* P = X[idx] (Alg. 1: "P <- uniform random sample"): P_dev is s x n. */
+bm_status bm_gather(const float* X_dev, int64_t m, int32_t n,
+                    const int32_t* idx_dev, int64_t s, float* P_dev,
+                    void* stream);
+
+/* K-means++ reseed (Sec. 2; Sec. 3.3; three candidates, Sec. 5) of every
+ * degenerate centroid of (C_dev, mask_dev) (k x n and k bytes, updated in
+ * place) on the sample P_dev (s x n), in ascending slot order, with the
+ * uniforms of chunk t (purposes 1 and 2 of the Philox stream). */
+bm_status bm_kpp_reseed(const float* P_dev, int64_t s, int32_t n, int32_t k,
+                        float* C_dev, uint8_t* mask_dev, uint64_t seed,
+                        int64_t t, int32_t trials, void* stream);
+
+/* K-means (Lloyd) on P_dev from (C_dev, mask_dev) (Sec. 2; stop rule Sec. 5):
+ * updates C and the mask in place (clusters that empty become degenerate),
+ * *f_out (host) = f(C'', P) in float64, *iters_out (host) = update steps. */
+bm_status bm_lloyd(const float* P_dev, int64_t s, int32_t n, int32_t k,
+                   float* C_dev, uint8_t* mask_dev, int32_t max_iter,
+                   double tol, double* f_out, int32_t* iters_out,
+                   void* stream);
+
+/* Nearest-centroid assignment of arbitrary rows (Alg. 1's final step,
+ * Sec. 3.4): labels_dev[i] (int32, may be NULL) = nearest live centroid,
+ * dmin_dev[i] (float32, may be NULL) = its squared distance, *sse_out (host,
+ * may be NULL) = sum of those distances accumulated in float64. */
+bm_status bm_assign_rows(const float* X_dev, int64_t m, int32_t n,
+                         const float* C_dev, const uint8_t* mask_dev,
+                         int32_t k, int32_t* labels_dev, float* dmin_dev,
+                         double* sse_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BIGMEANS_H */

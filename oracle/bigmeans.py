@@ -179,7 +179,8 @@ def lloyd(P, C, live, tol=1e-4, max_iter=300):
         f = float(d1.sum())
         f_trace.append(f)
         with np.errstate(invalid="ignore", divide="ignore"):
-            gaps = np.where(np.isfinite(d2), (d2 - d1) / d2, np.inf)
+            gaps = np.where(np.isfinite(d2),
+                            np.where(d2 > 0, (d2 - d1) / d2, 0.0), np.inf)
         if gaps.size:
             min_gap = min(min_gap, float(np.nanmin(gaps)))
         if it > 0 and f_prev > 0:

@@ -1,0 +1,212 @@
+"""Python binding of libbigmeans.so (GB300 Big-means, arXiv 2204.07485).
+
+Argument marshalling only: every step of the clustering runs in the CUDA
+library through its C ABI (``include/bigmeans.h``); the functions here carry
+the same names.  Pointer arguments accept a plain integer address or any
+object with ``data_ptr()`` (e.g. a torch tensor); streams accept an integer
+handle or an object with ``cuda_stream``.  There is no CPU fallback: if the
+shared library has not been built, importing this package raises.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbigmeans.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        "libbigmeans.so is not built (expected at %s); run "
+        "`python -c 'import __graft_entry__ as g; g.build()'` first" % LIB_PATH)
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+BM_OK, BM_EINVAL, BM_ENOMEM, BM_ECUDA, BM_ETIMEOUT, BM_EBUSY, BM_ECANCELLED, \
+    BM_EUNSUPPORTED = range(8)
+BM_FP32, BM_BF16_RESCORE, BM_FP8_RESCORE = range(3)
+
+
+class bm_config(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("s", ctypes.c_int64), ("max_iter", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("kpp_trials", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
+                ("time_budget_s", ctypes.c_double)]
+
+
+class bm_fit_report(ctypes.Structure):
+    _fields_ = [("chunks", ctypes.c_int64), ("accepted", ctypes.c_int64),
+                ("lloyd_iters", ctypes.c_int64), ("n_d", ctypes.c_int64),
+                ("chunk_counter", ctypes.c_int64), ("f_opt", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class BigMeansError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s failed: %s (%d)" % (where, bm_status_string(status), status))
+
+
+_vp, _i32, _i64, _u64, _dbl = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                               ctypes.c_uint64, ctypes.c_double)
+_P = ctypes.POINTER
+
+_SIGS = {
+    "bm_config_default": (None, [_P(bm_config)]),
+    "bm_status_string": (ctypes.c_char_p, [_i32]),
+    "bm_create": (_i32, [_P(bm_config), _vp, _vp, _P(_vp)]),
+    "bm_destroy": (_i32, [_vp]),
+    "bm_reset": (_i32, [_vp]),
+    "bm_fit_chunk": (_i32, [_vp, _i32, _P(bm_fit_report)]),
+    "bm_assign": (_i32, [_vp, _vp, _P(_dbl)]),
+    "bm_objective": (_i32, [_vp, _P(_dbl), _vp, _vp]),
+    "bm_get_state": (_i32, [_vp, _vp, _vp, _P(_dbl), _P(_i64)]),
+    "bm_set_state": (_i32, [_vp, _vp, _vp, _dbl, _i64]),
+    "bm_fit_host": (_i32, [_P(bm_config), _vp, _i32, _vp, _vp, _vp, _P(_dbl),
+                           _P(bm_fit_report)]),
+    "bm_draw_chunk": (_i32, [_i64, _i64, _u64, _i64, _vp, _vp]),
+    "bm_gather": (_i32, [_vp, _i64, _i32, _vp, _i64, _vp, _vp]),
+    "bm_kpp_reseed": (_i32, [_vp, _i64, _i32, _i32, _vp, _vp, _u64, _i64, _i32, _vp]),
+    "bm_lloyd": (_i32, [_vp, _i64, _i32, _i32, _vp, _vp, _i32, _dbl, _P(_dbl),
+                        _P(_i32), _vp]),
+    "bm_assign_rows": (_i32, [_vp, _i64, _i32, _vp, _vp, _i32, _vp, _vp, _P(_dbl), _vp]),
+}
+
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):            # numpy array (host memory)
+        return x.ctypes.data
+    raise TypeError("expected an address or an object with data_ptr(): %r" % type(x))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return getattr(s, "cuda_stream")
+
+
+def _check(status, where):
+    if status != BM_OK:
+        raise BigMeansError(status, where)
+
+
+def bm_status_string(status):
+    return _lib.bm_status_string(int(status)).decode()
+
+
+def bm_config_default(**overrides):
+    cfg = bm_config()
+    _lib.bm_config_default(ctypes.byref(cfg))
+    for key, val in overrides.items():
+        setattr(cfg, key, val)
+    return cfg
+
+
+def bm_create(cfg, X_dev, stream=None):
+    ctx = _vp()
+    _check(_lib.bm_create(ctypes.byref(cfg), _ptr(X_dev), _stream(stream),
+                          ctypes.byref(ctx)), "bm_create")
+    return ctx.value
+
+
+def bm_destroy(ctx):
+    _check(_lib.bm_destroy(ctx), "bm_destroy")
+
+
+def bm_reset(ctx):
+    _check(_lib.bm_reset(ctx), "bm_reset")
+
+
+def bm_fit_chunk(ctx, chunks):
+    rep = bm_fit_report()
+    _check(_lib.bm_fit_chunk(ctx, int(chunks), ctypes.byref(rep)), "bm_fit_chunk")
+    return rep.as_dict()
+
+
+def bm_assign(ctx, labels_dev=None):
+    sse = _dbl()
+    _check(_lib.bm_assign(ctx, _ptr(labels_dev), ctypes.byref(sse)), "bm_assign")
+    return sse.value
+
+
+def bm_objective(ctx, C_out_host=None, mask_out_host=None):
+    f = _dbl()
+    _check(_lib.bm_objective(ctx, ctypes.byref(f), _ptr(C_out_host),
+                             _ptr(mask_out_host)), "bm_objective")
+    return f.value
+
+
+def bm_get_state(ctx, C_host, mask_host):
+    f = _dbl()
+    t = _i64()
+    _check(_lib.bm_get_state(ctx, _ptr(C_host), _ptr(mask_host), ctypes.byref(f),
+                             ctypes.byref(t)), "bm_get_state")
+    return f.value, t.value
+
+
+def bm_set_state(ctx, C_host, mask_host, f_opt, chunk_counter):
+    _check(_lib.bm_set_state(ctx, _ptr(C_host), _ptr(mask_host), float(f_opt),
+                             int(chunk_counter)), "bm_set_state")
+
+
+def bm_fit_host(cfg, X_host, chunks, C_out_host=None, mask_out_host=None,
+                labels_out_host=None):
+    sse = _dbl()
+    rep = bm_fit_report()
+    _check(_lib.bm_fit_host(ctypes.byref(cfg), _ptr(X_host), int(chunks),
+                            _ptr(C_out_host), _ptr(mask_out_host),
+                            _ptr(labels_out_host), ctypes.byref(sse),
+                            ctypes.byref(rep)), "bm_fit_host")
+    return sse.value, rep.as_dict()
+
+
+def bm_draw_chunk(m, s, seed, t, idx_dev, stream=None):
+    _check(_lib.bm_draw_chunk(int(m), int(s), int(seed), int(t), _ptr(idx_dev),
+                              _stream(stream)), "bm_draw_chunk")
+
+
+def bm_gather(X_dev, m, n, idx_dev, s, P_dev, stream=None):
+    _check(_lib.bm_gather(_ptr(X_dev), int(m), int(n), _ptr(idx_dev), int(s),
+                          _ptr(P_dev), _stream(stream)), "bm_gather")
+
+
+def bm_kpp_reseed(P_dev, s, n, k, C_dev, mask_dev, seed, t, trials=3, stream=None):
+    _check(_lib.bm_kpp_reseed(_ptr(P_dev), int(s), int(n), int(k), _ptr(C_dev),
+                              _ptr(mask_dev), int(seed), int(t), int(trials),
+                              _stream(stream)), "bm_kpp_reseed")
+
+
+def bm_lloyd(P_dev, s, n, k, C_dev, mask_dev, max_iter=300, tol=1e-4, stream=None):
+    f = _dbl()
+    it = _i32()
+    _check(_lib.bm_lloyd(_ptr(P_dev), int(s), int(n), int(k), _ptr(C_dev),
+                         _ptr(mask_dev), int(max_iter), float(tol), ctypes.byref(f),
+                         ctypes.byref(it), _stream(stream)), "bm_lloyd")
+    return f.value, it.value
+
+
+def bm_assign_rows(X_dev, m, n, C_dev, mask_dev, k, labels_dev=None, dmin_dev=None,
+                   stream=None):
+    sse = _dbl()
+    _check(_lib.bm_assign_rows(_ptr(X_dev), int(m), int(n), _ptr(C_dev),
+                               _ptr(mask_dev), int(k), _ptr(labels_dev),
+                               _ptr(dmin_dev), ctypes.byref(sse), _stream(stream)),
+           "bm_assign_rows")
+    return sse.value

@@ -1,0 +1,617 @@
+// C ABI of the Big-means library: contexts, the chunk driver and the
+// step-level entry points.  All compute runs in the kernels of
+// bm_kernels.cu; this file sizes buffers, picks a launch shape, queues the
+// launches on the caller's stream and reports status.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <mutex>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/bigmeans.h"
+#include "bm_internal.h"
+
+namespace bm {
+
+// ------------------------------------------------------------------ plan
+// Kernel family and launch shape for one (n, k, s) on the current device.
+struct Plan {
+  bool generic = false;
+  int np = 0;        // register row width of the np path
+  int npad = 0;      // row stride of P and C (floats)
+  int kpad = 0;      // k rounded up to 32 (generic path)
+  int grid = 0;      // CTAs of the chunk kernel
+  int R = 0;         // sample rows per CTA
+  size_t smem = 0;   // dynamic shared memory of the chunk kernel
+  int agrid = 0;     // CTAs of the assign kernel
+  size_t asmem = 0;
+};
+
+static constexpr size_t kSmemLimit = 227 * 1024;
+
+static bm_status make_plan(int n, int k, long long s, Plan* out) {
+  Plan p;
+  if (k > kMaxK) return BM_EUNSUPPORTED;
+  if (n <= kNpMax) {
+    p.generic = false;
+    p.np = n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32;
+    p.npad = p.np;
+    p.kpad = 0;
+  } else {
+    p.generic = true;
+    p.np = 0;
+    p.npad = align_up(n, 4);
+    p.kpad = align_up(k, 32);
+  }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return BM_ECUDA;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // Grid: about 128 sample rows per CTA, at most what stays co-resident.
+  int grid = (int)std::min<long long>((s + 127) / 128, (long long)sms * 8);
+  grid = std::max(grid, 1);
+  for (int iter = 0; iter < 8; ++iter) {
+    const int R = (int)((s + grid - 1) / grid);
+    const ChunkSmem L = chunk_smem(p.npad, k, p.kpad, R, p.generic);
+    if ((size_t)L.total > kSmemLimit) {
+      if (grid >= sms * 8) return BM_EUNSUPPORTED;
+      grid = std::min(grid * 2, sms * 8);
+      continue;
+    }
+    const int maxg = chunk_max_grid(p.generic, p.np, L.total);
+    if (maxg <= 0) return BM_EUNSUPPORTED;
+    if (grid > maxg) { grid = maxg; continue; }
+    p.grid = grid;
+    p.R = R;
+    p.smem = L.total;
+    break;
+  }
+  if (p.grid == 0) return BM_EUNSUPPORTED;
+  p.asmem = assign_smem(p.npad, k, p.kpad, p.generic);
+  if (p.asmem > kSmemLimit) return BM_EUNSUPPORTED;
+  p.agrid = assign_max_grid(p.generic, p.np, p.asmem);
+  if (p.agrid <= 0) return BM_EUNSUPPORTED;
+  *out = p;
+  return BM_OK;
+}
+
+// ------------------------------------------------------------ workspace
+struct Workspace {
+  int32_t* idx = nullptr;
+  uint32_t* bitmap = nullptr;
+  float* P = nullptr;
+  float* C = nullptr;
+  uint8_t* mask = nullptr;
+  float* Cinc = nullptr;
+  uint8_t* mask_inc = nullptr;
+  double* f_opt = nullptr;
+  float* part_sum = nullptr;
+  int32_t* part_cnt = nullptr;
+  double* part_f = nullptr;
+  int32_t* blk_cnt = nullptr;
+  Ctl* ctl = nullptr;
+  Stats* stats = nullptr;
+  double* apart = nullptr;   // assign per-CTA partials
+  double* asse = nullptr;    // assign result
+  std::vector<void*> owned;
+
+  template <typename T>
+  cudaError_t alloc(T** p, size_t count) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, std::max<size_t>(count * sizeof(T), 16));
+    if (e != cudaSuccess) return e;
+    owned.push_back(v);
+    *p = static_cast<T*>(v);
+    return cudaSuccess;
+  }
+  void release() {
+    for (void* v : owned) cudaFree(v);
+    owned.clear();
+  }
+};
+
+static bm_status ws_create(Workspace* w, long long m, int k, long long s,
+                           const Plan& p, cudaStream_t st) {
+  const size_t words = (size_t)((m + 31) / 32);
+  const int G = p.grid;
+  cudaError_t e = cudaSuccess;
+#define BM_TRY(x) do { e = (x); if (e != cudaSuccess) { w->release(); return BM_ENOMEM; } } while (0)
+  BM_TRY(w->alloc(&w->idx, (size_t)s));
+  BM_TRY(w->alloc(&w->bitmap, words));
+  BM_TRY(w->alloc(&w->P, (size_t)s * p.npad));
+  BM_TRY(w->alloc(&w->C, (size_t)k * p.npad));
+  BM_TRY(w->alloc(&w->mask, (size_t)k));
+  BM_TRY(w->alloc(&w->Cinc, (size_t)k * p.npad));
+  BM_TRY(w->alloc(&w->mask_inc, (size_t)k));
+  BM_TRY(w->alloc(&w->f_opt, 1));
+  BM_TRY(w->alloc(&w->part_sum, (size_t)k * p.npad * G));
+  BM_TRY(w->alloc(&w->part_cnt, (size_t)k * G));
+  BM_TRY(w->alloc(&w->part_f, (size_t)(kMaxTrials + 2) * G));
+  BM_TRY(w->alloc(&w->blk_cnt, (size_t)G));
+  BM_TRY(w->alloc(&w->ctl, 1));
+  BM_TRY(w->alloc(&w->stats, 1));
+  BM_TRY(w->alloc(&w->apart, (size_t)p.agrid));
+  BM_TRY(w->alloc(&w->asse, 1));
+#undef BM_TRY
+  cudaMemsetAsync(w->bitmap, 0, words * 4, st);
+  cudaMemsetAsync(w->C, 0, (size_t)k * p.npad * 4, st);
+  cudaMemsetAsync(w->Cinc, 0, (size_t)k * p.npad * 4, st);
+  cudaMemsetAsync(w->mask, 0, k, st);
+  cudaMemsetAsync(w->mask_inc, 0, k, st);
+  cudaMemsetAsync(w->ctl, 0, sizeof(Ctl), st);
+  cudaMemsetAsync(w->stats, 0, sizeof(Stats), st);
+  const double inf = std::numeric_limits<double>::infinity();
+  cudaMemcpyAsync(w->f_opt, &inf, sizeof(double), cudaMemcpyHostToDevice, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) { w->release(); return BM_ECUDA; }
+  return BM_OK;
+}
+
+static ChunkArgs chunk_args(const Workspace& w, const Plan& p, const float* X,
+                            long long m, int n, int k, long long s) {
+  ChunkArgs a{};
+  a.X = X; a.m = m; a.n = n; a.npad = p.npad; a.k = k; a.s = (int)s;
+  a.rows_per_cta = p.R; a.kpad = p.kpad;
+  a.max_iter = 300; a.tol = 1e-4; a.trials = 3;
+  a.idx = w.idx; a.bitmap = w.bitmap; a.P = w.P; a.C = w.C; a.mask = w.mask;
+  a.Cinc = w.Cinc; a.mask_inc = w.mask_inc; a.f_opt = w.f_opt;
+  a.part_sum = w.part_sum; a.part_cnt = w.part_cnt; a.part_f = w.part_f;
+  a.blk_cnt = w.blk_cnt; a.ctl = w.ctl; a.stats = w.stats;
+  return a;
+}
+
+static bool shape_ok(long long m, int n, int k, long long s) {
+  const long long lim = 2147483647LL;
+  return m >= 1 && n >= 1 && k >= 1 && s >= 1 && s <= m && k <= s && m <= lim &&
+         s <= lim;
+}
+
+// Reads the status word; on error clears the control block so that the
+// workspace can be used again.
+static bm_status check_status(Workspace& w, cudaStream_t st, long long m) {
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return BM_ECUDA;
+  int32_t status = 0;
+  e = cudaMemcpy(&status, &w.ctl->status, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return BM_ECUDA;
+  if (status != 0) {
+    // an aborted launch may leave barrier counters and sample bits behind
+    cudaMemset(w.ctl, 0, sizeof(Ctl));
+    cudaMemset(w.bitmap, 0, (size_t)((m + 31) / 32) * 4);
+    cudaDeviceSynchronize();
+    return (bm_status)status;
+  }
+  return BM_OK;
+}
+
+}  // namespace bm
+
+using namespace bm;
+
+// ====================================================================== ctx
+struct bm_ctx {
+  bm_config cfg;
+  const float* X;
+  cudaStream_t stream;
+  Plan plan;
+  Workspace ws;
+  long long t = 0;          // next chunk index
+  long long launches = 0;   // selects the barrier counter
+  long long nd_assign = 0;  // distance evaluations of bm_assign calls
+  std::mutex mu;
+};
+
+extern "C" {
+
+void bm_config_default(bm_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->max_iter = 300;
+  cfg->tol = 1e-4;
+  cfg->kpp_trials = 3;
+  cfg->seed = 0;
+  cfg->precision = BM_FP32;
+  cfg->time_budget_s = 0.0;
+}
+
+const char* bm_status_string(int32_t s) {
+  switch (s) {
+    case BM_OK: return "ok";
+    case BM_EINVAL: return "invalid argument";
+    case BM_ENOMEM: return "out of device memory";
+    case BM_ECUDA: return "CUDA error";
+    case BM_ETIMEOUT: return "device wait timed out";
+    case BM_EBUSY: return "busy";
+    case BM_ECANCELLED: return "cancelled";
+    case BM_EUNSUPPORTED: return "unsupported shape";
+    default: return "unknown status";
+  }
+}
+
+bm_status bm_create(const bm_config* cfg, const float* X_dev, void* stream,
+                    bm_ctx** out) {
+  if (!cfg || !out || !X_dev) return BM_EINVAL;
+  *out = nullptr;
+  if (!shape_ok(cfg->m, cfg->n, cfg->k, cfg->s)) return BM_EINVAL;
+  if (cfg->kpp_trials < 1 || cfg->kpp_trials > kMaxTrials || cfg->max_iter < 0 ||
+      !(cfg->tol >= 0.0))
+    return BM_EINVAL;
+  if (cfg->precision != BM_FP32) return BM_EUNSUPPORTED;
+  bm_ctx* c = new (std::nothrow) bm_ctx();
+  if (!c) return BM_ENOMEM;
+  c->cfg = *cfg;
+  c->X = X_dev;
+  c->stream = static_cast<cudaStream_t>(stream);
+  bm_status st = make_plan(cfg->n, cfg->k, cfg->s, &c->plan);
+  if (st != BM_OK) { delete c; return st; }
+  st = ws_create(&c->ws, cfg->m, cfg->k, cfg->s, c->plan, c->stream);
+  if (st != BM_OK) { delete c; return st; }
+  *out = c;
+  return BM_OK;
+}
+
+bm_status bm_destroy(bm_ctx* c) {
+  if (!c) return BM_OK;
+  cudaStreamSynchronize(c->stream);
+  c->ws.release();
+  delete c;
+  return BM_OK;
+}
+
+bm_status bm_reset(bm_ctx* c) {
+  if (!c) return BM_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  const int k = c->cfg.k;
+  cudaStream_t st = c->stream;
+  cudaMemsetAsync(c->ws.Cinc, 0, (size_t)k * c->plan.npad * 4, st);
+  cudaMemsetAsync(c->ws.mask_inc, 0, k, st);
+  cudaMemsetAsync(c->ws.ctl, 0, sizeof(Ctl), st);
+  cudaMemsetAsync(c->ws.stats, 0, sizeof(Stats), st);
+  const size_t words = (size_t)((c->cfg.m + 31) / 32);
+  cudaMemsetAsync(c->ws.bitmap, 0, words * 4, st);
+  static const double inf = std::numeric_limits<double>::infinity();
+  cudaMemcpyAsync(c->ws.f_opt, &inf, sizeof(double), cudaMemcpyHostToDevice, st);
+  c->t = 0;
+  c->launches = 0;
+  c->nd_assign = 0;
+  return cudaStreamSynchronize(st) == cudaSuccess ? BM_OK : BM_ECUDA;
+}
+
+bm_status bm_fit_chunk(bm_ctx* c, int32_t chunks, bm_fit_report* out) {
+  if (!c || chunks < 0) return BM_EINVAL;
+  if (chunks == 0 && !(c->cfg.time_budget_s > 0.0)) return BM_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  const auto t0 = std::chrono::steady_clock::now();
+  Stats before{};
+  if (cudaMemcpyAsync(&before, c->ws.stats, sizeof(Stats), cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return BM_ECUDA;
+  ChunkArgs a = chunk_args(c->ws, c->plan, c->X, c->cfg.m, c->cfg.n, c->cfg.k, c->cfg.s);
+  a.seed = c->cfg.seed;
+  a.max_iter = c->cfg.max_iter;
+  a.tol = c->cfg.tol;
+  a.trials = c->cfg.kpp_trials;
+  a.phases = kPhaseDraw | kPhaseGather | kPhaseKpp | kPhaseLloyd | kPhaseKeep;
+  long long done = 0;
+  bm_status st = BM_OK;
+  const bool timed = chunks == 0;
+  while (true) {
+    if (!timed && done >= chunks) break;
+    a.t = c->t;
+    a.bar_sel = (int)(c->launches & 1);
+    cudaError_t e = launch_chunk(a, c->plan.grid, c->plan.generic, c->plan.np,
+                                 c->plan.smem, c->stream);
+    if (e != cudaSuccess) { st = BM_ECUDA; break; }
+    ++c->launches;
+    ++c->t;
+    ++done;
+    if (timed) {
+      // the paper's time budget: check between chunks
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) { st = BM_ECUDA; break; }
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el >= c->cfg.time_budget_s) break;
+    }
+  }
+  const bm_status st2 = check_status(c->ws, c->stream, c->cfg.m);
+  if (st == BM_OK) st = st2;
+  if (st != BM_OK) return st;
+  if (out) {
+    Stats after{};
+    double f_opt = 0.0;
+    cudaMemcpy(&after, c->ws.stats, sizeof(Stats), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&f_opt, c->ws.f_opt, sizeof(double), cudaMemcpyDeviceToHost);
+    out->chunks = after.chunks - before.chunks;
+    out->accepted = after.accepted - before.accepted;
+    out->lloyd_iters = after.lloyd_iters - before.lloyd_iters;
+    out->n_d = after.n_d + c->nd_assign;
+    out->chunk_counter = c->t;
+    out->f_opt = f_opt;
+    out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return BM_OK;
+}
+
+static bm_status assign_impl(const float* X, long long m, int n, int k,
+                             const Plan& p, const float* C, int cstride,
+                             const uint8_t* mask, int32_t* labels, float* dmin,
+                             Workspace& w, cudaStream_t st, double* sse_out) {
+  AssignArgs a{};
+  a.X = X; a.m = m; a.n = n; a.npad = p.npad; a.k = k; a.kpad = p.kpad;
+  a.C = C; a.cstride = cstride; a.mask = mask; a.labels = labels; a.dmin = dmin;
+  a.part = w.apart; a.sse = w.asse; a.ticket = &w.ctl->assign_ticket;
+  const long long rows_per = p.generic ? 64 : 256;  // rows per CTA pass
+  const int grid = (int)std::max<long long>(1, std::min<long long>(p.agrid, (m + rows_per - 1) / rows_per));
+  if (launch_assign(a, grid, p.generic, p.np, p.asmem, st) != cudaSuccess) return BM_ECUDA;
+  double sse = 0.0;
+  if (cudaMemcpyAsync(&sse, w.asse, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return BM_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return BM_ECUDA;
+  if (sse_out) *sse_out = sse;
+  return BM_OK;
+}
+
+static int count_live_host(const uint8_t* mask_dev, int k, cudaStream_t st) {
+  std::vector<uint8_t> h(k);
+  if (cudaMemcpyAsync(h.data(), mask_dev, k, cudaMemcpyDeviceToHost, st) != cudaSuccess) return -1;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+  int n = 0;
+  for (uint8_t v : h) n += v != 0;
+  return n;
+}
+
+bm_status bm_assign(bm_ctx* c, int32_t* labels_dev, double* sse_out) {
+  if (!c) return BM_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  const int live = count_live_host(c->ws.mask_inc, c->cfg.k, c->stream);
+  if (live < 0) return BM_ECUDA;
+  if (live == 0) return BM_EINVAL;   // no incumbent yet
+  bm_status st = assign_impl(c->X, c->cfg.m, c->cfg.n, c->cfg.k, c->plan, c->ws.Cinc,
+                             c->plan.npad, c->ws.mask_inc, labels_dev, nullptr, c->ws,
+                             c->stream, sse_out);
+  if (st == BM_OK) c->nd_assign += c->cfg.m * (long long)live;
+  return st;
+}
+
+bm_status bm_get_state(bm_ctx* c, float* C_host, uint8_t* mask_host,
+                       double* f_opt, int64_t* chunk_counter) {
+  if (!c) return BM_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  const int k = c->cfg.k, n = c->cfg.n, npad = c->plan.npad;
+  cudaStream_t st = c->stream;
+  if (C_host &&
+      cudaMemcpy2DAsync(C_host, n * 4, c->ws.Cinc, npad * 4, n * 4, k,
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return BM_ECUDA;
+  if (mask_host && cudaMemcpyAsync(mask_host, c->ws.mask_inc, k, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return BM_ECUDA;
+  if (f_opt && cudaMemcpyAsync(f_opt, c->ws.f_opt, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return BM_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return BM_ECUDA;
+  if (chunk_counter) *chunk_counter = c->t;
+  return BM_OK;
+}
+
+bm_status bm_objective(bm_ctx* c, double* f_opt_out, float* C_out_host,
+                       uint8_t* mask_out_host) {
+  return bm_get_state(c, C_out_host, mask_out_host, f_opt_out, nullptr);
+}
+
+bm_status bm_set_state(bm_ctx* c, const float* C_host, const uint8_t* mask_host,
+                       double f_opt, int64_t chunk_counter) {
+  if (!c || !C_host || !mask_host || chunk_counter < 0) return BM_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  const int k = c->cfg.k, n = c->cfg.n, npad = c->plan.npad;
+  cudaStream_t st = c->stream;
+  std::vector<float> pad((size_t)k * npad, 0.f);
+  std::vector<uint8_t> m(k);
+  for (int j = 0; j < k; ++j) {
+    m[j] = mask_host[j] ? 1 : 0;
+    for (int f = 0; f < n; ++f) pad[(size_t)j * npad + f] = C_host[(size_t)j * n + f];
+  }
+  if (cudaMemcpyAsync(c->ws.Cinc, pad.data(), pad.size() * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(c->ws.mask_inc, m.data(), k, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(c->ws.f_opt, &f_opt, 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return BM_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return BM_ECUDA;
+  c->t = chunk_counter;
+  return BM_OK;
+}
+
+bm_status bm_fit_host(const bm_config* cfg, const float* X_host, int32_t chunks,
+                      float* C_out_host, uint8_t* mask_out_host,
+                      int32_t* labels_out_host, double* sse_out,
+                      bm_fit_report* report) {
+  if (!cfg || !X_host || chunks < 0) return BM_EINVAL;
+  if (!shape_ok(cfg->m, cfg->n, cfg->k, cfg->s)) return BM_EINVAL;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return BM_ECUDA;
+  float* X = nullptr;
+  int32_t* labels = nullptr;
+  const size_t xbytes = (size_t)cfg->m * cfg->n * 4;
+  bm_status rc = BM_OK;
+  bm_ctx* c = nullptr;
+  if (cudaMalloc(&X, xbytes) != cudaSuccess) { rc = BM_ENOMEM; goto done; }
+  if (labels_out_host && cudaMalloc(&labels, (size_t)cfg->m * 4) != cudaSuccess) { rc = BM_ENOMEM; goto done; }
+  if (cudaMemcpyAsync(X, X_host, xbytes, cudaMemcpyHostToDevice, st) != cudaSuccess) { rc = BM_ECUDA; goto done; }
+  rc = bm_create(cfg, X, st, &c);
+  if (rc != BM_OK) goto done;
+  rc = bm_fit_chunk(c, chunks, report);
+  if (rc != BM_OK) goto done;
+  rc = bm_assign(c, labels, sse_out);
+  if (rc != BM_OK) goto done;
+  if (labels_out_host &&
+      (cudaMemcpyAsync(labels_out_host, labels, (size_t)cfg->m * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess)) { rc = BM_ECUDA; goto done; }
+  rc = bm_objective(c, nullptr, C_out_host, mask_out_host);
+done:
+  if (c) bm_destroy(c);
+  if (labels) cudaFree(labels);
+  if (X) cudaFree(X);
+  cudaStreamDestroy(st);
+  return rc;
+}
+
+// ------------------------------------------------------------ step level
+// Each call builds a private workspace, runs, and frees it.
+static std::mutex g_ops_mu;
+
+bm_status bm_draw_chunk(int64_t m, int64_t s, uint64_t seed, int64_t t,
+                        int32_t* idx_dev, void* stream) {
+  if (!idx_dev || !shape_ok(m, 1, 1, s) || t < 0) return BM_EINVAL;
+  std::lock_guard<std::mutex> g(g_ops_mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Plan p;
+  bm_status rc = make_plan(1, 1, s, &p);
+  if (rc != BM_OK) return rc;
+  Workspace w;
+  rc = ws_create(&w, m, 1, s, p, st);
+  if (rc != BM_OK) return rc;
+  ChunkArgs a = chunk_args(w, p, nullptr, m, 1, 1, s);
+  a.idx = idx_dev;
+  a.seed = seed;
+  a.t = t;
+  a.phases = kPhaseDraw;
+  if (launch_chunk(a, p.grid, p.generic, p.np, p.smem, st) != cudaSuccess) rc = BM_ECUDA;
+  if (rc == BM_OK) rc = check_status(w, st, m);
+  cudaStreamSynchronize(st);
+  w.release();
+  return rc;
+}
+
+bm_status bm_gather(const float* X_dev, int64_t m, int32_t n,
+                    const int32_t* idx_dev, int64_t s, float* P_dev,
+                    void* stream) {
+  if (!X_dev || !idx_dev || !P_dev || !shape_ok(m, n, 1, s)) return BM_EINVAL;
+  std::lock_guard<std::mutex> g(g_ops_mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Plan p;
+  bm_status rc = make_plan(n, 1, s, &p);
+  if (rc != BM_OK) return rc;
+  Workspace w;
+  rc = ws_create(&w, m, 1, s, p, st);
+  if (rc != BM_OK) return rc;
+  ChunkArgs a = chunk_args(w, p, X_dev, m, n, 1, s);
+  a.idx = const_cast<int32_t*>(idx_dev);
+  a.phases = kPhaseGather;
+  if (launch_chunk(a, p.grid, p.generic, p.np, p.smem, st) != cudaSuccess) rc = BM_ECUDA;
+  if (rc == BM_OK) rc = check_status(w, st, m);
+  if (rc == BM_OK &&
+      cudaMemcpy2DAsync(P_dev, n * 4, w.P, p.npad * 4, n * 4, s, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    rc = BM_ECUDA;
+  cudaStreamSynchronize(st);
+  w.release();
+  return rc;
+}
+
+// Copies P (s x n) and (C, mask) into a fresh workspace with padded rows.
+static bm_status stage_inputs(Workspace& w, const Plan& p, const float* P_dev,
+                              long long s, int n, int k, const float* C_dev,
+                              const uint8_t* mask_dev, cudaStream_t st) {
+  if (cudaMemsetAsync(w.P, 0, (size_t)s * p.npad * 4, st) != cudaSuccess) return BM_ECUDA;
+  if (cudaMemcpy2DAsync(w.P, p.npad * 4, P_dev, n * 4, n * 4, s, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return BM_ECUDA;
+  if (cudaMemcpy2DAsync(w.C, p.npad * 4, C_dev, n * 4, n * 4, k, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return BM_ECUDA;
+  if (cudaMemcpyAsync(w.mask, mask_dev, k, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return BM_ECUDA;
+  return BM_OK;
+}
+
+static bm_status unstage_outputs(Workspace& w, const Plan& p, int n, int k,
+                                 float* C_dev, uint8_t* mask_dev, cudaStream_t st) {
+  if (cudaMemcpy2DAsync(C_dev, n * 4, w.C, p.npad * 4, n * 4, k, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return BM_ECUDA;
+  if (cudaMemcpyAsync(mask_dev, w.mask, k, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return BM_ECUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? BM_OK : BM_ECUDA;
+}
+
+bm_status bm_kpp_reseed(const float* P_dev, int64_t s, int32_t n, int32_t k,
+                        float* C_dev, uint8_t* mask_dev, uint64_t seed,
+                        int64_t t, int32_t trials, void* stream) {
+  if (!P_dev || !C_dev || !mask_dev || !shape_ok(s, n, k, s) || t < 0 ||
+      trials < 1 || trials > kMaxTrials)
+    return BM_EINVAL;
+  std::lock_guard<std::mutex> g(g_ops_mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Plan p;
+  bm_status rc = make_plan(n, k, s, &p);
+  if (rc != BM_OK) return rc;
+  Workspace w;
+  rc = ws_create(&w, s, k, s, p, st);
+  if (rc != BM_OK) return rc;
+  rc = stage_inputs(w, p, P_dev, s, n, k, C_dev, mask_dev, st);
+  ChunkArgs a = chunk_args(w, p, nullptr, s, n, k, s);
+  a.seed = seed;
+  a.t = t;
+  a.trials = trials;
+  a.phases = kPhaseKpp;
+  if (rc == BM_OK && launch_chunk(a, p.grid, p.generic, p.np, p.smem, st) != cudaSuccess)
+    rc = BM_ECUDA;
+  if (rc == BM_OK) rc = check_status(w, st, s);
+  if (rc == BM_OK) rc = unstage_outputs(w, p, n, k, C_dev, mask_dev, st);
+  cudaStreamSynchronize(st);
+  w.release();
+  return rc;
+}
+
+bm_status bm_lloyd(const float* P_dev, int64_t s, int32_t n, int32_t k,
+                   float* C_dev, uint8_t* mask_dev, int32_t max_iter,
+                   double tol, double* f_out, int32_t* iters_out,
+                   void* stream) {
+  if (!P_dev || !C_dev || !mask_dev || !shape_ok(s, n, k, s) || max_iter < 0 ||
+      !(tol >= 0.0))
+    return BM_EINVAL;
+  std::lock_guard<std::mutex> g(g_ops_mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (count_live_host(mask_dev, k, st) <= 0) return BM_EINVAL;
+  Plan p;
+  bm_status rc = make_plan(n, k, s, &p);
+  if (rc != BM_OK) return rc;
+  Workspace w;
+  rc = ws_create(&w, s, k, s, p, st);
+  if (rc != BM_OK) return rc;
+  rc = stage_inputs(w, p, P_dev, s, n, k, C_dev, mask_dev, st);
+  ChunkArgs a = chunk_args(w, p, nullptr, s, n, k, s);
+  a.max_iter = max_iter;
+  a.tol = tol;
+  a.phases = kPhaseLloyd;
+  if (rc == BM_OK && launch_chunk(a, p.grid, p.generic, p.np, p.smem, st) != cudaSuccess)
+    rc = BM_ECUDA;
+  if (rc == BM_OK) rc = check_status(w, st, s);
+  if (rc == BM_OK) rc = unstage_outputs(w, p, n, k, C_dev, mask_dev, st);
+  if (rc == BM_OK) {
+    Ctl h{};
+    if (cudaMemcpy(&h, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess) rc = BM_ECUDA;
+    if (f_out) *f_out = h.f_out;
+    if (iters_out) *iters_out = h.iters_out;
+  }
+  cudaStreamSynchronize(st);
+  w.release();
+  return rc;
+}
+
+bm_status bm_assign_rows(const float* X_dev, int64_t m, int32_t n,
+                         const float* C_dev, const uint8_t* mask_dev,
+                         int32_t k, int32_t* labels_dev, float* dmin_dev,
+                         double* sse_out, void* stream) {
+  if (!X_dev || !C_dev || !mask_dev || m < 1 || n < 1 || k < 1 || m > 2147483647LL)
+    return BM_EINVAL;
+  std::lock_guard<std::mutex> g(g_ops_mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (count_live_host(mask_dev, k, st) <= 0) return BM_EINVAL;
+  Plan p;
+  bm_status rc = make_plan(n, k, std::max<long long>(k, 1), &p);
+  if (rc != BM_OK) return rc;
+  Workspace w;
+  rc = ws_create(&w, k, k, k, p, st);
+  if (rc != BM_OK) return rc;
+  rc = assign_impl(X_dev, m, n, k, p, C_dev, n, mask_dev, labels_dev, dmin_dev, w, st, sse_out);
+  cudaStreamSynchronize(st);
+  w.release();
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,182 @@
+// Device-side building blocks shared by the Big-means kernels: the Philox
+// stream, bounded-wait grid barrier, deterministic reductions and the
+// fixed-order argmin.  sm_103a only.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bm {
+
+constexpr int kThreads = 256;            // threads per CTA of every kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxRounds = 64;           // sample-draw rounds (never reached)
+
+// Status codes written to the device status word (same values as bm_status).
+constexpr int kStatusOk = 0;
+constexpr int kStatusTimeout = 4;
+
+// Bounds of every device-side spin: the wait gives up after this many polls
+// or this much wall time (read from %globaltimer), whichever comes first.
+constexpr uint32_t kSpinLimit = 1u << 26;
+constexpr uint64_t kSpinTimeoutNs = 2000000000ull;   // 2 s
+
+// ------------------------------------------------------------ Philox4x64-10
+// Salmon, Moraes, Dror, Shaw, SC'11: 10 rounds of two 64x64->128 products
+// with multipliers M0, M1 and a Weyl key schedule W0, W1.
+struct U64x4 { uint64_t x[4]; };
+
+__device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1,
+                                               uint64_t c2, uint64_t c3,
+                                               uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+    const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+    const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += W0; k1 += W1;
+  }
+  return U64x4{{c0, c1, c2, c3}};
+}
+
+// Word i of stream (seed, chunk t, purpose, round): counter (i/4, round, t,
+// purpose), key (seed, 0), output word i % 4.
+__device__ __forceinline__ uint64_t philox_word(uint64_t seed, uint64_t t,
+                                                uint64_t purpose, uint64_t rnd,
+                                                uint64_t i) {
+  U64x4 w = philox4x64_10(i >> 2, rnd, t, purpose, seed, 0);
+  const int q = int(i & 3);
+  return q == 0 ? w.x[0] : q == 1 ? w.x[1] : q == 2 ? w.x[2] : w.x[3];
+}
+
+// Top 53 bits scaled by 2^-53: a double in [0, 1), exact.
+__device__ __forceinline__ double unit_double(uint64_t w) {
+  return double(w >> 11) * 0x1.0p-53;
+}
+
+// ------------------------------------------------------------ memory helpers
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int ld_volatile(const int* p) {
+  return *reinterpret_cast<const volatile int*>(p);
+}
+
+// ------------------------------------------------------------ grid barrier
+// Monotone-counter barrier for a cooperative launch (all CTAs co-resident).
+// Barrier number e completes when the counter reaches e * gridDim.x.  The
+// waiting thread gives up after kSpinLimit polls or kSpinTimeoutNs, or as
+// soon as another CTA has recorded an error, records BM_ETIMEOUT and
+// returns false; callers then leave the kernel.
+struct GridBarrier {
+  uint32_t* counter;
+  int* status;
+  uint32_t epoch;
+
+  __device__ bool sync() {
+    __shared__ int s_ok;
+    __syncthreads();
+    ++epoch;
+    if (threadIdx.x == 0) {
+      const uint32_t target = epoch * gridDim.x;
+      __threadfence();
+      atomicAdd(counter, 1u);
+      int ok = 1;
+      const uint64_t t0 = global_timer_ns();
+      uint32_t polls = 0;
+      while (ld_acquire(counter) < target) {
+        ++polls;
+        if ((polls & 255u) == 0) {
+          if (ld_volatile(status) != kStatusOk || polls > kSpinLimit ||
+              global_timer_ns() - t0 > kSpinTimeoutNs) {
+            atomicCAS(status, kStatusOk, kStatusTimeout);
+            ok = 0;
+            break;
+          }
+        }
+        __nanosleep(20);
+      }
+      __threadfence();
+      s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+  }
+};
+
+// ------------------------------------------------------------ reductions
+// Fixed-order sums: the result depends only on the inputs and blockDim, so
+// every CTA computing the same sum gets the same bits.
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum_f32(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_sum_i32(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide fixed-order FP64 sum; every thread gets the result.
+__device__ __forceinline__ double block_sum_f64(double v, double* red /*kWarps*/) {
+  v = warp_sum_f64(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int i = 0; i < kWarps; ++i) t += red[i];
+  return t;
+}
+__device__ __forceinline__ int block_sum_i32(int v, int* red /*kWarps*/) {
+  v = warp_sum_i32(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  int t = 0;
+#pragma unroll
+  for (int i = 0; i < kWarps; ++i) t += red[i];
+  return t;
+}
+
+// Sum of x[0..len) (L2-coherent loads) by one warp in a fixed order; every
+// lane gets the result.
+__device__ __forceinline__ double warp_sum_array_f64(const double* x, int len) {
+  const int l = threadIdx.x & 31;
+  double v = 0.0;
+  for (int i = l; i < len; i += 32) v += __ldcg(x + i);
+  return warp_sum_f64(v);
+}
+
+// (d, j) argmin with the lowest index winning ties.
+__device__ __forceinline__ bool better(float d, int j, float bd, int bj) {
+  return d < bd || (d == bd && j < bj);
+}
+__device__ __forceinline__ void warp_argmin(float& d, int& j) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float od = __shfl_xor_sync(0xffffffffu, d, o);
+    const int oj = __shfl_xor_sync(0xffffffffu, j, o);
+    if (better(od, oj, d, j)) { d = od; j = oj; }
+  }
+}
+
+}  // namespace bm
