@@ -186,6 +186,27 @@ bm_status bm_assign_rows(const float* X_dev, int64_t m, int32_t n,
                          int32_t k, int32_t* labels_dev, float* dmin_dev,
                          double* sse_out, void* stream);
 
+/* Allocation-free variant of bm_assign_rows (same arguments, same results
+ * within rounding).  The paper has no counterpart: this serves callers that
+ * cannot allocate device memory when they need an assignment -- a process
+ * that has handed its device memory to its own pool allocator, or a
+ * latency-critical loop that cannot afford cudaMalloc / cudaFree, which may
+ * synchronise the whole device.  The call allocates nothing: its scratch (one
+ * float64 partial per CTA, the last-CTA ticket and the result, 16,640 bytes)
+ * is a fixed array inside the library that every GPU loading the library
+ * holds until the process exits.  The first call on each device looks up that
+ * array's device address (cudaGetSymbolAddress, with the device current);
+ * make that first call before any stream capture begins.  All calls share the
+ * one array, so calls that overlap on the GPU (for example on two streams)
+ * race and must be serialised by the caller.  A launch that would need more
+ * than 2048 CTAs, k > 128, or a centroid table beyond shared memory returns
+ * BM_EUNSUPPORTED. */
+bm_status bm_assign_rows_noalloc(const float* X_dev, int64_t m, int32_t n,
+                                 const float* C_dev, const uint8_t* mask_dev,
+                                 int32_t k, int32_t* labels_dev,
+                                 float* dmin_dev, double* sse_out,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,8 @@ _SIGS = {
     "bm_lloyd": (_i32, [_vp, _i64, _i32, _i32, _vp, _vp, _i32, _dbl, _P(_dbl),
                         _P(_i32), _vp]),
     "bm_assign_rows": (_i32, [_vp, _i64, _i32, _vp, _vp, _i32, _vp, _vp, _P(_dbl), _vp]),
+    "bm_assign_rows_noalloc": (_i32, [_vp, _i64, _i32, _vp, _vp, _i32, _vp, _vp,
+                                      _P(_dbl), _vp]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -209,4 +211,16 @@ def bm_assign_rows(X_dev, m, n, C_dev, mask_dev, k, labels_dev=None, dmin_dev=No
                                _ptr(mask_dev), int(k), _ptr(labels_dev),
                                _ptr(dmin_dev), ctypes.byref(sse), _stream(stream)),
            "bm_assign_rows")
+    return sse.value
+
+
+def bm_assign_rows_noalloc(X_dev, m, n, C_dev, mask_dev, k, labels_dev=None,
+                           dmin_dev=None, stream=None):
+    """bm_assign_rows without device allocation (scratch inside the library)."""
+    sse = _dbl()
+    _check(_lib.bm_assign_rows_noalloc(_ptr(X_dev), int(m), int(n), _ptr(C_dev),
+                                       _ptr(mask_dev), int(k), _ptr(labels_dev),
+                                       _ptr(dmin_dev), ctypes.byref(sse),
+                                       _stream(stream)),
+           "bm_assign_rows_noalloc")
     return sse.value
