@@ -227,6 +227,7 @@ def run_ours(args, wl):
     asg_ms = [e[1].elapsed_time(e[2]) for e in events]
     step_ms = [a + b for a, b in zip(fit_ms, asg_ms)]
     rep, sse = reps[-1]
+    phases = bm.bm_trace(ctx)      # device phase times of the last step
     C = np.zeros((k, n), np.float32)
     mask = np.zeros(k, np.uint8)
     f_opt = bm.bm_objective(ctx, C, mask)
@@ -299,8 +300,9 @@ def run_ours(args, wl):
                "lloyd_iters_per_step": rep["lloyd_iters"],
                "accepted_per_step": rep["accepted"], "n_d_per_step": nd_step,
                "fit_ms_per_step": fit_per_step, "assign_ms_per_step": asg_per_step,
+               "chunk_phase_ms_per_step": phases,
                "wall_s": t_wall,
-               "gpu_launches": args.steps * (T + 1),
+               "gpu_launches": args.steps * (T + (T + 63) // 64 + 1),
                "roofline": roofline,
                "kernels": {"chunk": chunk_kernel, "assign": assign_kernel},
                "clocks": clocks.summary(),

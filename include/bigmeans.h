@@ -132,6 +132,17 @@ bm_status bm_set_state(bm_ctx* ctx, const float* C_host,
                        const uint8_t* mask_host, double f_opt,
                        int64_t chunk_counter);
 
+/* Tracing: cumulative device time (ns) of the chunk phases since bm_create
+ * or bm_reset, as seen by CTA 0 between its phase boundaries: [0] set-up,
+ * [1] gather, [2] K-means++ reseed, [3] Lloyd assignment + partial sums of
+ * CTA 0's rows, [4] wait at the first Lloyd grid barrier, [5] cross-CTA
+ * reduction + centroid update, [6] wait at the second barrier + reload,
+ * [7] keep-the-best; [8], [9], [10] split [3] into the assignment, the
+ * per-warp update slices and their combination into the partial sums
+ * (row-in-register kernels only).  ns_out receives min(count, 11) values.
+ * Diagnostic only; it adds no synchronisation to the kernels. */
+bm_status bm_trace(bm_ctx* ctx, double* ns_out, int32_t count);
+
 /* One-call job on HOST memory: copies X_host (m x n) to the device, runs
  * `chunks` chunks and the final assignment, and copies back C (k x n),
  * mask (k), labels (m) and f(C, X).  Outputs may be NULL.  Uses and frees

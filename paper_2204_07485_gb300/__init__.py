@@ -64,6 +64,7 @@ _SIGS = {
     "bm_objective": (_i32, [_vp, _P(_dbl), _vp, _vp]),
     "bm_get_state": (_i32, [_vp, _vp, _vp, _P(_dbl), _P(_i64)]),
     "bm_set_state": (_i32, [_vp, _vp, _vp, _dbl, _i64]),
+    "bm_trace": (_i32, [_vp, _P(_dbl), _i32]),
     "bm_fit_host": (_i32, [_P(bm_config), _vp, _i32, _vp, _vp, _vp, _P(_dbl),
                            _P(bm_fit_report)]),
     "bm_draw_chunk": (_i32, [_i64, _i64, _u64, _i64, _vp, _vp]),
@@ -166,6 +167,18 @@ def bm_get_state(ctx, C_host, mask_host):
 def bm_set_state(ctx, C_host, mask_host, f_opt, chunk_counter):
     _check(_lib.bm_set_state(ctx, _ptr(C_host), _ptr(mask_host), float(f_opt),
                              int(chunk_counter)), "bm_set_state")
+
+
+PHASES = ("setup", "gather", "kmeanspp", "lloyd_own_rows", "lloyd_barrier1",
+          "lloyd_reduce", "lloyd_barrier2", "keep", "own_assign", "own_slices",
+          "own_combine")
+
+
+def bm_trace(ctx):
+    """Cumulative device time per chunk phase, in ms, keyed by PHASES."""
+    buf = (_dbl * len(PHASES))()
+    _check(_lib.bm_trace(ctx, buf, len(PHASES)), "bm_trace")
+    return {p: buf[i] / 1e6 for i, p in enumerate(PHASES)}
 
 
 def bm_fit_host(cfg, X_host, chunks, C_out_host=None, mask_out_host=None,

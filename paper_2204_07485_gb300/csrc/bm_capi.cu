@@ -39,7 +39,7 @@ static bm_status make_plan(int n, int k, long long s, Plan* out) {
   if (k > kMaxK) return BM_EUNSUPPORTED;
   if (n <= kNpMax) {
     p.generic = false;
-    p.np = n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32;
+    p.np = np_width(n);
     p.npad = p.np;
     p.kpad = 0;
   } else {
@@ -51,8 +51,12 @@ static bm_status make_plan(int n, int k, long long s, Plan* out) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return BM_ECUDA;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // Grid: about 128 sample rows per CTA, at most what stays co-resident.
-  int grid = (int)std::min<long long>((s + 127) / 128, (long long)sms * 8);
+  // Grid: at most one CTA per SM, so that every SM carries the same share of
+  // the sample, and at least 64 (row-in-register path) or 256 (tiled path)
+  // rows per CTA so that small samples do not pay for idle CTAs in every
+  // grid barrier.
+  const int rows_target = p.generic ? 256 : 64;
+  int grid = (int)std::min<long long>((s + rows_target - 1) / rows_target, (long long)sms);
   grid = std::max(grid, 1);
   for (int iter = 0; iter < 8; ++iter) {
     const int R = (int)((s + grid - 1) / grid);
@@ -81,8 +85,9 @@ static bm_status make_plan(int n, int k, long long s, Plan* out) {
 
 // ------------------------------------------------------------ workspace
 struct Workspace {
-  int32_t* idx = nullptr;
-  uint32_t* bitmap = nullptr;
+  int32_t* idx = nullptr;       // sample plan: [plan_cap][s] sorted rows
+  uint32_t* bitmap = nullptr;   // [plan_cap][ceil(m / 32)], zero between draws
+  int plan_cap = 1;             // chunks drawn per sample-plan launch
   float* P = nullptr;
   float* C = nullptr;
   uint8_t* mask = nullptr;
@@ -114,14 +119,22 @@ struct Workspace {
   }
 };
 
+// Chunks per sample-plan launch: up to 64, within 256 MB of plan memory.
+static int plan_capacity(long long m, long long s) {
+  const long long per = ((m + 31) / 32) * 4 + s * 4;
+  long long cap = (256LL << 20) / std::max<long long>(per, 1);
+  return (int)std::max<long long>(1, std::min<long long>(64, cap));
+}
+
 static bm_status ws_create(Workspace* w, long long m, int k, long long s,
-                           const Plan& p, cudaStream_t st) {
+                           const Plan& p, cudaStream_t st, int plan_cap = 1) {
   const size_t words = (size_t)((m + 31) / 32);
   const int G = p.grid;
+  w->plan_cap = plan_cap;
   cudaError_t e = cudaSuccess;
 #define BM_TRY(x) do { e = (x); if (e != cudaSuccess) { w->release(); return BM_ENOMEM; } } while (0)
-  BM_TRY(w->alloc(&w->idx, (size_t)s));
-  BM_TRY(w->alloc(&w->bitmap, words));
+  BM_TRY(w->alloc(&w->idx, (size_t)s * plan_cap));
+  BM_TRY(w->alloc(&w->bitmap, words * plan_cap));
   BM_TRY(w->alloc(&w->P, (size_t)s * p.npad));
   BM_TRY(w->alloc(&w->C, (size_t)k * p.npad));
   BM_TRY(w->alloc(&w->mask, (size_t)k));
@@ -137,7 +150,7 @@ static bm_status ws_create(Workspace* w, long long m, int k, long long s,
   BM_TRY(w->alloc(&w->apart, (size_t)p.agrid));
   BM_TRY(w->alloc(&w->asse, 1));
 #undef BM_TRY
-  cudaMemsetAsync(w->bitmap, 0, words * 4, st);
+  cudaMemsetAsync(w->bitmap, 0, words * 4 * plan_cap, st);
   cudaMemsetAsync(w->C, 0, (size_t)k * p.npad * 4, st);
   cudaMemsetAsync(w->Cinc, 0, (size_t)k * p.npad * 4, st);
   cudaMemsetAsync(w->mask, 0, k, st);
@@ -156,7 +169,7 @@ static ChunkArgs chunk_args(const Workspace& w, const Plan& p, const float* X,
   a.X = X; a.m = m; a.n = n; a.npad = p.npad; a.k = k; a.s = (int)s;
   a.rows_per_cta = p.R; a.kpad = p.kpad;
   a.max_iter = 300; a.tol = 1e-4; a.trials = 3;
-  a.idx = w.idx; a.bitmap = w.bitmap; a.P = w.P; a.C = w.C; a.mask = w.mask;
+  a.idx = w.idx; a.P = w.P; a.C = w.C; a.mask = w.mask;
   a.Cinc = w.Cinc; a.mask_inc = w.mask_inc; a.f_opt = w.f_opt;
   a.part_sum = w.part_sum; a.part_cnt = w.part_cnt; a.part_f = w.part_f;
   a.blk_cnt = w.blk_cnt; a.ctl = w.ctl; a.stats = w.stats;
@@ -172,15 +185,15 @@ static bool shape_ok(long long m, int n, int k, long long s) {
 // Reads the status word; on error clears the control block so that the
 // workspace can be used again.
 static bm_status check_status(Workspace& w, cudaStream_t st, long long m) {
+  (void)m;
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return BM_ECUDA;
   int32_t status = 0;
   e = cudaMemcpy(&status, &w.ctl->status, sizeof(int32_t), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return BM_ECUDA;
   if (status != 0) {
-    // an aborted launch may leave barrier counters and sample bits behind
+    // an aborted launch may leave barrier counters behind
     cudaMemset(w.ctl, 0, sizeof(Ctl));
-    cudaMemset(w.bitmap, 0, (size_t)((m + 31) / 32) * 4);
     cudaDeviceSynchronize();
     return (bm_status)status;
   }
@@ -200,6 +213,8 @@ struct bm_ctx {
   Workspace ws;
   long long t = 0;          // next chunk index
   long long launches = 0;   // selects the barrier counter
+  long long plan_t0 = -1;   // first chunk held by the sample plan (-1: none)
+  long long plan_n = 0;     // chunks held by the sample plan
   long long nd_assign = 0;  // distance evaluations of bm_assign calls
   std::mutex mu;
 };
@@ -247,7 +262,8 @@ bm_status bm_create(const bm_config* cfg, const float* X_dev, void* stream,
   c->stream = static_cast<cudaStream_t>(stream);
   bm_status st = make_plan(cfg->n, cfg->k, cfg->s, &c->plan);
   if (st != BM_OK) { delete c; return st; }
-  st = ws_create(&c->ws, cfg->m, cfg->k, cfg->s, c->plan, c->stream);
+  st = ws_create(&c->ws, cfg->m, cfg->k, cfg->s, c->plan, c->stream,
+                 plan_capacity(cfg->m, cfg->s));
   if (st != BM_OK) { delete c; return st; }
   *out = c;
   return BM_OK;
@@ -271,7 +287,8 @@ bm_status bm_reset(bm_ctx* c) {
   cudaMemsetAsync(c->ws.ctl, 0, sizeof(Ctl), st);
   cudaMemsetAsync(c->ws.stats, 0, sizeof(Stats), st);
   const size_t words = (size_t)((c->cfg.m + 31) / 32);
-  cudaMemsetAsync(c->ws.bitmap, 0, words * 4, st);
+  cudaMemsetAsync(c->ws.bitmap, 0, words * 4 * c->ws.plan_cap, st);
+  c->plan_t0 = -1;
   static const double inf = std::numeric_limits<double>::infinity();
   cudaMemcpyAsync(c->ws.f_opt, &inf, sizeof(double), cudaMemcpyHostToDevice, st);
   c->t = 0;
@@ -295,12 +312,24 @@ bm_status bm_fit_chunk(bm_ctx* c, int32_t chunks, bm_fit_report* out) {
   a.max_iter = c->cfg.max_iter;
   a.tol = c->cfg.tol;
   a.trials = c->cfg.kpp_trials;
-  a.phases = kPhaseDraw | kPhaseGather | kPhaseKpp | kPhaseLloyd | kPhaseKeep;
+  a.phases = kPhaseGather | kPhaseKpp | kPhaseLloyd | kPhaseKeep;
   long long done = 0;
   bm_status st = BM_OK;
   const bool timed = chunks == 0;
   while (true) {
     if (!timed && done >= chunks) break;
+    // the sample plan holds chunks [plan_t0, plan_t0 + plan_cap)
+    if (c->plan_t0 < 0 || c->t < c->plan_t0 || c->t >= c->plan_t0 + c->plan_n) {
+      DrawArgs d{};
+      d.m = c->cfg.m; d.s = (int)c->cfg.s; d.seed = c->cfg.seed; d.t0 = c->t;
+      d.idx = c->ws.idx; d.bitmaps = c->ws.bitmap;
+      int batch = c->ws.plan_cap;
+      if (!timed) batch = (int)std::min<long long>(batch, chunks - done);
+      if (launch_draw(d, batch, c->stream) != cudaSuccess) { st = BM_ECUDA; break; }
+      c->plan_t0 = c->t;
+      c->plan_n = batch;
+    }
+    a.idx = c->ws.idx + (size_t)(c->t - c->plan_t0) * c->cfg.s;
     a.t = c->t;
     a.bar_sel = (int)(c->launches & 1);
     cudaError_t e = launch_chunk(a, c->plan.grid, c->plan.generic, c->plan.np,
@@ -374,6 +403,17 @@ bm_status bm_assign(bm_ctx* c, int32_t* labels_dev, double* sse_out) {
                              c->stream, sse_out);
   if (st == BM_OK) c->nd_assign += c->cfg.m * (long long)live;
   return st;
+}
+
+bm_status bm_trace(bm_ctx* c, double* ns_out, int32_t count) {
+  if (!c || !ns_out || count < 0) return BM_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  Stats h{};
+  if (cudaMemcpyAsync(&h, c->ws.stats, sizeof(Stats), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return BM_ECUDA;
+  for (int i = 0; i < count && i < kNumPhaseTimers; ++i) ns_out[i] = (double)h.phase_ns[i];
+  return BM_OK;
 }
 
 bm_status bm_get_state(bm_ctx* c, float* C_host, uint8_t* mask_host,
@@ -464,21 +504,16 @@ bm_status bm_draw_chunk(int64_t m, int64_t s, uint64_t seed, int64_t t,
   if (!idx_dev || !shape_ok(m, 1, 1, s) || t < 0) return BM_EINVAL;
   std::lock_guard<std::mutex> g(g_ops_mu);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Plan p;
-  bm_status rc = make_plan(1, 1, s, &p);
-  if (rc != BM_OK) return rc;
-  Workspace w;
-  rc = ws_create(&w, m, 1, s, p, st);
-  if (rc != BM_OK) return rc;
-  ChunkArgs a = chunk_args(w, p, nullptr, m, 1, 1, s);
-  a.idx = idx_dev;
-  a.seed = seed;
-  a.t = t;
-  a.phases = kPhaseDraw;
-  if (launch_chunk(a, p.grid, p.generic, p.np, p.smem, st) != cudaSuccess) rc = BM_ECUDA;
-  if (rc == BM_OK) rc = check_status(w, st, m);
-  cudaStreamSynchronize(st);
-  w.release();
+  uint32_t* bitmap = nullptr;
+  const size_t words = (size_t)((m + 31) / 32);
+  if (cudaMalloc(&bitmap, words * 4) != cudaSuccess) return BM_ENOMEM;
+  bm_status rc = BM_OK;
+  if (cudaMemsetAsync(bitmap, 0, words * 4, st) != cudaSuccess) rc = BM_ECUDA;
+  DrawArgs d{};
+  d.m = m; d.s = (int)s; d.seed = seed; d.t0 = t; d.idx = idx_dev; d.bitmaps = bitmap;
+  if (rc == BM_OK && launch_draw(d, 1, st) != cudaSuccess) rc = BM_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) rc = BM_ECUDA;
+  cudaFree(bitmap);
   return rc;
 }
 

@@ -11,11 +11,11 @@ constexpr int kMaxTrials = 4;      // K-means++ candidates per centre (paper: 3)
 constexpr int kMaxK = 128;         // centroids per job handled by the kernels
 constexpr int kRoundSlots = 64;    // per-round draw counters (== kMaxRounds)
 constexpr int kNpMax = 32;         // widest row kept in registers
+constexpr int kNumPhaseTimers = 11;  // see Stats::phase_ns
 
 // Phases of the chunk kernel (Alg. 1 loop body).
 enum Phase : int {
-  kPhaseDraw = 1,     // sample indices of chunk t
-  kPhaseGather = 2,   // P = X[idx]
+  kPhaseGather = 2,   // P = X[idx] (idx drawn ahead by the sample plan)
   kPhaseKpp = 4,      // K-means++ reseed of degenerate centroids
   kPhaseLloyd = 8,    // K-means on P
   kPhaseKeep = 16,    // keep-the-best against the incumbent
@@ -25,7 +25,6 @@ enum Phase : int {
 // leaves it ready for the next one (see the kernel epilogue).
 struct Ctl {
   uint32_t bar[2];                    // alternating grid-barrier counters
-  uint32_t round_cnt[kRoundSlots];    // new distinct draws per sample round
   int32_t status;                     // sticky error word (bm_status values)
   int32_t cand[kMaxTrials];           // K-means++ candidate rows of a slot
   int32_t iters_out;                  // Lloyd update steps of the last launch
@@ -40,6 +39,13 @@ struct Stats {
   long long accepted;
   long long lloyd_iters;
   long long n_d;
+  // device time per phase (ns, CTA 0's %globaltimer between its phase
+  // boundaries): [0] setup, [1] gather, [2] K-means++, [3] Lloyd own rows
+  // (assignment + partial sums), [4] Lloyd first barrier wait, [5] Lloyd
+  // cross-CTA reduction + update, [6] Lloyd second barrier wait + reload,
+  // [7] keep-the-best; [8..10] split [3] into assignment, update slices and
+  // slice combination + partial-sum stores
+  unsigned long long phase_ns[kNumPhaseTimers];
 };
 
 struct ChunkArgs {
@@ -56,7 +62,6 @@ struct ChunkArgs {
   int bar_sel;         // which Ctl::bar counter this launch uses
   int kpad;            // k rounded up to 32 (generic path)
   int32_t* idx;        // s
-  uint32_t* bitmap;    // ceil(m / 32), all zero between launches
   float* P;            // s x npad
   float* C;            // k x npad working centroids (C', C'')
   uint8_t* mask;       // k working mask
@@ -85,39 +90,73 @@ struct AssignArgs {
   uint32_t* ticket;    // zero between launches
 };
 
+struct DrawArgs {
+  long long m;
+  int s;
+  unsigned long long seed;
+  long long t0;        // first chunk of the batch; CTA b draws chunk t0 + b
+  int32_t* idx;        // [batch][s] sorted sample rows
+  uint32_t* bitmaps;   // [batch][ceil(m / 32)], all zero between launches
+};
+
 // Shared-memory layout of the chunk kernel (bytes), identical on host/device.
 struct ChunkSmem {
-  int cen, live, sw, cw, lab, dmin, dc, cand, stage, red, total;
-  int wu;              // warps that own an update slice
+  int cen, crow, live, lidx, sw, cw, lab, dmin, dc, cand, stage, prow, red, total;
+  int wu;              // update accumulators: warps (row-in-register path) or
+                       // row groups (tiled path) that own a private copy
 };
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
+
+// Register row width of the row-in-register kernels for n <= kNpMax.
+__host__ __device__ inline int np_width(int n) {
+  return n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : n <= 28 ? 28 : 32;
+}
+
+// Threads per CTA of the chunk kernel: 384 for the row-in-register path
+// (one sample row per thread for up to 384 rows per CTA, leaving up to 170
+// registers per thread), 256 for the tiled path.
+__host__ __device__ inline int chunk_threads(bool generic) { return generic ? 256 : 384; }
 
 __host__ __device__ inline ChunkSmem chunk_smem(int npad, int k, int kpad, int R,
                                                 bool generic) {
   ChunkSmem L;
   int o = 0;
+  const int nthreads = chunk_threads(generic);
   L.cen = o;   o += align_up((generic ? npad * kpad : k * npad) * 4, 16);
+  L.crow = o;  o += generic ? align_up(k * npad * 4, 16) : 0;   // row-major copy
   L.live = o;  o += align_up(k * 4, 16);
-  // update slices: as many warps as fit in 64 KB (at least one)
-  int per = k * 32 * 4;
-  int wu = (64 * 1024) / per;
-  if (wu > 8) wu = 8;
+  L.lidx = o;  o += align_up((k + 1) * 4, 16);   // live list, count at [k]
+  int wu;
+  if (!generic) {
+    // one 32-feature slice [k][32] per update warp, as many as fit in 64 KB
+    wu = (64 * 1024) / (k * 32 * 4);
+    if (wu > nthreads / 32) wu = nthreads / 32;
+  } else {
+    // one [k][npad] accumulator per row group, threads = groups x features
+    wu = nthreads / npad;
+    const int cap = (64 * 1024) / (k * npad * 4);
+    if (wu > cap) wu = cap;
+    if (wu > 8) wu = 8;
+  }
   if (wu < 1) wu = 1;
   L.wu = wu;
-  L.sw = o;    o += align_up(wu * per, 16);
-  L.cw = o;    o += align_up(wu * k * 4, 16);
+  L.sw = o;    o += align_up((generic ? wu * k * npad : wu * k * 32) * 4, 16);
+  L.cw = o;    o += align_up((generic ? wu : nthreads / 32) * k * 4, 16);
   L.lab = o;   o += align_up(R * 4, 16);
   L.dmin = o;  o += align_up(R * 4, 16);
   L.dc = o;    o += align_up(kMaxTrials * R * 4, 16);
   L.cand = o;  o += align_up(kMaxTrials * npad * 4, 16);
   L.stage = o; o += generic ? align_up(64 * npad * 4, 16) : 0;
-  L.red = o;   o += 64 * 8;
+  // row-in-register path: the CTA's R sample rows stay resident for the chunk
+  L.prow = o;  o += generic ? 0 : align_up(R * npad * 4, 16);
+  L.red = o;   o += 80 * 8;
   L.total = o;
   return L;
 }
 
-// Host-side launch helpers (bm_kernels.cu).
+// Host-side launch helpers (bm_kernels.cu, bm_sample.cu).
+cudaError_t launch_draw(const DrawArgs& a, int chunks, cudaStream_t st);
 cudaError_t launch_chunk(const ChunkArgs& a, int grid, bool generic, int np,
                          size_t smem, cudaStream_t st);
 int chunk_max_grid(bool generic, int np, size_t smem);

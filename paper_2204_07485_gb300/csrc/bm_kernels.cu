@@ -1,7 +1,7 @@
 // Big-means hot path on sm_103a.
 //
 // chunk_kernel: one cooperative launch per chunk runs Alg. 1's loop body on
-// the whole GPU -- sample draw (Sec. 3.5), gather P = X[idx], K-means++ reseed
+// the whole GPU -- gather P = X[idx] of the pre-drawn sample, K-means++ reseed
 // of degenerate centroids (Sec. 3.3, three candidates per Sec. 5), Lloyd
 // iterations (Sec. 2) with the stop rule of Sec. 5, and keep-the-best
 // (Alg. 1) -- separated by bounded-wait grid barriers instead of kernel
@@ -31,22 +31,27 @@ namespace bm {
 
 // ---------------------------------------------------------------- smem view
 struct Smem {
-  float* cen;   // np: [k][npad]   generic: [npad][kpad]
+  float* cen;   // np: [k][npad]   generic: [npad][kpad] (transposed)
+  float* crow;  // generic: [k][npad] row-major copy of the centroids
   int* live;    // [k]
-  float* sw;    // [wu][k][32] per-warp update slices
-  int* cw;      // [wu][k] per-warp member counts
+  int* lidx;    // [k + 1]: live centroid indices ascending, count at [k]
+  float* sw;    // update accumulators (np: [wu][k][32], generic: [wu][k][npad])
+  int* cw;      // [wu][k] member counts
   int* lab;     // [R] labels of own rows
   float* dmin;  // [R] nearest squared distance / K-means++ D^2 of own rows
   float* dc;    // [kMaxTrials][R] candidate distances of own rows
   float* cand;  // [kMaxTrials][npad] candidate rows
-  float* stage; // [npad][64] transposed row tile (generic)
+  float* stage; // generic: swizzled transposed 64-row tile
+  float* prow;  // np: [R][npad] own sample rows, resident for the chunk
   double* red;  // scratch for block reductions (64 doubles)
 };
 
 __device__ __forceinline__ Smem carve(char* base, const ChunkSmem& L) {
   Smem S;
   S.cen = reinterpret_cast<float*>(base + L.cen);
+  S.crow = reinterpret_cast<float*>(base + L.crow);
   S.live = reinterpret_cast<int*>(base + L.live);
+  S.lidx = reinterpret_cast<int*>(base + L.lidx);
   S.sw = reinterpret_cast<float*>(base + L.sw);
   S.cw = reinterpret_cast<int*>(base + L.cw);
   S.lab = reinterpret_cast<int*>(base + L.lab);
@@ -54,26 +59,75 @@ __device__ __forceinline__ Smem carve(char* base, const ChunkSmem& L) {
   S.dc = reinterpret_cast<float*>(base + L.dc);
   S.cand = reinterpret_cast<float*>(base + L.cand);
   S.stage = reinterpret_cast<float*>(base + L.stage);
+  S.prow = reinterpret_cast<float*>(base + L.prow);
   S.red = reinterpret_cast<double*>(base + L.red);
   return S;
 }
 
 __device__ __forceinline__ float sq(float e, float acc) { return fmaf(e, e, acc); }
 
-// Centroid row j (global, k x cstride) -> shared table, both layouts.
-template <bool GENERIC>
-__device__ void load_centroids(float* cen, int* live, const float* C,
+// Phase timers of CTA 0, accumulated in shared memory during the launch and
+// added to Stats::phase_ns once at its end (a global read-modify-write per
+// tick would stall CTA 0, and through the next grid barrier every CTA).
+__device__ __forceinline__ unsigned long long* phase_slots() {
+  __shared__ unsigned long long slots[kNumPhaseTimers];
+  return slots;
+}
+
+// Thread 0 of CTA 0 adds the time since *t0 to slot i.
+__device__ __forceinline__ void phase_tick(Stats* st, int i, uint64_t* t0) {
+  (void)st;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const uint64_t t = global_timer_ns();
+    phase_slots()[i] += t - *t0;
+    *t0 = t;
+  }
+}
+
+// lidx[0..c) <- indices of the live centroids in ascending order, lidx[k] = c.
+// Called by all threads; ends with a barrier.
+__device__ __forceinline__ void build_live_list(const int* live, int* lidx, int k) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int c = 0;
+    for (int base = 0; base < k; base += 32) {
+      const int j = base + (int)threadIdx.x;
+      const bool on = j < k && live[j];
+      const unsigned bal = __ballot_sync(0xffffffffu, on);
+      if (on) lidx[c + __popc(bal & ((1u << threadIdx.x) - 1u))] = j;
+      c += __popc(bal);
+    }
+    if (threadIdx.x == 0) lidx[k] = c;
+  }
+  __syncthreads();
+}
+
+// Centroid (j, f) into the shared tables of either layout (the tiled layout
+// keeps a row-major copy too unless WITH_ROW is false).
+template <bool GENERIC, bool WITH_ROW = true>
+__device__ __forceinline__ void put_centroid(float* cen, float* crow, int j, int f,
+                                             float v, int npad, int kpad) {
+  if (GENERIC) {
+    cen[f * kpad + j] = v;
+    if (WITH_ROW) crow[j * npad + f] = v;
+  } else {
+    cen[j * npad + f] = v;
+  }
+}
+
+// Centroid rows (global, k x cstride) -> shared tables; mask -> live.
+template <bool GENERIC, bool WITH_ROW = true>
+__device__ void load_centroids(float* cen, float* crow, int* live, const float* C,
                                int cstride, const uint8_t* mask, int k, int n,
                                int npad, int kpad, bool coherent) {
-  for (int q = threadIdx.x; q < k * npad; q += kThreads) {
+  for (int q = threadIdx.x; q < k * npad; q += blockDim.x) {
     const int j = q / npad, f = q - j * npad;
     float v = 0.f;
     if (f < n) v = coherent ? __ldcg(C + (size_t)j * cstride + f)
                             : __ldg(C + (size_t)j * cstride + f);
-    if (GENERIC) cen[f * kpad + j] = v;
-    else cen[j * npad + f] = v;
+    put_centroid<GENERIC, WITH_ROW>(cen, crow, j, f, v, npad, kpad);
   }
-  for (int j = threadIdx.x; j < k; j += kThreads) {
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
     const unsigned char mv = coherent
         ? __ldcg(reinterpret_cast<const unsigned char*>(mask) + j)
         : __ldg(reinterpret_cast<const unsigned char*>(mask) + j);
@@ -83,6 +137,7 @@ __device__ void load_centroids(float* cen, int* live, const float* C,
 }
 
 // ------------------------------------------------------------ np path rows
+// Row of n floats (zero padded to NP) from global memory into registers.
 template <int NP>
 __device__ __forceinline__ void load_row_np(float (&p)[NP], const float* row,
                                             int n, bool vec4, bool coherent) {
@@ -102,63 +157,103 @@ __device__ __forceinline__ void load_row_np(float (&p)[NP], const float* row,
   }
 }
 
+// Row of NP floats from shared memory (16-byte aligned) into registers.
+template <int NP>
+__device__ __forceinline__ void load_row_smem(float (&p)[NP], const float* row) {
+#pragma unroll
+  for (int q = 0; q < NP / 4; ++q) {
+    const float4 v = reinterpret_cast<const float4*>(row)[q];
+    p[4 * q] = v.x; p[4 * q + 1] = v.y; p[4 * q + 2] = v.z; p[4 * q + 3] = v.w;
+  }
+}
+
+// Squared distance of a register-held row to centroid row c (NP floats in
+// shared memory): four independent partial sums (features f mod 4),
+// combined as (s0 + s1) + (s2 + s3).
+template <int NP>
+__device__ __forceinline__ float dist_np(const float (&p)[NP], const float* c) {
+  const float4* c4 = reinterpret_cast<const float4*>(c);
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+  for (int u = 0; u < NP / 4; ++u) {
+    const float4 v = c4[u];
+    s0 = sq(p[4 * u] - v.x, s0);
+    s1 = sq(p[4 * u + 1] - v.y, s1);
+    s2 = sq(p[4 * u + 2] - v.z, s2);
+    s3 = sq(p[4 * u + 3] - v.w, s3);
+  }
+  return (s0 + s1) + (s2 + s3);
+}
+
+// Nearest live centroid of one register-held row.  Two centroids per step
+// keep eight independent chains in flight; centroids are compared in
+// ascending index order with strict <, so the lowest index wins ties.  bj
+// stays out of range when no centroid is live.
 template <int NP>
 __device__ __forceinline__ void nearest_np(const float (&p)[NP],
-                                           const float* cen, const int* live,
+                                           const float* cen, const int* lidx,
                                            int k, int& bj, float& bd) {
   bd = INFINITY;
-  bj = INT_MAX;   // stays out of range when no centroid is live
-  bool any = false;
-  for (int j = 0; j < k; ++j) {
-    if (!live[j]) continue;
-    const float4* c4 = reinterpret_cast<const float4*>(cen + j * NP);
-    float d = 0.f;
-#pragma unroll
-    for (int q = 0; q < NP / 4; ++q) {
-      const float4 c = c4[q];
-      d = sq(p[4 * q] - c.x, d);
-      d = sq(p[4 * q + 1] - c.y, d);
-      d = sq(p[4 * q + 2] - c.z, d);
-      d = sq(p[4 * q + 3] - c.w, d);
-    }
-    if (!any || d < bd) { bd = d; bj = j; any = true; }
+  bj = INT_MAX;
+  const int nl = lidx[k];
+  int q = 0;
+#pragma unroll 1
+  for (; q + 2 <= nl; q += 2) {
+    const int j0 = lidx[q], j1 = lidx[q + 1];
+    const float d0 = dist_np<NP>(p, cen + j0 * NP);
+    const float d1 = dist_np<NP>(p, cen + j1 * NP);
+    if (bj == INT_MAX || d0 < bd) { bd = d0; bj = j0; }
+    if (d1 < bd) { bd = d1; bj = j1; }
+  }
+  if (q < nl) {
+    const int j0 = lidx[q];
+    const float d0 = dist_np<NP>(p, cen + j0 * NP);
+    if (bj == INT_MAX || d0 < bd) { bd = d0; bj = j0; }
   }
 }
 
 // -------------------------------------------------------- generic path rows
-// stage[f][r] <- src[r][f] for r < rows (64-row tile), zero elsewhere.
+// 64-row tiles are staged transposed, element (f, r) at f * 64 + (r ^ swz(f)).
+// The XOR moves whole 4-row groups, so 4 consecutive rows stay one aligned
+// float4, lanes walking rows hit 32 distinct banks, and threads walking
+// features see at most a 4-way bank conflict.
+__device__ __forceinline__ int swz(int f) { return (f & 7) << 2; }
+
+// stage <- rows [0, rows) of src (row stride `stride`), zero elsewhere.
 __device__ void stage_tile(float* stage, const float* src, size_t stride,
                            int rows, int n, int npad, bool vec4, bool coherent) {
   if (vec4) {
     const int nq = npad / 4;
-    for (int e = threadIdx.x; e < 64 * nq; e += kThreads) {
+    for (int e = threadIdx.x; e < 64 * nq; e += blockDim.x) {
       const int r = e & 63, q = e >> 6;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (r < rows && 4 * q < n) {
         const float4* p = reinterpret_cast<const float4*>(src + (size_t)r * stride) + q;
         v = coherent ? __ldcg(p) : __ldg(p);
       }
-      stage[(4 * q) * 64 + r] = v.x;
-      stage[(4 * q + 1) * 64 + r] = v.y;
-      stage[(4 * q + 2) * 64 + r] = v.z;
-      stage[(4 * q + 3) * 64 + r] = v.w;
+      const int f = 4 * q;
+      stage[f * 64 + (r ^ swz(f))] = v.x;
+      stage[(f + 1) * 64 + (r ^ swz(f + 1))] = v.y;
+      stage[(f + 2) * 64 + (r ^ swz(f + 2))] = v.z;
+      stage[(f + 3) * 64 + (r ^ swz(f + 3))] = v.w;
     }
   } else {
-    for (int e = threadIdx.x; e < 64 * npad; e += kThreads) {
+    for (int e = threadIdx.x; e < 64 * npad; e += blockDim.x) {
       const int r = e & 63, f = e >> 6;
       float v = 0.f;
       if (r < rows && f < n) {
         const float* p = src + (size_t)r * stride + f;
         v = coherent ? __ldcg(p) : __ldg(p);
       }
-      stage[f * 64 + r] = v;
+      stage[f * 64 + (r ^ swz(f))] = v;
     }
   }
   __syncthreads();
 }
 
-// Nearest live centroid of the 64 staged rows; lane r of warp w reports tile
-// row 8w + r through (bj, bd) and returns true when that row exists.
+// Nearest live centroid of the 64 staged rows (8 warps x 8 rows, one lane
+// per centroid of each group of 32); lane r of warp w reports tile row
+// 8w + r through (bj, bd) and returns true when that row exists.
 __device__ __forceinline__ bool nearest_tile(const float* stage,
                                              const float* cenT,
                                              const int* live, int k, int kpad,
@@ -171,10 +266,11 @@ __device__ __forceinline__ bool nearest_tile(const float* stage,
   for (int g = 0; g < 4; ++g)
 #pragma unroll
     for (int r = 0; r < 8; ++r) acc[g][r] = 0.f;
-  const float* sp = stage + w * 8;
   for (int f = 0; f < n; ++f) {
-    const float4 pa = *reinterpret_cast<const float4*>(sp + f * 64);
-    const float4 pb = *reinterpret_cast<const float4*>(sp + f * 64 + 4);
+    const float* sp = stage + f * 64;
+    const int sz = swz(f);
+    const float4 pa = *reinterpret_cast<const float4*>(sp + ((w * 8) ^ sz));
+    const float4 pb = *reinterpret_cast<const float4*>(sp + ((w * 8 + 4) ^ sz));
     const float* cf = cenT + f * kpad + l;
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
@@ -210,18 +306,31 @@ __device__ __forceinline__ bool nearest_tile(const float* stage,
   return mine;
 }
 
-// ------------------------------------------------------ own-row assignment
+// ------------------------------------------------------ own-row helpers
+// Own sample rows -> the resident shared copy (row-in-register path), when
+// P was written by the host rather than by this launch's gather.
+template <int NP>
+__device__ void stage_own_rows(const ChunkArgs& a, const Smem& S, int r0, int nrows) {
+  const int nq = NP / 4;
+  for (int e = threadIdx.x; e < nrows * nq; e += blockDim.x) {
+    const int i = e / nq, q = e - i * nq;
+    reinterpret_cast<float4*>(S.prow + i * NP)[q] =
+        __ldcg(reinterpret_cast<const float4*>(a.P + (size_t)(r0 + i) * NP) + q);
+  }
+  __syncthreads();
+}
+
 // Nearest live centroid of every own row -> S.lab / S.dmin.
 template <int NP, bool GENERIC>
 __device__ void assign_own_rows(const ChunkArgs& a, const Smem& S, int r0,
                                 int nrows) {
   if constexpr (!GENERIC) {
-    for (int i = threadIdx.x; i < nrows; i += kThreads) {
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
       float p[NP];
-      load_row_np<NP>(p, a.P + (size_t)(r0 + i) * a.npad, a.n, true, true);
+      load_row_smem<NP>(p, S.prow + i * NP);
       int j;
       float d;
-      nearest_np<NP>(p, S.cen, S.live, a.k, j, d);
+      nearest_np<NP>(p, S.cen, S.lidx, a.k, j, d);
       S.lab[i] = j;
       S.dmin[i] = d;
     }
@@ -243,81 +352,239 @@ __device__ void assign_own_rows(const ChunkArgs& a, const Smem& S, int r0,
   }
 }
 
-// Fixed-order float64 sum of S.dmin over own rows (every thread gets it).
+// Fixed-order sum of S.dmin over own rows, carried exactly in FP32 pairs
+// (TwoSum) within each warp and added up in FP64 by one thread; every thread
+// gets the result.
 __device__ __forceinline__ double own_dmin_sum(const Smem& S, int nrows) {
-  double v = 0.0;
-  for (int i = threadIdx.x; i < nrows; i += kThreads) v += (double)S.dmin[i];
-  return block_sum_f64(v, S.red);
+  float hi = 0.f, lo = 0.f;
+  for (int i = threadIdx.x; i < nrows; i += blockDim.x) two_sum_acc(hi, lo, S.dmin[i]);
+  warp_two_sum(hi, lo);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) S.red[w] = (double)hi + (double)lo;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t += S.red[i];
+    S.red[32] = t;
+  }
+  __syncthreads();
+  return S.red[32];
 }
 
 // Squared distances of own rows to the nc candidate rows in S.cand
-// (warp per row, lanes over features) -> S.dc[c][i].
+// -> S.dc[c][i].
+template <int NP, bool GENERIC>
 __device__ void own_rows_to_cands(const ChunkArgs& a, const Smem& S, int r0,
                                   int nrows, int nc) {
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const int R = a.rows_per_cta;
-  for (int i = w; i < nrows; i += kWarps) {
-    float d[kMaxTrials];
+  const int R = a.rows_per_cta, npad = a.npad;
+  if constexpr (!GENERIC) {
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+      float p[NP];
+      load_row_smem<NP>(p, S.prow + i * NP);
+      for (int c = 0; c < nc; ++c) {
+        const float4* c4 = reinterpret_cast<const float4*>(S.cand + c * npad);
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
-    for (int c = 0; c < kMaxTrials; ++c) d[c] = 0.f;
-    const float* row = a.P + (size_t)(r0 + i) * a.npad;
-    for (int f = l; f < a.n; f += 32) {
-      const float p = __ldcg(row + f);
-#pragma unroll
-      for (int c = 0; c < kMaxTrials; ++c)
-        if (c < nc) d[c] = sq(p - S.cand[c * a.npad + f], d[c]);
-    }
-#pragma unroll
-    for (int c = 0; c < kMaxTrials; ++c)
-      if (c < nc) {
-        const float t = warp_sum_f32(d[c]);
-        if (l == 0) S.dc[c * R + i] = t;
-      }
-  }
-  __syncthreads();
-}
-
-// Per-warp slices of sum_i (p_i - c_{label_i}) and member counts of own rows,
-// combined over warps in a fixed order into part_sum[j][f][b], part_cnt[j][b].
-template <bool GENERIC>
-__device__ void update_partials(const ChunkArgs& a, const Smem& S,
-                                const ChunkSmem& L, int r0, int nrows, int G) {
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const int k = a.k, n = a.n, npad = a.npad, b = blockIdx.x;
-  for (int fs = 0; fs < n; fs += 32) {
-    if (w < L.wu) {
-      float* my = S.sw + w * k * 32;
-      for (int q = l; q < k * 32; q += 32) my[q] = 0.f;
-      if (fs == 0)
-        for (int j = l; j < k; j += 32) S.cw[w * k + j] = 0;
-      __syncwarp();
-      const int f = fs + l;
-      for (int i = w; i < nrows; i += L.wu) {
-        const int j = S.lab[i];
-        if (j >= k) continue;   // no live centroid: nothing to accumulate
-        if (f < n) {
-          const float c = GENERIC ? __ldcg(a.C + (size_t)j * npad + f)
-                                  : S.cen[j * npad + f];
-          my[j * 32 + l] += __ldcg(a.P + (size_t)(r0 + i) * npad + f) - c;
+        for (int u = 0; u < NP / 4; ++u) {
+          const float4 v = c4[u];
+          s0 = sq(p[4 * u] - v.x, s0);
+          s1 = sq(p[4 * u + 1] - v.y, s1);
+          s2 = sq(p[4 * u + 2] - v.z, s2);
+          s3 = sq(p[4 * u + 3] - v.w, s3);
         }
-        if (fs == 0 && l == 0) S.cw[w * k + j] += 1;
+        S.dc[c * R + i] = (s0 + s1) + (s2 + s3);
       }
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < k * 32; q += kThreads) {
-      const int j = q >> 5, f = fs + (q & 31);
-      if (f < n) {
-        float sum = 0.f;
-        for (int u = 0; u < L.wu; ++u) sum += S.sw[u * k * 32 + q];
-        a.part_sum[((size_t)j * npad + f) * G + b] = sum;
+  } else {
+    for (int t0 = 0; t0 < nrows; t0 += 64) {
+      const int rows = min(64, nrows - t0);
+      stage_tile(S.stage, a.P + (size_t)(r0 + t0) * npad, npad, rows, a.n, npad,
+                 true, true);
+      for (int e = threadIdx.x; e < 64 * nc; e += blockDim.x) {
+        const int r = e & 63, c = e >> 6;
+        const float* cr = S.cand + c * npad;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int f = 0;
+        for (; f + 4 <= a.n; f += 4) {
+          s0 = sq(S.stage[f * 64 + (r ^ swz(f))] - cr[f], s0);
+          s1 = sq(S.stage[(f + 1) * 64 + (r ^ swz(f + 1))] - cr[f + 1], s1);
+          s2 = sq(S.stage[(f + 2) * 64 + (r ^ swz(f + 2))] - cr[f + 2], s2);
+          s3 = sq(S.stage[(f + 3) * 64 + (r ^ swz(f + 3))] - cr[f + 3], s3);
+        }
+        for (; f < a.n; ++f) s0 = sq(S.stage[f * 64 + (r ^ swz(f))] - cr[f], s0);
+        if (r < rows) S.dc[c * R + t0 + r] = (s0 + s1) + (s2 + s3);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// One Lloyd assignment over own rows plus the partial sums of the update:
+// S.lab / S.dmin, part_sum[j][f][b] = sum over own rows labelled j of
+// (p_f - c_jf) and part_cnt[j][b].  Every sum has a fixed order.
+//   np path: per-warp slices [k][32], lane = feature, warp w takes rows
+//            w, w + wu, ...; rows and centroids read from shared memory;
+//   generic: per row-group accumulators [k][npad], thread = (group, feature),
+//            rows of each staged tile split among the groups.
+template <int NP, bool GENERIC>
+__device__ void lloyd_own_rows(const ChunkArgs& a, const Smem& S,
+                               const ChunkSmem& L, int r0, int nrows, int G) {
+  const int k = a.k, n = a.n, npad = a.npad, b = blockIdx.x;
+  if constexpr (!GENERIC) {
+    uint64_t tsub = global_timer_ns();
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // member counts: in the update slices' spare lane 31 when n < 32,
+    // otherwise per warp by ballot during the assignment
+    const bool count_lane = n < 32;
+    for (int q = threadIdx.x; q < nw * k; q += blockDim.x) S.cw[q] = 0;
+    __syncthreads();
+    for (int i0 = 0; i0 < nrows; i0 += blockDim.x) {
+      const int i = i0 + threadIdx.x;
+      int j = INT_MAX;
+      if (i < nrows) {
+        float p[NP];
+        load_row_smem<NP>(p, S.prow + i * NP);
+        float d;
+        nearest_np<NP>(p, S.cen, S.lidx, k, j, d);
+        S.lab[i] = j;
+        S.dmin[i] = d;
+      }
+      if (!count_lane) {
+        const int nl = S.lidx[k];
+        for (int q = 0; q < nl; ++q) {
+          const int jj = S.lidx[q];
+          const unsigned bal = __ballot_sync(0xffffffffu, j == jj);
+          if (l == 0 && bal) S.cw[w * k + jj] += __popc(bal);
+        }
       }
     }
-    if (fs == 0)
-      for (int j = threadIdx.x; j < k; j += kThreads) {
-        int c = 0;
-        for (int u = 0; u < L.wu; ++u) c += S.cw[u * k + j];
-        a.part_cnt[(size_t)j * G + b] = c;
+    __syncthreads();
+    phase_tick(a.stats, 8, &tsub);
+    for (int fs = 0; fs < n; fs += 32) {
+      if (w < L.wu) {
+        float* my = S.sw + w * k * 32;
+        for (int q = l; q < k * 32; q += 32) my[q] = 0.f;
+        __syncwarp();
+        const int f = fs + l;
+        const bool feat = f < n;
+        const bool cnt = count_lane && fs == 0 && l == 31;   // adds 1 per member
+        const bool on = feat || cnt;
+        const int fc = feat ? f : 0;
+        const int step = L.wu;
+        int i = w;
+        // four rows at a time: when their labels differ the four
+        // read-modify-writes are independent and overlap; otherwise they run
+        // in row order.  Either way each slice entry sums its rows in row
+        // order, so the result does not depend on the batching.
+        for (; i + 3 * step < nrows; i += 4 * step) {
+          const int j0 = S.lab[i], j1 = S.lab[i + step];
+          const int j2 = S.lab[i + 2 * step], j3 = S.lab[i + 3 * step];
+          if ((j0 | j1 | j2 | j3) >= k) {   // a row without a live centroid
+            for (int u = 0; u < 4; ++u) {
+              const int ju = S.lab[i + u * step];
+              if (ju < k && on)
+                my[ju * 32 + l] += feat ? S.prow[(i + u * step) * NP + fc] - S.cen[ju * NP + fc]
+                                        : 1.f;
+            }
+            continue;
+          }
+          float v0 = 1.f, v1 = 1.f, v2 = 1.f, v3 = 1.f;
+          if (feat) {
+            v0 = S.prow[i * NP + f] - S.cen[j0 * NP + f];
+            v1 = S.prow[(i + step) * NP + f] - S.cen[j1 * NP + f];
+            v2 = S.prow[(i + 2 * step) * NP + f] - S.cen[j2 * NP + f];
+            v3 = S.prow[(i + 3 * step) * NP + f] - S.cen[j3 * NP + f];
+          } else if (!cnt) {
+            v0 = v1 = v2 = v3 = 0.f;
+          }
+          const bool distinct = j0 != j1 && j0 != j2 && j0 != j3 && j1 != j2 &&
+                                j1 != j3 && j2 != j3;
+          if (distinct) {
+            const float o0 = my[j0 * 32 + l], o1 = my[j1 * 32 + l];
+            const float o2 = my[j2 * 32 + l], o3 = my[j3 * 32 + l];
+            my[j0 * 32 + l] = o0 + v0;
+            my[j1 * 32 + l] = o1 + v1;
+            my[j2 * 32 + l] = o2 + v2;
+            my[j3 * 32 + l] = o3 + v3;
+          } else {
+            my[j0 * 32 + l] += v0;
+            my[j1 * 32 + l] += v1;
+            my[j2 * 32 + l] += v2;
+            my[j3 * 32 + l] += v3;
+          }
+        }
+        for (; i < nrows; i += step) {
+          const int j = S.lab[i];
+          if (j < k && on)
+            my[j * 32 + l] += feat ? S.prow[i * NP + fc] - S.cen[j * NP + fc] : 1.f;
+        }
       }
+      __syncthreads();
+      phase_tick(a.stats, 9, &tsub);
+      for (int q = threadIdx.x; q < k * 32; q += blockDim.x) {
+        const int j = q >> 5, f = fs + (q & 31);
+        if (f < n) {
+          float sum = 0.f;
+          for (int u = 0; u < L.wu; ++u) sum += S.sw[u * k * 32 + q];
+          a.part_sum[((size_t)j * npad + f) * G + b] = sum;
+        }
+      }
+      if (fs == 0)
+        for (int j = threadIdx.x; j < k; j += blockDim.x) {
+          int c = 0;
+          if (count_lane)
+            for (int u = 0; u < L.wu; ++u) c += (int)S.sw[u * k * 32 + j * 32 + 31];
+          else
+            for (int u = 0; u < nw; ++u) c += S.cw[u * k + j];
+          a.part_cnt[(size_t)j * G + b] = c;
+        }
+      __syncthreads();
+      phase_tick(a.stats, 10, &tsub);
+    }
+  } else {
+    const int ng = L.wu;
+    for (int q = threadIdx.x; q < ng * k * npad; q += blockDim.x) S.sw[q] = 0.f;
+    for (int q = threadIdx.x; q < ng * k; q += blockDim.x) S.cw[q] = 0;
+    for (int t0 = 0; t0 < nrows; t0 += 64) {
+      const int rows = min(64, nrows - t0);
+      stage_tile(S.stage, a.P + (size_t)(r0 + t0) * npad, npad, rows, n, npad, true, true);
+      int j;
+      float d;
+      if (nearest_tile(S.stage, S.cen, S.live, k, a.kpad, n, rows, j, d)) {
+        const int i = t0 + (threadIdx.x >> 5) * 8 + (threadIdx.x & 31);
+        S.lab[i] = j;
+        S.dmin[i] = d;
+      }
+      __syncthreads();
+      for (int slot = threadIdx.x; slot < ng * npad; slot += blockDim.x) {
+        const int g = slot / npad, f = slot - g * npad;
+        if (f >= n) continue;
+        float* acc = S.sw + g * k * npad;
+        const int sz = swz(f);
+        for (int r = g; r < rows; r += ng) {
+          const int jr = S.lab[t0 + r];
+          if (jr >= k) continue;
+          acc[jr * npad + f] += S.stage[f * 64 + (r ^ sz)] - S.crow[jr * npad + f];
+          if (f == 0) S.cw[g * k + jr] += 1;
+        }
+      }
+      __syncthreads();
+    }
+    for (int q = threadIdx.x; q < k * npad; q += blockDim.x) {
+      const int jj = q / npad, f = q - jj * npad;
+      if (f < n) {
+        float sum = 0.f;
+        for (int g = 0; g < ng; ++g) sum += S.sw[g * k * npad + q];
+        a.part_sum[((size_t)jj * npad + f) * G + b] = sum;
+      }
+    }
+    for (int jj = threadIdx.x; jj < k; jj += blockDim.x) {
+      int c = 0;
+      for (int g = 0; g < ng; ++g) c += S.cw[g * k + jj];
+      a.part_cnt[(size_t)jj * G + b] = c;
+    }
     __syncthreads();
   }
 }
@@ -335,7 +602,8 @@ __device__ __forceinline__ int block_excl_scan(int v, int* buf, int* total) {
   if (l == 31) buf[w] = x;
   __syncthreads();
   int before = 0, all = 0;
-  for (int i = 0; i < kWarps; ++i) {
+  const int nw = blockDim.x >> 5;
+  for (int i = 0; i < nw; ++i) {
     if (i < w) before += buf[i];
     all += buf[i];
   }
@@ -344,119 +612,61 @@ __device__ __forceinline__ int block_excl_scan(int v, int* buf, int* total) {
 }
 
 // ------------------------------------------------------------------ phases
-__device__ __forceinline__ uint32_t sample_word(const ChunkArgs& a, long long w,
-                                                bool complement) {
-  const uint32_t raw = __ldcg(a.bitmap + w);
-  if (!complement) return raw;
-  uint32_t v = ~raw;
-  const long long lo = w * 32;
-  if (lo + 32 > a.m) v &= (a.m - lo >= 32) ? 0xffffffffu : ((1u << (a.m - lo)) - 1u);
-  return v;
-}
-
-// Sample draw: rounds of Philox draws deduplicated in the bitmap, then a
-// fixed-order compaction of the set (or unset) bits into sorted indices.
-__device__ bool phase_draw(const ChunkArgs& a, const Smem& S, GridBarrier& gb) {
-  const bool complement = 2 * (long long)a.s > a.m;
-  const uint32_t target = complement ? (uint32_t)(a.m - a.s) : (uint32_t)a.s;
-  int* ired = reinterpret_cast<int*>(S.red);
-  const unsigned long long gtid = (unsigned long long)blockIdx.x * kThreads + threadIdx.x;
-  const unsigned long long gstride = (unsigned long long)gridDim.x * kThreads;
-  uint32_t have = 0;
-  if (target > 0) {
-    for (int r = 0; r < kRoundSlots; ++r) {
-      const uint32_t need = target - have;
-      if (need == 0) break;
-      int mine = 0;
-      for (unsigned long long i = gtid; i < need; i += gstride) {
-        const uint64_t w = philox_word(a.seed, (uint64_t)a.t, 0, (uint64_t)r, i);
-        const uint64_t v = __umul64hi(w, (uint64_t)a.m);
-        const uint32_t bit = 1u << (v & 31);
-        const uint32_t old = atomicOr(a.bitmap + (v >> 5), bit);
-        mine += (old & bit) ? 0 : 1;
+// P[i] = X[idx[i]] for own rows (zero padding to npad).  The row-in-register
+// path gathers one row per thread with independent vector loads and also
+// keeps the row in the CTA's resident copy; the tiled path copies elements,
+// eight independent loads in flight per thread.
+template <int NP, bool GENERIC>
+__device__ void phase_gather(const ChunkArgs& a, const Smem& S, int r0, int nrows) {
+  const int npad = a.npad, n = a.n;
+  if constexpr (!GENERIC) {
+    const bool vec4 = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.X) & 15) == 0);
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+      const long long row = __ldcg(a.idx + r0 + i);
+      float p[NP];
+      load_row_np<NP>(p, a.X + (size_t)row * n, n, vec4, false);
+      float4* dst = reinterpret_cast<float4*>(a.P + (size_t)(r0 + i) * NP);
+      float4* res = reinterpret_cast<float4*>(S.prow + i * NP);
+#pragma unroll
+      for (int q = 0; q < NP / 4; ++q) {
+        const float4 v = make_float4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
+        dst[q] = v;
+        res[q] = v;
       }
-      const int blk = block_sum_i32(mine, ired);
-      if (threadIdx.x == 0 && blk) atomicAdd(&a.ctl->round_cnt[r], (uint32_t)blk);
-      if (!gb.sync()) return false;
-      have += __ldcg(&a.ctl->round_cnt[r]);
     }
-    if (have < target) {
-      // Rounds exhausted (never in practice): the smallest absent values
-      // complete the set.
-      if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const long long W = (a.m + 31) / 32;
-        for (long long w = 0; w < W && have < target; ++w) {
-          uint32_t word = a.bitmap[w];
-          for (int bpos = 0; bpos < 32 && have < target; ++bpos) {
-            if (w * 32 + bpos >= a.m) break;
-            if (!(word & (1u << bpos))) { word |= 1u << bpos; ++have; }
-          }
-          a.bitmap[w] = word;
+  } else {
+    const int total = nrows * npad;
+    for (int e0 = threadIdx.x; e0 < total; e0 += 8 * blockDim.x) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x;
+        v[u] = 0.f;
+        if (e < total) {
+          const int i = e / npad, f = e - i * npad;
+          if (f < n) v[u] = __ldg(a.X + (size_t)__ldcg(a.idx + r0 + i) * n + f);
         }
       }
-      if (!gb.sync()) return false;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < total) a.P[(size_t)r0 * npad + e] = v[u];
+      }
     }
-  }
-  // compaction: CTA b owns words [w0, w1)
-  const long long W = (a.m + 31) / 32;
-  const long long wb = (W + gridDim.x - 1) / gridDim.x;
-  const long long w0 = min(W, (long long)blockIdx.x * wb), w1 = min(W, w0 + wb);
-  int cnt = 0;
-  for (long long w = w0 + threadIdx.x; w < w1; w += kThreads)
-    cnt += __popc(sample_word(a, w, complement));
-  cnt = block_sum_i32(cnt, ired);
-  if (threadIdx.x == 0) a.blk_cnt[blockIdx.x] = cnt;
-  if (!gb.sync()) return false;
-  int base = 0;
-  for (int q = threadIdx.x; q < (int)blockIdx.x; q += kThreads) base += __ldcg(a.blk_cnt + q);
-  base = block_sum_i32(base, ired);
-  for (long long t0 = w0; t0 < w1; t0 += kThreads) {
-    const long long w = t0 + threadIdx.x;
-    uint32_t bits = w < w1 ? sample_word(a, w, complement) : 0u;
-    int tile_total;
-    int pos = base + block_excl_scan(__popc(bits), ired + 16, &tile_total);
-    while (bits) {
-      const int bp = __ffs(bits) - 1;
-      if (pos < a.s) a.idx[pos] = (int32_t)(w * 32 + bp);   // bound: stray bits
-      ++pos;
-      bits &= bits - 1;
-    }
-    base += tile_total;
   }
   __syncthreads();
-  for (long long w = w0 + threadIdx.x; w < w1; w += kThreads) a.bitmap[w] = 0u;
-  if (!gb.sync()) return false;
-  if (blockIdx.x == 0)
-    for (int r = threadIdx.x; r < kRoundSlots; r += kThreads) a.ctl->round_cnt[r] = 0u;
-  return true;
-}
-
-// P[i] = X[idx[i]] for own rows (zero padding to npad).
-__device__ void phase_gather(const ChunkArgs& a, int r0, int nrows) {
-  const int npad = a.npad, n = a.n;
-  for (int e = threadIdx.x; e < nrows * npad; e += kThreads) {
-    const int i = e / npad, f = e - i * npad;
-    float v = 0.f;
-    if (f < n) {
-      const long long row = __ldcg(a.idx + r0 + i);
-      v = __ldg(a.X + (size_t)row * n + f);
-    }
-    a.P[(size_t)(r0 + i) * npad + f] = v;
-  }
 }
 
 template <bool GENERIC>
 __device__ __forceinline__ void set_centroid_row(const Smem& S, const float* src,
                                                  int j, int npad, int kpad) {
-  for (int f = threadIdx.x; f < npad; f += kThreads) {
-    if (GENERIC) S.cen[f * kpad + j] = src[f];
-    else S.cen[j * npad + f] = src[f];
-  }
+  for (int f = threadIdx.x; f < npad; f += blockDim.x)
+    put_centroid<GENERIC>(S.cen, S.crow, j, f, src[f], npad, kpad);
 }
 
 __device__ __forceinline__ void load_cand_row(const ChunkArgs& a, const Smem& S,
                                               int c, int row) {
-  for (int f = threadIdx.x; f < a.npad; f += kThreads)
+  for (int f = threadIdx.x; f < a.npad; f += blockDim.x)
     S.cand[c * a.npad + f] = __ldcg(a.P + (size_t)row * a.npad + f);
 }
 
@@ -466,8 +676,7 @@ __device__ bool phase_kpp(const ChunkArgs& a, const Smem& S, GridBarrier& gb,
                           int r0, int nrows, long long* nd_out) {
   const int k = a.k, G = gridDim.x, b = blockIdx.x;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  int nlive = 0;
-  for (int j = 0; j < k; ++j) nlive += S.live[j];
+  const int nlive = S.lidx[k];
   if (nlive == k) return true;
   long long nd = 0;
   __shared__ double s_tgt[kMaxTrials], s_excl[kMaxTrials], s_total;
@@ -484,11 +693,11 @@ __device__ bool phase_kpp(const ChunkArgs& a, const Smem& S, GridBarrier& gb,
     set_centroid_row<GENERIC>(S, S.cand, 0, a.npad, a.kpad);
     if (threadIdx.x == 0) S.live[0] = 1;
     if (b == 0) {
-      for (int f = threadIdx.x; f < a.npad; f += kThreads) a.C[f] = S.cand[f];
+      for (int f = threadIdx.x; f < a.npad; f += blockDim.x) a.C[f] = S.cand[f];
       if (threadIdx.x == 0) a.mask[0] = 1;
     }
-    own_rows_to_cands(a, S, r0, nrows, 1);
-    for (int i = threadIdx.x; i < nrows; i += kThreads) S.dmin[i] = S.dc[i];
+    own_rows_to_cands<NP, GENERIC>(a, S, r0, nrows, 1);
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) S.dmin[i] = S.dc[i];
     __syncthreads();
     nd += a.s;
   }
@@ -600,10 +809,10 @@ __device__ bool phase_kpp(const ChunkArgs& a, const Smem& S, GridBarrier& gb,
     // (C) potentials of the candidates
     for (int t = 0; t < a.trials; ++t) load_cand_row(a, S, t, __ldcg(a.ctl->cand + t));
     __syncthreads();
-    own_rows_to_cands(a, S, r0, nrows, a.trials);
+    own_rows_to_cands<NP, GENERIC>(a, S, r0, nrows, a.trials);
     for (int t = 0; t < a.trials; ++t) {
       double v = 0.0;
-      for (int i = threadIdx.x; i < nrows; i += kThreads)
+      for (int i = threadIdx.x; i < nrows; i += blockDim.x)
         v += (double)fminf(S.dmin[i], S.dc[t * R + i]);
       v = block_sum_f64(v, S.red);
       if (threadIdx.x == 0) a.part_f[(size_t)t * G + b] = v;
@@ -612,11 +821,21 @@ __device__ bool phase_kpp(const ChunkArgs& a, const Smem& S, GridBarrier& gb,
     if (!gb.sync()) return false;
     // (D) choose the candidate with the lowest potential
     if (w == 0) {
+      double v[kMaxTrials];
+#pragma unroll
+      for (int t = 0; t < kMaxTrials; ++t) v[t] = 0.0;
+      for (int u = l; u < G; u += 32)
+#pragma unroll
+        for (int t = 0; t < kMaxTrials; ++t)
+          if (t < a.trials) v[t] += __ldcg(a.part_f + (size_t)t * G + u);
       int best = 0;
       double bestv = 0.0;
-      for (int t = 0; t < a.trials; ++t) {
-        const double phi = warp_sum_array_f64(a.part_f + (size_t)t * G, G);
-        if (t == 0 || phi < bestv) { bestv = phi; best = t; }
+#pragma unroll
+      for (int t = 0; t < kMaxTrials; ++t) {
+        if (t < a.trials) {
+          const double phi = warp_sum_f64(v[t]);
+          if (t == 0 || phi < bestv) { bestv = phi; best = t; }
+        }
       }
       if (l == 0) s_best = best;
     }
@@ -625,14 +844,15 @@ __device__ bool phase_kpp(const ChunkArgs& a, const Smem& S, GridBarrier& gb,
     set_centroid_row<GENERIC>(S, S.cand + bt * a.npad, j, a.npad, a.kpad);
     if (threadIdx.x == 0) S.live[j] = 1;
     if (b == 0) {
-      for (int f = threadIdx.x; f < a.npad; f += kThreads)
+      for (int f = threadIdx.x; f < a.npad; f += blockDim.x)
         a.C[(size_t)j * a.npad + f] = S.cand[bt * a.npad + f];
       if (threadIdx.x == 0) a.mask[j] = 1;
     }
-    for (int i = threadIdx.x; i < nrows; i += kThreads)
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x)
       S.dmin[i] = fminf(S.dmin[i], S.dc[bt * R + i]);
     __syncthreads();
   }
+  build_live_list(S.live, S.lidx, k);
   // make the reseeded rows of the global working C visible before Lloyd
   if (!gb.sync()) return false;
   *nd_out += nd;
@@ -644,7 +864,7 @@ template <int NP, bool GENERIC>
 __device__ bool phase_lloyd(const ChunkArgs& a, const Smem& S,
                             const ChunkSmem& L, GridBarrier& gb, int r0,
                             int nrows, long long* nd_out, double* f_out,
-                            int* it_out) {
+                            int* it_out, uint64_t* tclk) {
   const int k = a.k, n = a.n, npad = a.npad, G = gridDim.x, b = blockIdx.x;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   double* FPART = a.part_f + (size_t)(kMaxTrials + 1) * G;
@@ -653,14 +873,14 @@ __device__ bool phase_lloyd(const ChunkArgs& a, const Smem& S,
   int it = 0;
   long long nd = 0;
   while (true) {
-    int nlive = 0;
-    for (int j = 0; j < k; ++j) nlive += S.live[j];
-    assign_own_rows<NP, GENERIC>(a, S, r0, nrows);
+    const int nlive = S.lidx[k];
+    lloyd_own_rows<NP, GENERIC>(a, S, L, r0, nrows, G);
     const double fp = own_dmin_sum(S, nrows);
-    update_partials<GENERIC>(a, S, L, r0, nrows, G);
     if (threadIdx.x == 0) FPART[b] = fp;
     nd += (long long)a.s * nlive;
+    phase_tick(a.stats, 3, tclk);
     if (!gb.sync()) return false;
+    phase_tick(a.stats, 4, tclk);
     if (w == 0) {
       const double t = warp_sum_array_f64(FPART, G);
       if (l == 0) s_f = t;
@@ -669,39 +889,43 @@ __device__ bool phase_lloyd(const ChunkArgs& a, const Smem& S,
     f = s_f;
     const bool stop = (f == 0.0) || (it > 0 && f_prev - f <= a.tol * f_prev) ||
                       (it == a.max_iter);
-    const int gw = b * kWarps + w, nw = G * kWarps;
+    const int nwb = blockDim.x >> 5;
+    const int gw = b * nwb + w, nw = G * nwb;
     for (int q = gw; q < k * n; q += nw) {
       const int j = q / n, ff = q - j * n;
       if (!S.live[j]) continue;
       int cnt = 0;
-      for (int u = l; u < G; u += 32) cnt += __ldcg(a.part_cnt + (size_t)j * G + u);
+      float sum = 0.f;
+      const float* ps = a.part_sum + ((size_t)j * npad + ff) * G;
+      for (int u = l; u < G; u += 32) {
+        cnt += __ldcg(a.part_cnt + (size_t)j * G + u);
+        sum += __ldcg(ps + u);
+      }
       cnt = warp_sum_i32(cnt);
       if (cnt == 0) {
         if (ff == 0 && l == 0) a.mask[j] = 0;
         continue;
       }
       if (stop) continue;
-      float sum = 0.f;
-      const float* ps = a.part_sum + ((size_t)j * npad + ff) * G;
-      for (int u = l; u < G; u += 32) sum += __ldcg(ps + u);
       sum = warp_sum_f32(sum);
       if (l == 0) {
-        const float c = GENERIC ? S.cen[ff * a.kpad + j] : S.cen[j * npad + ff];
+        const float c = GENERIC ? S.crow[j * npad + ff] : S.cen[j * npad + ff];
         a.C[(size_t)j * npad + ff] = c + sum / (float)cnt;
       }
     }
+    phase_tick(a.stats, 5, tclk);
     if (!gb.sync()) return false;
-    for (int j = threadIdx.x; j < k; j += kThreads)
+    for (int j = threadIdx.x; j < k; j += blockDim.x)
       S.live[j] = __ldcg(reinterpret_cast<const unsigned char*>(a.mask) + j) != 0;
+    build_live_list(S.live, S.lidx, k);
     if (!stop) {
-      for (int q = threadIdx.x; q < k * npad; q += kThreads) {
+      for (int q = threadIdx.x; q < k * npad; q += blockDim.x) {
         const int j = q / npad, ff = q - j * npad;
-        const float v = __ldcg(a.C + q);
-        if (GENERIC) S.cen[ff * a.kpad + j] = v;
-        else S.cen[q] = v;
+        put_centroid<GENERIC>(S.cen, S.crow, j, ff, __ldcg(a.C + q), npad, a.kpad);
       }
     }
     __syncthreads();
+    phase_tick(a.stats, 6, tclk);
     if (stop) break;
     f_prev = f;
     ++it;
@@ -714,7 +938,7 @@ __device__ bool phase_lloyd(const ChunkArgs& a, const Smem& S,
 
 // ------------------------------------------------------------ chunk kernel
 template <int NP, bool GENERIC>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(GENERIC ? 256 : 384)
 chunk_kernel(ChunkArgs a) {
   extern __shared__ __align__(16) char smem_raw[];
   const int G = gridDim.x;
@@ -728,26 +952,38 @@ chunk_kernel(ChunkArgs a) {
   int it = 0;
   bool ok = true;
 
+  if (threadIdx.x < kNumPhaseTimers) phase_slots()[threadIdx.x] = 0ull;
+  uint64_t tclk = global_timer_ns();
   const bool full = (a.phases & kPhaseKeep) != 0;
   if (a.phases & (kPhaseKpp | kPhaseLloyd)) {
     // C' <- C (Alg. 1): the working copy starts from the incumbent.
     const float* src = full ? a.Cinc : a.C;
     const uint8_t* msrc = full ? a.mask_inc : a.mask;
-    load_centroids<GENERIC>(S.cen, S.live, src, a.npad, msrc, a.k, a.n, a.npad,
-                            a.kpad, true);
+    load_centroids<GENERIC>(S.cen, S.crow, S.live, src, a.npad, msrc, a.k, a.n,
+                            a.npad, a.kpad, true);
+    build_live_list(S.live, S.lidx, a.k);
     if (full && blockIdx.x == 0) {
-      for (int q = threadIdx.x; q < a.k * a.npad; q += kThreads) a.C[q] = __ldcg(a.Cinc + q);
-      for (int j = threadIdx.x; j < a.k; j += kThreads) a.mask[j] = S.live[j];
+      for (int q = threadIdx.x; q < a.k * a.npad; q += blockDim.x) a.C[q] = __ldcg(a.Cinc + q);
+      for (int j = threadIdx.x; j < a.k; j += blockDim.x) a.mask[j] = S.live[j];
     }
   }
-  if (ok && (a.phases & kPhaseDraw)) ok = phase_draw(a, S, gb);
+  phase_tick(a.stats, 0, &tclk);
   if (ok && (a.phases & kPhaseGather)) {
-    phase_gather(a, r0, nrows);
-    ok = gb.sync();
+    phase_gather<NP, GENERIC>(a, S, r0, nrows);
+    // Only K-means++ reads sample rows gathered by other CTAs; Lloyd reads
+    // its own rows, so without a reseed no grid barrier is needed here.
+    const bool reseed = (a.phases & kPhaseKpp) && S.lidx[a.k] < a.k;
+    if (reseed) ok = gb.sync();
+    phase_tick(a.stats, 1, &tclk);
+  } else if (a.phases & (kPhaseKpp | kPhaseLloyd)) {
+    if constexpr (!GENERIC) stage_own_rows<NP>(a, S, r0, nrows);   // P written by the host
   }
-  if (ok && (a.phases & kPhaseKpp)) ok = phase_kpp<NP, GENERIC>(a, S, gb, r0, nrows, &nd);
+  if (ok && (a.phases & kPhaseKpp)) {
+    ok = phase_kpp<NP, GENERIC>(a, S, gb, r0, nrows, &nd);
+    phase_tick(a.stats, 2, &tclk);
+  }
   if (ok && (a.phases & kPhaseLloyd))
-    ok = phase_lloyd<NP, GENERIC>(a, S, L, gb, r0, nrows, &nd, &f, &it);
+    ok = phase_lloyd<NP, GENERIC>(a, S, L, gb, r0, nrows, &nd, &f, &it, &tclk);
   if (!ok) return;
   if (blockIdx.x == 0) {
     __shared__ int s_acc;
@@ -760,8 +996,8 @@ chunk_kernel(ChunkArgs a) {
     }
     __syncthreads();
     if (s_acc) {
-      for (int q = threadIdx.x; q < a.k * a.npad; q += kThreads) a.Cinc[q] = __ldcg(a.C + q);
-      for (int j = threadIdx.x; j < a.k; j += kThreads)
+      for (int q = threadIdx.x; q < a.k * a.npad; q += blockDim.x) a.Cinc[q] = __ldcg(a.C + q);
+      for (int j = threadIdx.x; j < a.k; j += blockDim.x)
         a.mask_inc[j] = __ldcg(reinterpret_cast<const unsigned char*>(a.mask) + j);
     }
     if (threadIdx.x == 0) {
@@ -773,6 +1009,9 @@ chunk_kernel(ChunkArgs a) {
       }
       a.stats->n_d += nd;
     }
+    phase_tick(a.stats, 7, &tclk);
+    if (threadIdx.x == 0)
+      for (int i = 0; i < kNumPhaseTimers; ++i) a.stats->phase_ns[i] += phase_slots()[i];
   }
   (void)G;
 }
@@ -804,19 +1043,23 @@ __global__ void __launch_bounds__(kThreads)
 assign_np_kernel(AssignArgs a) {
   extern __shared__ __align__(16) char smem_raw[];
   float* cen = reinterpret_cast<float*>(smem_raw);
-  int* live = reinterpret_cast<int*>(smem_raw + align_up(a.k * NP * 4, 16));
-  double* red = reinterpret_cast<double*>(smem_raw + align_up(a.k * NP * 4, 16) +
-                                          align_up(a.k * 4, 16));
-  load_centroids<false>(cen, live, a.C, a.cstride, a.mask, a.k, a.n, NP, 0, false);
+  int o = align_up(a.k * NP * 4, 16);
+  int* live = reinterpret_cast<int*>(smem_raw + o);
+  o += align_up(a.k * 4, 16);
+  int* lidx = reinterpret_cast<int*>(smem_raw + o);
+  o += align_up((a.k + 1) * 4, 16);
+  double* red = reinterpret_cast<double*>(smem_raw + o);
+  load_centroids<false>(cen, nullptr, live, a.C, a.cstride, a.mask, a.k, a.n, NP, 0, false);
+  build_live_list(live, lidx, a.k);
   const bool vec4 = (a.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.X) & 15) == 0);
   double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < a.m;
-       i += (long long)gridDim.x * kThreads) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.m;
+       i += (long long)gridDim.x * blockDim.x) {
     float p[NP];
     load_row_np<NP>(p, a.X + (size_t)i * a.n, a.n, vec4, false);
     int j;
     float d;
-    nearest_np<NP>(p, cen, live, a.k, j, d);
+    nearest_np<NP>(p, cen, lidx, a.k, j, d);
     if (a.labels) a.labels[i] = j;
     if (a.dmin) a.dmin[i] = d;
     acc += (double)d;
@@ -834,7 +1077,8 @@ assign_generic_kernel(AssignArgs a) {
   float* stage = reinterpret_cast<float*>(smem_raw + o);
   o += align_up(64 * a.npad * 4, 16);
   double* red = reinterpret_cast<double*>(smem_raw + o);
-  load_centroids<true>(cenT, live, a.C, a.cstride, a.mask, a.k, a.n, a.npad, a.kpad, false);
+  load_centroids<true, false>(cenT, nullptr, live, a.C, a.cstride, a.mask, a.k, a.n,
+                              a.npad, a.kpad, false);
   const bool vec4 = (a.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.X) & 15) == 0);
   double acc = 0.0;
   const long long tiles = (a.m + 63) / 64;
@@ -865,8 +1109,8 @@ static cudaError_t launch_chunk_t(const ChunkArgs& a, int grid, size_t smem,
   if (e != cudaSuccess) return e;
   ChunkArgs copy = a;
   void* args[] = {&copy};
-  return cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(kThreads),
-                                     args, smem, st);
+  return cudaLaunchCooperativeKernel((const void*)fn, dim3(grid),
+                                     dim3(chunk_threads(GENERIC)), args, smem, st);
 }
 
 template <int NP, bool GENERIC>
@@ -876,7 +1120,8 @@ static int chunk_max_grid_t(size_t smem) {
       cudaSuccess)
     return 0;
   int per_sm = 0, dev = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, chunk_threads(GENERIC),
+                                                    smem) != cudaSuccess)
     return 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -890,6 +1135,7 @@ cudaError_t launch_chunk(const ChunkArgs& a, int grid, bool generic, int np,
     case 4: return launch_chunk_t<4, false>(a, grid, smem, st);
     case 8: return launch_chunk_t<8, false>(a, grid, smem, st);
     case 16: return launch_chunk_t<16, false>(a, grid, smem, st);
+    case 28: return launch_chunk_t<28, false>(a, grid, smem, st);
     default: return launch_chunk_t<32, false>(a, grid, smem, st);
   }
 }
@@ -900,12 +1146,14 @@ int chunk_max_grid(bool generic, int np, size_t smem) {
     case 4: return chunk_max_grid_t<4, false>(smem);
     case 8: return chunk_max_grid_t<8, false>(smem);
     case 16: return chunk_max_grid_t<16, false>(smem);
+    case 28: return chunk_max_grid_t<28, false>(smem);
     default: return chunk_max_grid_t<32, false>(smem);
   }
 }
 
 size_t assign_smem(int npad, int k, int kpad, bool generic) {
-  if (!generic) return align_up(k * npad * 4, 16) + align_up(k * 4, 16) + 64 * 8;
+  if (!generic)
+    return align_up(k * npad * 4, 16) + align_up(k * 4, 16) + align_up((k + 1) * 4, 16) + 64 * 8;
   return align_up(npad * kpad * 4, 16) + align_up(k * 4, 16) +
          align_up(64 * npad * 4, 16) + 64 * 8;
 }
@@ -929,6 +1177,7 @@ int assign_max_grid(bool generic, int np, size_t smem) {
     case 4: return max_grid_of(assign_np_kernel<4>, smem);
     case 8: return max_grid_of(assign_np_kernel<8>, smem);
     case 16: return max_grid_of(assign_np_kernel<16>, smem);
+    case 28: return max_grid_of(assign_np_kernel<28>, smem);
     default: return max_grid_of(assign_np_kernel<32>, smem);
   }
 }
@@ -952,6 +1201,10 @@ cudaError_t launch_assign(const AssignArgs& a, int grid, bool generic, int np,
       case 16:
         cudaFuncSetAttribute(assign_np_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         assign_np_kernel<16><<<grid, kThreads, smem, st>>>(a);
+        break;
+      case 28:
+        cudaFuncSetAttribute(assign_np_kernel<28>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        assign_np_kernel<28><<<grid, kThreads, smem, st>>>(a);
         break;
       default:
         cudaFuncSetAttribute(assign_np_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -75,7 +75,7 @@ extern "C" bm_status bm_assign_rows_noalloc(const float* X_dev, int64_t m,
   if (live == 0) return BM_EINVAL;
   // launch shape: the same kernel family and grid rule as bm_assign_rows
   const bool generic = n > kNpMax;
-  const int np = n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32;
+  const int np = np_width(n);
   const int npad = generic ? align_up(n, 4) : np;
   const int kpad = generic ? align_up(k, 32) : 0;
   const size_t smem = assign_smem(npad, k, kpad, generic);

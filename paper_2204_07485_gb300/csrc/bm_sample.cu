@@ -1,0 +1,127 @@
+// Sample plan: the uniform samples of a batch of chunks, drawn in one launch.
+//
+// Alg. 1 draws a fresh uniform sample of s rows for every chunk (Sec. 3.1,
+// Eq. 2; Sec. 3.5).  The draws do not depend on the incumbent, so a batch of
+// B chunks is drawn ahead by one launch with one CTA per chunk, all chunks in
+// parallel, off the per-chunk critical path.  Per chunk t:
+//   round r draws (target - |S|) Philox words (purpose 0, counter
+//   (i / 4, r, t, 0)), maps each to a row by the high word of w * m, and adds
+//   it to S with atomicOr on the chunk's bitmap; a value is new when its bit
+//   was clear.  Rounds continue until |S| = target (64 rounds at most; the
+//   smallest absent rows complete S after that, which never happens in
+//   practice for target <= m / 2).  target = s, or m - s rows to leave out
+//   when 2s > m.  A fixed-order scan of the bitmap then writes the sample's
+//   rows in ascending order and clears the bitmap for the next use.
+// Nothing here waits on another CTA.
+#include <cuda_runtime.h>
+
+#include "bm_device.cuh"
+#include "bm_internal.h"
+
+namespace bm {
+
+constexpr int kDrawThreads = 512;
+constexpr int kWordsPerThread = 8;
+
+__device__ __forceinline__ int block_excl_scan_i32(int v, int* buf, int* total) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (l >= o) x += y;
+  }
+  __syncthreads();
+  if (l == 31) buf[w] = x;
+  __syncthreads();
+  int before = 0, all = 0;
+  const int nw = blockDim.x >> 5;
+  for (int i = 0; i < nw; ++i) {
+    if (i < w) before += buf[i];
+    all += buf[i];
+  }
+  *total = all;
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kDrawThreads) draw_kernel(DrawArgs a) {
+  __shared__ int red[32];
+  __shared__ int scan[32];
+  const long long W = (a.m + 31) / 32;
+  const long long t = a.t0 + blockIdx.x;
+  uint32_t* bm = a.bitmaps + (size_t)blockIdx.x * W;
+  int32_t* out = a.idx + (size_t)blockIdx.x * a.s;
+  const bool complement = 2 * (long long)a.s > a.m;
+  const uint32_t target = complement ? (uint32_t)(a.m - a.s) : (uint32_t)a.s;
+
+  uint32_t have = 0;
+  for (int r = 0; r < kRoundSlots && have < target; ++r) {
+    const uint32_t need = target - have;
+    int got = 0;
+    for (uint32_t i = threadIdx.x; i < need; i += blockDim.x) {
+      const uint64_t w = philox_word(a.seed, (uint64_t)t, 0, (uint64_t)r, i);
+      const uint64_t v = __umul64hi(w, (uint64_t)a.m);
+      const uint32_t bit = 1u << (v & 31);
+      const uint32_t old = atomicOr(bm + (v >> 5), bit);
+      got += (old & bit) ? 0 : 1;
+    }
+    have += (uint32_t)block_sum_i32(got, red);
+  }
+  if (have < target && threadIdx.x == 0) {
+    for (long long w = 0; w < W && have < target; ++w) {
+      uint32_t word = __ldcg(bm + w);
+      for (int bpos = 0; bpos < 32 && have < target; ++bpos) {
+        if (w * 32 + bpos >= a.m) break;
+        if (!(word & (1u << bpos))) { word |= 1u << bpos; ++have; }
+      }
+      bm[w] = word;
+    }
+  }
+  __syncthreads();
+
+  // compaction: kWordsPerThread consecutive words per thread per tile
+  int base = 0;
+  const long long tile = (long long)blockDim.x * kWordsPerThread;
+  for (long long t0 = 0; t0 < W; t0 += tile) {
+    const long long wb = t0 + (long long)threadIdx.x * kWordsPerThread;
+    uint32_t words[kWordsPerThread];
+    int c = 0;
+#pragma unroll
+    for (int u = 0; u < kWordsPerThread; ++u) {
+      const long long w = wb + u;
+      uint32_t v = 0u;
+      if (w < W) {
+        const uint32_t raw = __ldcg(bm + w);
+        v = raw;
+        if (complement) {
+          v = ~raw;
+          const long long lo = w * 32;
+          if (lo + 32 > a.m) v &= (1u << (a.m - lo)) - 1u;
+        }
+        bm[w] = 0u;
+      }
+      words[u] = v;
+      c += __popc(v);
+    }
+    int total;
+    int pos = base + block_excl_scan_i32(c, scan, &total);
+#pragma unroll
+    for (int u = 0; u < kWordsPerThread; ++u) {
+      uint32_t bits = words[u];
+      while (bits) {
+        const int bp = __ffs(bits) - 1;
+        if (pos < a.s) out[pos] = (int32_t)((wb + u) * 32 + bp);
+        ++pos;
+        bits &= bits - 1;
+      }
+    }
+    base += total;
+  }
+}
+
+cudaError_t launch_draw(const DrawArgs& a, int chunks, cudaStream_t st) {
+  draw_kernel<<<chunks, kDrawThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace bm
