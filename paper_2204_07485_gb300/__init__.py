@@ -22,7 +22,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 BM_OK, BM_EINVAL, BM_ENOMEM, BM_ECUDA, BM_ETIMEOUT, BM_EBUSY, BM_ECANCELLED, \
     BM_EUNSUPPORTED = range(8)
-BM_FP32, BM_BF16_RESCORE, BM_FP8_RESCORE = range(3)
+BM_FP32, BM_BF16_RESCORE, BM_FP8_RESCORE, BM_BF16X3_RESCORE = range(4)
 
 
 class bm_config(ctypes.Structure):
@@ -73,6 +73,8 @@ _SIGS = {
     "bm_lloyd": (_i32, [_vp, _i64, _i32, _i32, _vp, _vp, _i32, _dbl, _P(_dbl),
                         _P(_i32), _vp]),
     "bm_assign_rows": (_i32, [_vp, _i64, _i32, _vp, _vp, _i32, _vp, _vp, _P(_dbl), _vp]),
+    "bm_assign_rows_prec": (_i32, [_vp, _i64, _i32, _vp, _vp, _i32, _i32, _vp, _vp,
+                                   _P(_dbl), _P(ctypes.c_uint64), _vp]),
     "bm_assign_rows_noalloc": (_i32, [_vp, _i64, _i32, _vp, _vp, _i32, _vp, _vp,
                                       _P(_dbl), _vp]),
 }
@@ -225,6 +227,19 @@ def bm_assign_rows(X_dev, m, n, C_dev, mask_dev, k, labels_dev=None, dmin_dev=No
                                _ptr(dmin_dev), ctypes.byref(sse), _stream(stream)),
            "bm_assign_rows")
     return sse.value
+
+
+def bm_assign_rows_prec(X_dev, m, n, C_dev, mask_dev, k, precision, labels_dev=None,
+                        dmin_dev=None, stream=None):
+    """Returns (sse, rescored rows)."""
+    sse = _dbl()
+    resc = ctypes.c_uint64()
+    _check(_lib.bm_assign_rows_prec(_ptr(X_dev), int(m), int(n), _ptr(C_dev),
+                                    _ptr(mask_dev), int(k), int(precision),
+                                    _ptr(labels_dev), _ptr(dmin_dev), ctypes.byref(sse),
+                                    ctypes.byref(resc), _stream(stream)),
+           "bm_assign_rows_prec")
+    return sse.value, resc.value
 
 
 def bm_assign_rows_noalloc(X_dev, m, n, C_dev, mask_dev, k, labels_dev=None,

@@ -101,7 +101,9 @@ struct Workspace {
   Ctl* ctl = nullptr;
   Stats* stats = nullptr;
   double* apart = nullptr;   // assign per-CTA partials
+  int apart_cap = 0;
   double* asse = nullptr;    // assign result
+  unsigned long long* rescored = nullptr;  // tensor-core assign: rescored rows
   std::vector<void*> owned;
 
   template <typename T>
@@ -147,8 +149,10 @@ static bm_status ws_create(Workspace* w, long long m, int k, long long s,
   BM_TRY(w->alloc(&w->blk_cnt, (size_t)G));
   BM_TRY(w->alloc(&w->ctl, 1));
   BM_TRY(w->alloc(&w->stats, 1));
-  BM_TRY(w->alloc(&w->apart, (size_t)p.agrid));
+  w->apart_cap = std::max(p.agrid, 4096);
+  BM_TRY(w->alloc(&w->apart, (size_t)w->apart_cap));
   BM_TRY(w->alloc(&w->asse, 1));
+  BM_TRY(w->alloc(&w->rescored, 1));
 #undef BM_TRY
   cudaMemsetAsync(w->bitmap, 0, words * 4 * plan_cap, st);
   cudaMemsetAsync(w->C, 0, (size_t)k * p.npad * 4, st);
@@ -216,6 +220,7 @@ struct bm_ctx {
   long long plan_t0 = -1;   // first chunk held by the sample plan (-1: none)
   long long plan_n = 0;     // chunks held by the sample plan
   long long nd_assign = 0;  // distance evaluations of bm_assign calls
+  unsigned long long rescored = 0;  // rows rescored by the last tensor-core bm_assign
   std::mutex mu;
 };
 
@@ -254,7 +259,9 @@ bm_status bm_create(const bm_config* cfg, const float* X_dev, void* stream,
   if (cfg->kpp_trials < 1 || cfg->kpp_trials > kMaxTrials || cfg->max_iter < 0 ||
       !(cfg->tol >= 0.0))
     return BM_EINVAL;
-  if (cfg->precision != BM_FP32) return BM_EUNSUPPORTED;
+  if (cfg->precision != BM_FP32 && cfg->precision != BM_BF16_RESCORE &&
+      cfg->precision != BM_BF16X3_RESCORE)
+    return BM_EUNSUPPORTED;
   bm_ctx* c = new (std::nothrow) bm_ctx();
   if (!c) return BM_ENOMEM;
   c->cfg = *cfg;
@@ -383,6 +390,51 @@ static bm_status assign_impl(const float* X, long long m, int n, int k,
   return BM_OK;
 }
 
+// Tensor-core assignment (BF16 distances, exact FP32 rescoring).
+static bm_status assign_tc_impl(const float* X, long long m, int n, int k,
+                                const float* C, int cstride, const uint8_t* mask,
+                                int32_t* labels, float* dmin, Workspace& w,
+                                cudaStream_t st, double* sse_out,
+                                unsigned long long* rescored_out, int terms) {
+  if (k > kMaxK) return BM_EUNSUPPORTED;
+  int stages, kb, npad16, ncols, cf;
+  size_t smem = assign_tc_smem(n, k, terms, &stages, &kb, &npad16, &ncols, &cf);
+  if (smem > 227 * 1024 && terms == 3) {   // the split form does not fit: one term
+    terms = 1;
+    smem = assign_tc_smem(n, k, terms, &stages, &kb, &npad16, &ncols, &cf);
+  }
+  if (smem > 227 * 1024) return BM_EUNSUPPORTED;
+  int maxg = assign_tc_max_grid(smem);
+  if (maxg <= 0) return BM_EUNSUPPORTED;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  maxg = std::min(maxg, sms * std::max(1, 512 / ncols));   // TMEM columns per SM
+  const long long tiles = (m + 127) / 128;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(maxg, tiles));
+  if (grid > w.apart_cap) return BM_EUNSUPPORTED;
+  AssignTcArgs a{};
+  a.X = X; a.m = m; a.n = n; a.C = C; a.cstride = cstride; a.mask = mask; a.k = k;
+  a.labels = labels; a.dmin = dmin; a.part = w.apart; a.sse = w.asse;
+  a.ticket = &w.ctl->assign_ticket; a.rescored = w.rescored; a.status = &w.ctl->status;
+  a.kb = kb; a.npad16 = npad16; a.ncols = ncols; a.stages = stages;
+  a.use_bulk = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  a.terms = terms;
+  a.cf = cf;
+  if (cudaMemsetAsync(w.rescored, 0, sizeof(unsigned long long), st) != cudaSuccess) return BM_ECUDA;
+  if (launch_assign_tc(a, grid, smem, st) != cudaSuccess) return BM_ECUDA;
+  double sse = 0.0;
+  unsigned long long resc = 0;
+  if (cudaMemcpyAsync(&sse, w.asse, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&resc, w.rescored, sizeof(resc), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return BM_ECUDA;
+  const bm_status rc = check_status(w, st, 0);
+  if (rc != BM_OK) return rc;
+  if (sse_out) *sse_out = sse;
+  if (rescored_out) *rescored_out = resc;
+  return BM_OK;
+}
+
 static int count_live_host(const uint8_t* mask_dev, int k, cudaStream_t st) {
   std::vector<uint8_t> h(k);
   if (cudaMemcpyAsync(h.data(), mask_dev, k, cudaMemcpyDeviceToHost, st) != cudaSuccess) return -1;
@@ -398,9 +450,15 @@ bm_status bm_assign(bm_ctx* c, int32_t* labels_dev, double* sse_out) {
   const int live = count_live_host(c->ws.mask_inc, c->cfg.k, c->stream);
   if (live < 0) return BM_ECUDA;
   if (live == 0) return BM_EINVAL;   // no incumbent yet
-  bm_status st = assign_impl(c->X, c->cfg.m, c->cfg.n, c->cfg.k, c->plan, c->ws.Cinc,
-                             c->plan.npad, c->ws.mask_inc, labels_dev, nullptr, c->ws,
-                             c->stream, sse_out);
+  bm_status st;
+  if (c->cfg.precision == BM_BF16_RESCORE || c->cfg.precision == BM_BF16X3_RESCORE)
+    st = assign_tc_impl(c->X, c->cfg.m, c->cfg.n, c->cfg.k, c->ws.Cinc, c->plan.npad,
+                        c->ws.mask_inc, labels_dev, nullptr, c->ws, c->stream, sse_out,
+                        &c->rescored, c->cfg.precision == BM_BF16X3_RESCORE ? 3 : 1);
+  else
+    st = assign_impl(c->X, c->cfg.m, c->cfg.n, c->cfg.k, c->plan, c->ws.Cinc,
+                     c->plan.npad, c->ws.mask_inc, labels_dev, nullptr, c->ws,
+                     c->stream, sse_out);
   if (st == BM_OK) c->nd_assign += c->cfg.m * (long long)live;
   return st;
 }
@@ -623,6 +681,37 @@ bm_status bm_lloyd(const float* P_dev, int64_t s, int32_t n, int32_t k,
     if (f_out) *f_out = h.f_out;
     if (iters_out) *iters_out = h.iters_out;
   }
+  cudaStreamSynchronize(st);
+  w.release();
+  return rc;
+}
+
+bm_status bm_assign_rows_prec(const float* X_dev, int64_t m, int32_t n,
+                              const float* C_dev, const uint8_t* mask_dev,
+                              int32_t k, int32_t precision, int32_t* labels_dev,
+                              float* dmin_dev, double* sse_out,
+                              uint64_t* rescored_out, void* stream) {
+  if (precision == BM_FP32) {
+    if (rescored_out) *rescored_out = 0;
+    return bm_assign_rows(X_dev, m, n, C_dev, mask_dev, k, labels_dev, dmin_dev, sse_out,
+                          stream);
+  }
+  if (precision != BM_BF16_RESCORE && precision != BM_BF16X3_RESCORE) return BM_EUNSUPPORTED;
+  if (!X_dev || !C_dev || !mask_dev || m < 1 || n < 1 || k < 1 || m > 2147483647LL)
+    return BM_EINVAL;
+  std::lock_guard<std::mutex> g(g_ops_mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (count_live_host(mask_dev, k, st) <= 0) return BM_EINVAL;
+  Plan p;
+  bm_status rc = make_plan(n, k, std::max<long long>(k, 1), &p);
+  if (rc != BM_OK) return rc;
+  Workspace w;
+  rc = ws_create(&w, k, k, k, p, st);
+  if (rc != BM_OK) return rc;
+  unsigned long long resc = 0;
+  rc = assign_tc_impl(X_dev, m, n, k, C_dev, n, mask_dev, labels_dev, dmin_dev, w, st,
+                      sse_out, &resc, precision == BM_BF16X3_RESCORE ? 3 : 1);
+  if (rescored_out) *rescored_out = resc;
   cudaStreamSynchronize(st);
   w.release();
   return rc;

@@ -99,6 +99,30 @@ struct DrawArgs {
   uint32_t* bitmaps;   // [batch][ceil(m / 32)], all zero between launches
 };
 
+struct AssignTcArgs {
+  const float* X;      // m x n, row stride n
+  long long m;
+  int n;
+  const float* C;      // k x cstride
+  int cstride;
+  const uint8_t* mask; // k
+  int k;
+  int32_t* labels;     // m or null
+  float* dmin;         // m or null
+  double* part;        // [grid]
+  double* sse;         // device scalar
+  uint32_t* ticket;    // zero between launches
+  unsigned long long* rescored;  // rows that needed exact rechecks (added to)
+  int* status;         // BM_ETIMEOUT when a bounded wait gave up
+  int kb;              // K blocks of 64 BF16
+  int npad16;          // MMA N: k rounded up to 16 (<= 128)
+  int ncols;           // TMEM columns allocated
+  int stages;          // FP32 tile ring depth
+  int use_bulk;        // X is 16-byte aligned: bulk copies for full tiles
+  int terms;           // 1: BF16 products; 3: split BF16 (hi*hi + hi*lo + lo*hi)
+  int cf;              // FP32 centroid copy kept in shared memory
+};
+
 // Shared-memory layout of the chunk kernel (bytes), identical on host/device.
 struct ChunkSmem {
   int cen, crow, live, lidx, sw, cw, lab, dmin, dc, cand, stage, prow, red, total;
@@ -155,8 +179,12 @@ __host__ __device__ inline ChunkSmem chunk_smem(int npad, int k, int kpad, int R
   return L;
 }
 
-// Host-side launch helpers (bm_kernels.cu, bm_sample.cu).
+// Host-side launch helpers (bm_kernels.cu, bm_sample.cu, bm_tc.cu).
 cudaError_t launch_draw(const DrawArgs& a, int chunks, cudaStream_t st);
+size_t assign_tc_smem(int n, int k, int terms, int* stages, int* kb, int* npad16,
+                      int* ncols, int* cf);
+int assign_tc_max_grid(size_t smem);
+cudaError_t launch_assign_tc(const AssignTcArgs& a, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_chunk(const ChunkArgs& a, int grid, bool generic, int np,
                          size_t smem, cudaStream_t st);
 int chunk_max_grid(bool generic, int np, size_t smem);

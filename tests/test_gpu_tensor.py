@@ -1,0 +1,109 @@
+"""Tensor-core assignment (BF16 distances, exact FP32 rescoring) through the C ABI.
+
+The BF16 path must reproduce the FP32 arithmetic: for n <= 32 its labels and
+per-row distances equal bm_assign_rows' bit for bit (both finish with the
+same exact FP32 distance), and for every n they match the FP64 oracle under
+the parity rules of gpu_helpers.
+"""
+import numpy as np
+import pytest
+
+import bminputs as bi
+import oracle as o
+from gpu_helpers import OBJ_REL, dev, host, labels_match, rel, require_gpu, torch
+
+pytestmark = pytest.mark.gpu
+BF16 = 1
+BF16X3 = 3
+PRECS = [BF16, BF16X3]
+
+
+@pytest.fixture(scope="module")
+def bm():
+    require_gpu()
+    import paper_2204_07485_gb300 as lib
+    return lib
+
+
+def _case(m, n, k, seed, dead=True, scale=5.0):
+    X, _ = bi.mixtures.isotropic_blobs(m, n, max(k, 2), seed, box=scale)
+    rng = np.random.default_rng(seed)
+    C = (X[rng.choice(m, k, replace=False)]
+         + rng.normal(scale=0.1, size=(k, n))).astype(np.float32)
+    live = np.ones(k, np.uint8)
+    if dead and k > 3:
+        live[rng.choice(k, k // 4, replace=False)] = 0
+    return X, C, live
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("m,n,k,seed", [(10_000, 28, 25, 0), (4097, 2, 10, 1),
+                                        (3000, 1, 3, 2), (5000, 16, 128, 3),
+                                        (1000, 32, 1, 4), (20_011, 8, 50, 5)])
+def test_bf16_rescore_equals_fp32_path_bitwise(bm, m, n, k, seed, prec):
+    X, C, live = _case(m, n, k, seed)
+    Xd, Cd, md = dev(X), dev(C), dev(live)
+    lab32 = torch.empty(m, dtype=torch.int32, device="cuda:0")
+    d32 = torch.empty(m, dtype=torch.float32, device="cuda:0")
+    sse32 = bm.bm_assign_rows(Xd, m, n, Cd, md, k, lab32, d32)
+    lab = torch.empty_like(lab32)
+    dmin = torch.empty_like(d32)
+    sse, resc = bm.bm_assign_rows_prec(Xd, m, n, Cd, md, k, prec, lab, dmin)
+    assert torch.equal(lab, lab32)
+    assert torch.equal(dmin, d32)
+    assert rel(sse, sse32) <= 1e-12
+    assert 0 <= resc <= m
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("m,n,k,seed", [(6000, 128, 50, 0), (2050, 384, 20, 1),
+                                        (3001, 33, 100, 2), (1500, 64, 7, 3),
+                                        (777, 127, 64, 4), (129, 200, 9, 5)])
+def test_bf16_rescore_matches_oracle(bm, m, n, k, seed, prec):
+    X, C, live = _case(m, n, k, seed)
+    lab = torch.empty(m, dtype=torch.int32, device="cuda:0")
+    dmin = torch.empty(m, dtype=torch.float32, device="cuda:0")
+    sse, resc = bm.bm_assign_rows_prec(dev(X), m, n, dev(C), dev(live), k, prec, lab, dmin)
+    ref_lab, d1, d2 = o.nearest(X, C, live.astype(bool))
+    bad, _ = labels_match(host(lab), ref_lab, d1, d2)
+    assert bad == 0
+    np.testing.assert_allclose(host(dmin), d1, rtol=(n + 2) * 2.0 ** -24, atol=1e-30)
+    assert rel(sse, float(d1.sum())) <= OBJ_REL
+
+
+def test_bf16_unaligned_rows_use_plain_loads(bm):
+    # X starting 4 bytes past an aligned address: no bulk copies, same result
+    m, n, k = 3000, 28, 25
+    X, C, live = _case(m, n, k, 7)
+    buf = torch.zeros(m * n + 1, dtype=torch.float32, device="cuda:0")
+    buf[1:] = dev(X).reshape(-1)
+    Xd = buf[1:]
+    lab = torch.empty(m, dtype=torch.int32, device="cuda:0")
+    lab_ref = torch.empty_like(lab)
+    sse, _ = bm.bm_assign_rows_prec(Xd.data_ptr(), m, n, dev(C), dev(live), k, BF16, lab)
+    sse_ref = bm.bm_assign_rows(dev(X), m, n, dev(C), dev(live), k, lab_ref)
+    assert torch.equal(lab, lab_ref) and rel(sse, sse_ref) <= 1e-12
+
+
+def test_split_bf16_rescores_far_fewer_rows(bm):
+    m, n, k = 20_000, 28, 25
+    X, C, live = _case(m, n, k, 9)
+    _, r1 = bm.bm_assign_rows_prec(dev(X), m, n, dev(C), dev(live), k, BF16)
+    _, r3 = bm.bm_assign_rows_prec(dev(X), m, n, dev(C), dev(live), k, BF16X3)
+    assert r3 <= r1 and r3 < m // 100
+
+
+def test_bf16_close_centroids_force_rescoring(bm):
+    # centroids 1e-3 apart: BF16 cannot separate them, every row is rescored
+    m, n, k = 2048, 12, 4
+    rng = np.random.default_rng(11)
+    X = rng.normal(size=(m, n)).astype(np.float32) * 3
+    base = rng.normal(size=n).astype(np.float32)
+    C = np.stack([base + 1e-3 * j for j in range(k)]).astype(np.float32)
+    live = np.ones(k, np.uint8)
+    lab = torch.empty(m, dtype=torch.int32, device="cuda:0")
+    lab_ref = torch.empty_like(lab)
+    sse, resc = bm.bm_assign_rows_prec(dev(X), m, n, dev(C), dev(live), k, BF16, lab)
+    bm.bm_assign_rows(dev(X), m, n, dev(C), dev(live), k, lab_ref)
+    assert torch.equal(lab, lab_ref)
+    assert resc > m // 2
