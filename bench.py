@@ -33,6 +33,9 @@ UNIT = "TFLOP/s"
 WORKLOAD = dict(name="hepmass_like_m1e6_n28_k25_s50000_T100", m=1_000_000, n=28,
                 k=25, s=50_000, chunks=100, seed=0)
 CPU_SAMPLE_CHUNKS = 20
+# precision comparison on the m = 1e7, n = 128 mixture (generated on the device)
+C3_WORKLOAD = dict(name="gas_sensor_like_m1e7_n128_k50_s50000_T100", m=10_000_000, n=128,
+                   k=50, s=50_000, chunks=100, seed=0)
 
 
 def parse():
@@ -42,6 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--chunks", type=int, default=WORKLOAD["chunks"])
     return ap.parse_args()
 
@@ -172,6 +176,57 @@ def run_reference(args, wl):
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def time_jobs(bm, torch, ctx, stream, T, steps, warmup, flush, labels):
+    """Runs `warmup` + `steps` complete jobs; per-step CUDA-event times."""
+    def step(ev):
+        bm.bm_reset(ctx)
+        ev[0].record(stream)
+        rep = bm.bm_fit_chunk(ctx, T)
+        ev[1].record(stream)
+        sse = bm.bm_assign(ctx, labels)
+        ev[2].record(stream)
+        return rep, sse
+    for _ in range(warmup):
+        step([torch.cuda.Event(enable_timing=True) for _ in range(3)])
+    torch.cuda.synchronize()
+    events, reps = [], []
+    for i in range(steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        reps.append(step(ev))
+        events.append(ev)
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+    torch.cuda.synchronize()
+    fit = [e[0].elapsed_time(e[1]) for e in events]
+    asg = [e[1].elapsed_time(e[2]) for e in events]
+    return fit, asg, reps
+
+
+def precision_forms(bm, torch, dev, X, m, n, k, s, T, seed, steps, warmup, flush,
+                    forms=("fp32", "bf16x3")):
+    """Time to SSE of the same job in the FP32 and tensor-core forms."""
+    codes = {"fp32": bm.BM_FP32, "bf16": bm.BM_BF16_RESCORE, "bf16x3": bm.BM_BF16X3_RESCORE}
+    stream = torch.cuda.Stream(device=dev)
+    labels = torch.empty(m, dtype=torch.int32, device=dev)
+    out = {}
+    for form in forms:
+        cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=seed, precision=codes[form])
+        ctx = bm.bm_create(cfg, X, stream.cuda_stream)
+        try:
+            fit, asg, reps = time_jobs(bm, torch, ctx, stream, T, steps, warmup, flush, labels)
+        finally:
+            bm.bm_destroy(ctx)
+        rep, sse = reps[-1]
+        out[form] = {"time_to_sse_ms": float(np.mean(np.add(fit, asg))),
+                     "fit_ms": float(np.mean(fit)), "assign_ms": float(np.mean(asg)),
+                     "sse": sse, "f_opt": rep["f_opt"]}
+    base = out["fp32"]
+    for form, r in out.items():
+        r["sse_rel_diff_vs_fp32"] = abs(r["sse"] - base["sse"]) / base["sse"]
+        r["speedup_vs_fp32"] = base["time_to_sse_ms"] / r["time_to_sse_ms"]
+    return out
 
 
 def run_ours(args, wl):
@@ -311,6 +366,21 @@ def run_ours(args, wl):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+    if rank == 0 and not args.no_precision:
+        # same job, tensor-core form; and the m = 1e7, n = 128 workload
+        pw = min(args.steps, 3)
+        out["precision_forms"] = {
+            wl["name"]: precision_forms(bm, torch, dev, Xd, m, n, k, s, T, seed, pw, 1, flush)}
+        del Xd
+        torch.cuda.empty_cache()
+        import bminputs
+        big = C3_WORKLOAD
+        Xg = bminputs.mixtures.gas_sensor_like_device(big["seed"], m=big["m"], n=big["n"],
+                                                       device=dev)
+        out["precision_forms"][big["name"]] = precision_forms(
+            bm, torch, dev, Xg, big["m"], big["n"], big["k"], big["s"], big["chunks"],
+            big["seed"], pw, 1, flush)
+        del Xg
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(X, wl, CPU_SAMPLE_CHUNKS)
     if rank == 0:

@@ -103,3 +103,35 @@ def scaled_384(seed=0, m=2_000_000):
     rng = np.random.default_rng(seed + 7919)
     scale = np.exp(rng.uniform(np.log(0.1), np.log(10.0), size=384))
     return isotropic_blobs(m, 384, 100, seed, alpha=0.5, feature_scale=scale)[0]
+
+
+def isotropic_blobs_device(m, n, comps, seed, sigma=1.0, box=10.0, alpha=None,
+                           device="cuda"):
+    """isotropic_blobs generated on a CUDA device (for workloads of several GB).
+
+    Means and weights come from numpy PCG64(seed) as in isotropic_blobs; the
+    component ids and the Gaussian noise come from torch's CUDA generator
+    seeded with `seed`, so the data is a deterministic function of the seed
+    (but not the same numbers as isotropic_blobs).  Returns a float32 torch
+    tensor on `device`.
+    """
+    import torch
+    rng = np.random.default_rng(seed)
+    means = rng.uniform(-box, box, size=(comps, n))
+    w = _weights(rng, comps, alpha)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    mu = torch.tensor(means, dtype=torch.float32, device=device)
+    probs = torch.tensor(w, dtype=torch.float32, device=device)
+    X = torch.empty((m, n), dtype=torch.float32, device=device)
+    block = 1 << 21
+    for a in range(0, m, block):
+        b = min(m, a + block)
+        comp = torch.multinomial(probs, b - a, replacement=True, generator=g)
+        X[a:b] = mu[comp] + sigma * torch.randn((b - a, n), generator=g, device=device)
+    return X
+
+
+def gas_sensor_like_device(seed=0, m=10_000_000, n=128, device="cuda"):
+    """m = 1e7, n = 128, 100 isotropic components, Dirichlet(0.5) (k = 50), on device."""
+    return isotropic_blobs_device(m, n, 100, seed, alpha=0.5, device=device)

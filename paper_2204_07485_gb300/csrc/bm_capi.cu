@@ -8,7 +8,9 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -129,7 +131,8 @@ static int plan_capacity(long long m, long long s) {
 }
 
 static bm_status ws_create(Workspace* w, long long m, int k, long long s,
-                           const Plan& p, cudaStream_t st, int plan_cap = 1) {
+                           const Plan& p, cudaStream_t st, int plan_cap = 1,
+                           long long assign_rows = 0) {
   const size_t words = (size_t)((m + 31) / 32);
   const int G = p.grid;
   w->plan_cap = plan_cap;
@@ -149,7 +152,8 @@ static bm_status ws_create(Workspace* w, long long m, int k, long long s,
   BM_TRY(w->alloc(&w->blk_cnt, (size_t)G));
   BM_TRY(w->alloc(&w->ctl, 1));
   BM_TRY(w->alloc(&w->stats, 1));
-  w->apart_cap = std::max(p.agrid, 4096);
+  // assignment partials: per CTA (FP32 kernels) or per 128-row tile (tensor cores)
+  w->apart_cap = (int)std::max<long long>(std::max(p.agrid, 4096), (assign_rows + 127) / 128);
   BM_TRY(w->alloc(&w->apart, (size_t)w->apart_cap));
   BM_TRY(w->alloc(&w->asse, 1));
   BM_TRY(w->alloc(&w->rescored, 1));
@@ -270,7 +274,7 @@ bm_status bm_create(const bm_config* cfg, const float* X_dev, void* stream,
   bm_status st = make_plan(cfg->n, cfg->k, cfg->s, &c->plan);
   if (st != BM_OK) { delete c; return st; }
   st = ws_create(&c->ws, cfg->m, cfg->k, cfg->s, c->plan, c->stream,
-                 plan_capacity(cfg->m, cfg->s));
+                 plan_capacity(cfg->m, cfg->s), cfg->m);
   if (st != BM_OK) { delete c; return st; }
   *out = c;
   return BM_OK;
@@ -390,6 +394,56 @@ static bm_status assign_impl(const float* X, long long m, int n, int k,
   return BM_OK;
 }
 
+// Grid autotuner of the tensor-core assignment.  The best number of CTAs per
+// SM depends on (n, k, form): more CTAs overlap one tile's loads with another
+// tile's MMA and epilogue, until shared memory, TMEM or the tail of the
+// tile queue costs more.  The first call of a shape on a device times every
+// candidate on the caller's own data and keeps the fastest; results do not
+// depend on the grid (per-tile partial sums), so any candidate's output is
+// the call's output.
+}  // extern "C"
+
+template <typename Launch>
+static int tc_tuned_grid(int n, int k, int terms, size_t smem, int maxg, long long tiles,
+                         Launch launch, cudaStream_t st) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int>, int> best;   // (dev, n, k, terms)
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const auto key = std::make_tuple(dev, n, k, terms);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto itr = best.find(key);
+    if (itr != best.end()) return (int)std::min<long long>(itr->second, tiles);
+  }
+  const int per_max = std::max(1, maxg / sms);
+  int pick = maxg;
+  float pick_ms = 1e30f;
+  if (tiles >= (long long)sms * 4) {   // enough work to tell candidates apart
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int per = 1; per <= per_max; ++per) {
+      const int g = sms * per;
+      cudaEventRecord(e0, st);
+      if (launch(g) != cudaSuccess) break;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < pick_ms) { pick_ms = ms; pick = g; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> g(mu);
+    best[key] = pick;
+  }
+  return (int)std::max<long long>(1, std::min<long long>(pick, tiles));
+}
+
+extern "C" {
+
 // Tensor-core assignment (BF16 distances, exact FP32 rescoring).
 static bm_status assign_tc_impl(const float* X, long long m, int n, int k,
                                 const float* C, int cstride, const uint8_t* mask,
@@ -411,11 +465,21 @@ static bm_status assign_tc_impl(const float* X, long long m, int n, int k,
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   maxg = std::min(maxg, sms * std::max(1, 512 / ncols));   // TMEM columns per SM
   const long long tiles = (m + 127) / 128;
-  const int grid = (int)std::max<long long>(1, std::min<long long>(maxg, tiles));
-  if (grid > w.apart_cap) return BM_EUNSUPPORTED;
+  if (tiles > w.apart_cap) return BM_EUNSUPPORTED;
+  const int grid = tc_tuned_grid(n, k, terms, smem, maxg, tiles, [&](int g) {
+    AssignTcArgs t{};
+    t.X = X; t.m = m; t.n = n; t.C = C; t.cstride = cstride; t.mask = mask; t.k = k;
+    t.labels = labels; t.dmin = dmin; t.part = reinterpret_cast<float2*>(w.apart);
+    t.sse = w.asse; t.ticket = &w.ctl->assign_ticket; t.rescored = w.rescored;
+    t.status = &w.ctl->status; t.kb = kb; t.npad16 = npad16; t.ncols = ncols;
+    t.stages = stages; t.use_bulk = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+    t.terms = terms; t.cf = cf;
+    return launch_assign_tc(t, g, smem, st);
+  }, st);
   AssignTcArgs a{};
   a.X = X; a.m = m; a.n = n; a.C = C; a.cstride = cstride; a.mask = mask; a.k = k;
-  a.labels = labels; a.dmin = dmin; a.part = w.apart; a.sse = w.asse;
+  a.labels = labels; a.dmin = dmin; a.part = reinterpret_cast<float2*>(w.apart);
+  a.sse = w.asse;
   a.ticket = &w.ctl->assign_ticket; a.rescored = w.rescored; a.status = &w.ctl->status;
   a.kb = kb; a.npad16 = npad16; a.ncols = ncols; a.stages = stages;
   a.use_bulk = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
@@ -702,11 +766,11 @@ bm_status bm_assign_rows_prec(const float* X_dev, int64_t m, int32_t n,
   std::lock_guard<std::mutex> g(g_ops_mu);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (count_live_host(mask_dev, k, st) <= 0) return BM_EINVAL;
-  Plan p;
-  bm_status rc = make_plan(n, k, std::max<long long>(k, 1), &p);
+  Plan p;   // only the assignment scratch is used: a minimal chunk plan
+  bm_status rc = make_plan(1, 1, 1, &p);
   if (rc != BM_OK) return rc;
   Workspace w;
-  rc = ws_create(&w, k, k, k, p, st);
+  rc = ws_create(&w, 1, 1, 1, p, st, 1, m);
   if (rc != BM_OK) return rc;
   unsigned long long resc = 0;
   rc = assign_tc_impl(X_dev, m, n, k, C_dev, n, mask_dev, labels_dev, dmin_dev, w, st,

@@ -109,7 +109,7 @@ struct AssignTcArgs {
   int k;
   int32_t* labels;     // m or null
   float* dmin;         // m or null
-  double* part;        // [grid]
+  float2* part;        // [ceil(m / 128)] per-tile SSE as (hi, lo) pairs
   double* sse;         // device scalar
   uint32_t* ticket;    // zero between launches
   unsigned long long* rescored;  // rows that needed exact rechecks (added to)

@@ -124,6 +124,7 @@ assign_tc_kernel(AssignTcArgs a) {
   uint64_t* mma_bar = reinterpret_cast<uint64_t*>(smem_tc + L.bars);
   uint32_t* holder = reinterpret_cast<uint32_t*>(smem_tc + L.holder);
   __shared__ float s_bound[2];      // 2 eps max ||c_j||, e_c max ||c_j||^2
+  __shared__ float2 s_pair[kTcThreads / 32];   // per-warp SSE pairs
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long ntiles = (a.m + kTcRows - 1) / kTcRows;
   const int planeA = kb * kTcRows * 128, planeB = kb * N * 128;
@@ -192,7 +193,6 @@ assign_tc_kernel(AssignTcArgs a) {
                    : (nch <= 16) ? 4 : (nch <= 32) ? 5 : 6;   // log2 of chunk slots per row
   const int cslots = 1 << cshift;
 
-  float hi = 0.f, lo = 0.f;           // this thread's SSE (TwoSum pair)
   unsigned rescored = 0;
   bool ok = true;
   for (long long it = 0;; ++it) {
@@ -331,41 +331,56 @@ assign_tc_kernel(AssignTcArgs a) {
         if (bj == INT_MAX || d < best) { best = d; bj = j; }
       }
     }
+    // the tile's SSE as an exact (hi, lo) pair, so that the total does not
+    // depend on how tiles are spread over CTAs
+    float th = valid ? best : 0.f, tl = 0.f;
     if (valid) {
       if (a.labels) a.labels[r0 + r] = bj;
       if (a.dmin) a.dmin[r0 + r] = best;
-      two_sum_acc(hi, lo, best);
       rescored += ncand > 1;
     }
+    warp_two_sum(th, tl);
+    if (lane == 0) s_pair[warp] = make_float2(th, tl);
     xx[r] = 0.f;
     BM_TC_TICK(3);
     tc_fence_before();
     __syncthreads();
+    if (tid == 0) {
+      float2 p = s_pair[0];
+      for (int w = 1; w < kTcThreads / 32; ++w) {
+        two_sum_acc(p.x, p.y, s_pair[w].x);
+        p.y = __fadd_rn(p.y, s_pair[w].y);
+      }
+      a.part[t] = p;
+    }
     BM_TC_TICK(4);
   }
 
-  // ---- SSE: TwoSum pairs per warp, FP64 per CTA, last CTA sums in order
-  warp_two_sum(hi, lo);
+  // ---- SSE: the last CTA adds the per-tile pairs in tile order (TwoSum)
   const unsigned resc = __reduce_add_sync(0xffffffffu, rescored);
-  if (lane == 0) {
-    red[warp] = (double)hi + (double)lo;
-    if (resc) atomicAdd(a.rescored, (unsigned long long)resc);
-  }
+  if (lane == 0 && resc) atomicAdd(a.rescored, (unsigned long long)resc);
   if (!ok) atomicCAS(a.status, 0, kStatusTimeout);
   __syncthreads();
   __shared__ int s_last;
   if (tid == 0) {
-    double blk = 0.0;
-    for (int w = 0; w < kTcThreads / 32; ++w) blk += red[w];
-    a.part[blockIdx.x] = blk;
     __threadfence();
     s_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (s_last && tid < 32) {
+  if (s_last) {
     __threadfence();
-    const double tot = warp_sum_array_f64(a.part, gridDim.x);
+    float hi = 0.f, lo = 0.f;
+    for (long long q = tid; q < ntiles; q += kTcThreads) {
+      const float2 p = __ldcg(a.part + q);
+      two_sum_acc(hi, lo, p.x);
+      lo = __fadd_rn(lo, p.y);
+    }
+    warp_two_sum(hi, lo);
+    if (lane == 0) s_pair[warp] = make_float2(hi, lo);
+    __syncthreads();
     if (tid == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < kTcThreads / 32; ++w) tot += (double)s_pair[w].x + (double)s_pair[w].y;
       *a.sse = tot;
       *a.ticket = 0u;
     }

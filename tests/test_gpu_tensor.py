@@ -58,7 +58,8 @@ def test_bf16_rescore_equals_fp32_path_bitwise(bm, m, n, k, seed, prec):
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("m,n,k,seed", [(6000, 128, 50, 0), (2050, 384, 20, 1),
                                         (3001, 33, 100, 2), (1500, 64, 7, 3),
-                                        (777, 127, 64, 4), (129, 200, 9, 5)])
+                                        (777, 127, 64, 4), (129, 200, 9, 5),
+                                        (1100, 384, 100, 6)])
 def test_bf16_rescore_matches_oracle(bm, m, n, k, seed, prec):
     X, C, live = _case(m, n, k, seed)
     lab = torch.empty(m, dtype=torch.int32, device="cuda:0")
@@ -107,3 +108,20 @@ def test_bf16_close_centroids_force_rescoring(bm):
     bm.bm_assign_rows(dev(X), m, n, dev(C), dev(live), k, lab_ref)
     assert torch.equal(lab, lab_ref)
     assert resc > m // 2
+
+
+def test_results_do_not_depend_on_the_tuned_grid(bm):
+    # the first call of a shape times several grids; every later call uses
+    # the chosen one -- all must give the same bits
+    m, n, k = 300_001, 20, 30
+    X, C, live = _case(m, n, k, 13)
+    Xd, Cd, md = dev(X), dev(C), dev(live)
+    outs = []
+    for _ in range(3):
+        lab = torch.empty(m, dtype=torch.int32, device="cuda:0")
+        dmin = torch.empty(m, dtype=torch.float32, device="cuda:0")
+        sse, _ = bm.bm_assign_rows_prec(Xd, m, n, Cd, md, k, BF16X3, lab, dmin)
+        outs.append((lab, dmin, sse))
+    for lab, dmin, sse in outs[1:]:
+        assert torch.equal(lab, outs[0][0]) and torch.equal(dmin, outs[0][1])
+        assert sse == outs[0][2]
