@@ -23,6 +23,7 @@ namespace bm {
 // ------------------------------------------------------------------ plan
 // Kernel family and launch shape for one (n, k, s) on the current device.
 struct Plan {
+  bool tc = false;   // tensor-core chunk kernel (rows wider than 32 features)
   bool generic = false;
   int np = 0;        // register row width of the np path
   int npad = 0;      // row stride of P and C (floats)
@@ -30,13 +31,74 @@ struct Plan {
   int grid = 0;      // CTAs of the chunk kernel
   int R = 0;         // sample rows per CTA
   size_t smem = 0;   // dynamic shared memory of the chunk kernel
-  int agrid = 0;     // CTAs of the assign kernel
+  int agrid = 0;     // CTAs of the FP32 assign kernel (0: tensor cores only)
   size_t asmem = 0;
+  int tc_kb = 0, tc_n16 = 0, tc_ncols = 0, tc_fb = 0, tc_ns = 0, tc_tpc = 0;
 };
 
 static constexpr size_t kSmemLimit = 227 * 1024;
 
-static bm_status make_plan(int n, int k, long long s, Plan* out) {
+// Tensor-core chunk plan: one CTA per SM (TMEM, grid barrier), at least one
+// 128-row tile per CTA, the widest staged feature block that fits.
+static bm_status make_plan_tc(int n, int k, long long s, Plan* out) {
+  if (k > kMaxK || n > 512) return BM_EUNSUPPORTED;
+  Plan p;
+  p.tc = true;
+  p.generic = true;
+  p.npad = align_up(n, 4);
+  p.kpad = align_up(k, 32);
+  p.tc_kb = (n + 63) / 64;
+  p.tc_n16 = align_up(k, 16);
+  p.tc_ncols = 32;
+  while (p.tc_ncols < p.tc_n16) p.tc_ncols <<= 1;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return BM_ECUDA;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int grid = (int)std::max<long long>(1, std::min<long long>((s + 127) / 128, sms));
+  for (int iter = 0; iter < 4 && p.grid == 0; ++iter) {
+    const int R = (int)((s + grid - 1) / grid);
+    size_t smem = 0;
+    int fb = 0, ns = 0;
+    // widest staged block first, then a three-slot ring if it still fits
+    for (int f : {64, 32, 16, 8, 4}) {
+      for (int r : {3, 2}) {
+        smem = chunk_tc_smem(p.npad, k, R, p.tc_n16, f, r);
+        if (smem + 2048 <= kSmemLimit) { fb = f; ns = r; break; }   // + static smem
+      }
+      if (fb) break;
+    }
+    if (fb == 0) return BM_EUNSUPPORTED;   // sample too large per SM
+    const int maxg = chunk_tc_max_grid(smem);
+    if (maxg <= 0) return BM_EUNSUPPORTED;
+    if (grid > maxg) { grid = maxg; continue; }
+    p.grid = grid;
+    p.R = R;
+    p.smem = smem;
+    p.tc_fb = fb;
+    p.tc_ns = ns;
+    p.tc_tpc = (R + 127) / 128;
+  }
+  if (p.grid == 0) return BM_EUNSUPPORTED;
+  // final assignment: the FP32 kernel when its tables fit, else tensor cores
+  p.asmem = assign_smem(p.npad, k, p.kpad, true);
+  p.agrid = p.asmem <= kSmemLimit ? assign_max_grid(true, 0, p.asmem) : 0;
+  *out = p;
+  return BM_OK;
+}
+
+static bm_status make_plan_simt(int n, int k, long long s, Plan* out);
+
+// Kernel family for (n, k, s): the row-in-register path for n <= 32; for
+// wider rows the tensor-core path when asked for (tc) or when the FP32
+// tables do not fit in shared memory, else the tiled FP32 path.
+static bm_status make_plan(int n, int k, long long s, Plan* out, bool tc = false) {
+  if (n > kNpMax && tc) return make_plan_tc(n, k, s, out);
+  const bm_status st = make_plan_simt(n, k, s, out);
+  if (st == BM_EUNSUPPORTED && n > kNpMax) return make_plan_tc(n, k, s, out);
+  return st;
+}
+
+static bm_status make_plan_simt(int n, int k, long long s, Plan* out) {
   Plan p;
   if (k > kMaxK) return BM_EUNSUPPORTED;
   if (n <= kNpMax) {
@@ -106,6 +168,9 @@ struct Workspace {
   int apart_cap = 0;
   double* asse = nullptr;    // assign result
   unsigned long long* rescored = nullptr;  // tensor-core assign: rescored rows
+  unsigned char* Cb = nullptr;  // tensor-core chunk kernel: centroid BF16 planes,
+  float* sqs = nullptr;         // squared norms of 8-feature slices,
+  unsigned char* Pb = nullptr;  // own-row BF16 planes
   std::vector<void*> owned;
 
   template <typename T>
@@ -157,7 +222,14 @@ static bm_status ws_create(Workspace* w, long long m, int k, long long s,
   BM_TRY(w->alloc(&w->apart, (size_t)w->apart_cap));
   BM_TRY(w->alloc(&w->asse, 1));
   BM_TRY(w->alloc(&w->rescored, 1));
+  const size_t cb_bytes = p.tc ? (size_t)p.tc_kb * 2 * p.tc_n16 * 128 : 16;
+  if (p.tc) {
+    BM_TRY(w->alloc(&w->Cb, cb_bytes));
+    BM_TRY(w->alloc(&w->sqs, (size_t)k * ((p.npad + 7) / 8)));
+    BM_TRY(w->alloc(&w->Pb, (size_t)p.grid * p.tc_tpc * p.tc_kb * 32768));
+  }
 #undef BM_TRY
+  if (p.tc) cudaMemsetAsync(w->Cb, 0, cb_bytes, st);
   cudaMemsetAsync(w->bitmap, 0, words * 4 * plan_cap, st);
   cudaMemsetAsync(w->C, 0, (size_t)k * p.npad * 4, st);
   cudaMemsetAsync(w->Cinc, 0, (size_t)k * p.npad * 4, st);
@@ -181,7 +253,16 @@ static ChunkArgs chunk_args(const Workspace& w, const Plan& p, const float* X,
   a.Cinc = w.Cinc; a.mask_inc = w.mask_inc; a.f_opt = w.f_opt;
   a.part_sum = w.part_sum; a.part_cnt = w.part_cnt; a.part_f = w.part_f;
   a.blk_cnt = w.blk_cnt; a.ctl = w.ctl; a.stats = w.stats;
+  a.tc_kb = p.tc_kb; a.tc_n16 = p.tc_n16; a.tc_ncols = p.tc_ncols; a.tc_fb = p.tc_fb;
+  a.tc_tpc = p.tc_tpc; a.tc_ns = p.tc_ns;
+  a.Cb = w.Cb; a.sqs = w.sqs; a.Pb = w.Pb;
   return a;
+}
+
+// One chunk-kernel launch of the plan's family.
+static cudaError_t launch_plan(const ChunkArgs& a, const Plan& p, cudaStream_t st) {
+  if (p.tc) return launch_chunk_tc(a, p.grid, p.smem, st);
+  return launch_chunk(a, p.grid, p.generic, p.np, p.smem, st);
 }
 
 static bool shape_ok(long long m, int n, int k, long long s) {
@@ -271,7 +352,8 @@ bm_status bm_create(const bm_config* cfg, const float* X_dev, void* stream,
   c->cfg = *cfg;
   c->X = X_dev;
   c->stream = static_cast<cudaStream_t>(stream);
-  bm_status st = make_plan(cfg->n, cfg->k, cfg->s, &c->plan);
+  const bool tc = cfg->precision == BM_BF16_RESCORE || cfg->precision == BM_BF16X3_RESCORE;
+  bm_status st = make_plan(cfg->n, cfg->k, cfg->s, &c->plan, tc);
   if (st != BM_OK) { delete c; return st; }
   st = ws_create(&c->ws, cfg->m, cfg->k, cfg->s, c->plan, c->stream,
                  plan_capacity(cfg->m, cfg->s), cfg->m);
@@ -343,8 +425,7 @@ bm_status bm_fit_chunk(bm_ctx* c, int32_t chunks, bm_fit_report* out) {
     a.idx = c->ws.idx + (size_t)(c->t - c->plan_t0) * c->cfg.s;
     a.t = c->t;
     a.bar_sel = (int)(c->launches & 1);
-    cudaError_t e = launch_chunk(a, c->plan.grid, c->plan.generic, c->plan.np,
-                                 c->plan.smem, c->stream);
+    cudaError_t e = launch_plan(a, c->plan, c->stream);
     if (e != cudaSuccess) { st = BM_ECUDA; break; }
     ++c->launches;
     ++c->t;
@@ -515,10 +596,13 @@ bm_status bm_assign(bm_ctx* c, int32_t* labels_dev, double* sse_out) {
   if (live < 0) return BM_ECUDA;
   if (live == 0) return BM_EINVAL;   // no incumbent yet
   bm_status st;
-  if (c->cfg.precision == BM_BF16_RESCORE || c->cfg.precision == BM_BF16X3_RESCORE)
+  // FP32 results from the tensor cores too when the FP32 kernel's tables do
+  // not fit (the rescoring makes the labels and distances those of FP32)
+  if (c->cfg.precision == BM_BF16_RESCORE || c->cfg.precision == BM_BF16X3_RESCORE ||
+      c->plan.agrid == 0)
     st = assign_tc_impl(c->X, c->cfg.m, c->cfg.n, c->cfg.k, c->ws.Cinc, c->plan.npad,
                         c->ws.mask_inc, labels_dev, nullptr, c->ws, c->stream, sse_out,
-                        &c->rescored, c->cfg.precision == BM_BF16X3_RESCORE ? 3 : 1);
+                        &c->rescored, c->cfg.precision == BM_BF16_RESCORE ? 1 : 3);
   else
     st = assign_impl(c->X, c->cfg.m, c->cfg.n, c->cfg.k, c->plan, c->ws.Cinc,
                      c->plan.npad, c->ws.mask_inc, labels_dev, nullptr, c->ws,
@@ -654,7 +738,7 @@ bm_status bm_gather(const float* X_dev, int64_t m, int32_t n,
   ChunkArgs a = chunk_args(w, p, X_dev, m, n, 1, s);
   a.idx = const_cast<int32_t*>(idx_dev);
   a.phases = kPhaseGather;
-  if (launch_chunk(a, p.grid, p.generic, p.np, p.smem, st) != cudaSuccess) rc = BM_ECUDA;
+  if (launch_plan(a, p, st) != cudaSuccess) rc = BM_ECUDA;
   if (rc == BM_OK) rc = check_status(w, st, m);
   if (rc == BM_OK &&
       cudaMemcpy2DAsync(P_dev, n * 4, w.P, p.npad * 4, n * 4, s, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
@@ -705,8 +789,7 @@ bm_status bm_kpp_reseed(const float* P_dev, int64_t s, int32_t n, int32_t k,
   a.t = t;
   a.trials = trials;
   a.phases = kPhaseKpp;
-  if (rc == BM_OK && launch_chunk(a, p.grid, p.generic, p.np, p.smem, st) != cudaSuccess)
-    rc = BM_ECUDA;
+  if (rc == BM_OK && launch_plan(a, p, st) != cudaSuccess) rc = BM_ECUDA;
   if (rc == BM_OK) rc = check_status(w, st, s);
   if (rc == BM_OK) rc = unstage_outputs(w, p, n, k, C_dev, mask_dev, st);
   cudaStreamSynchronize(st);
@@ -735,8 +818,7 @@ bm_status bm_lloyd(const float* P_dev, int64_t s, int32_t n, int32_t k,
   a.max_iter = max_iter;
   a.tol = tol;
   a.phases = kPhaseLloyd;
-  if (rc == BM_OK && launch_chunk(a, p.grid, p.generic, p.np, p.smem, st) != cudaSuccess)
-    rc = BM_ECUDA;
+  if (rc == BM_OK && launch_plan(a, p, st) != cudaSuccess) rc = BM_ECUDA;
   if (rc == BM_OK) rc = check_status(w, st, s);
   if (rc == BM_OK) rc = unstage_outputs(w, p, n, k, C_dev, mask_dev, st);
   if (rc == BM_OK) {
@@ -794,9 +876,13 @@ bm_status bm_assign_rows(const float* X_dev, int64_t m, int32_t n,
   bm_status rc = make_plan(n, k, std::max<long long>(k, 1), &p);
   if (rc != BM_OK) return rc;
   Workspace w;
-  rc = ws_create(&w, k, k, k, p, st);
+  rc = ws_create(&w, k, k, k, p, st, 1, p.agrid == 0 ? m : 0);
   if (rc != BM_OK) return rc;
-  rc = assign_impl(X_dev, m, n, k, p, C_dev, n, mask_dev, labels_dev, dmin_dev, w, st, sse_out);
+  if (p.agrid == 0)
+    rc = assign_tc_impl(X_dev, m, n, k, C_dev, n, mask_dev, labels_dev, dmin_dev, w, st,
+                        sse_out, nullptr, 3);
+  else
+    rc = assign_impl(X_dev, m, n, k, p, C_dev, n, mask_dev, labels_dev, dmin_dev, w, st, sse_out);
   cudaStreamSynchronize(st);
   w.release();
   return rc;

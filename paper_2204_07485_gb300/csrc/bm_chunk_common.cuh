@@ -1,0 +1,66 @@
+// Pieces shared by the chunk kernels: CTA 0's phase timers, the live
+// centroid list and the fixed-order sum of per-row minima.
+#pragma once
+
+#include "bm_device.cuh"
+#include "bm_internal.h"
+
+namespace bm {
+
+// Phase timers of CTA 0, accumulated in shared memory during the launch and
+// added to Stats::phase_ns once at its end (a global read-modify-write per
+// tick would stall CTA 0, and through the next grid barrier every CTA).
+__device__ __forceinline__ unsigned long long* phase_slots() {
+  __shared__ unsigned long long slots[kNumPhaseTimers];
+  return slots;
+}
+
+// Thread 0 of CTA 0 adds the time since *t0 to slot i.
+__device__ __forceinline__ void phase_tick(Stats* st, int i, uint64_t* t0) {
+  (void)st;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const uint64_t t = global_timer_ns();
+    phase_slots()[i] += t - *t0;
+    *t0 = t;
+  }
+}
+
+// lidx[0..c) <- indices of the live centroids in ascending order, lidx[k] = c.
+// Called by all threads; ends with a barrier.
+__device__ __forceinline__ void build_live_list(const int* live, int* lidx, int k) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int c = 0;
+    for (int base = 0; base < k; base += 32) {
+      const int j = base + (int)threadIdx.x;
+      const bool on = j < k && live[j];
+      const unsigned bal = __ballot_sync(0xffffffffu, on);
+      if (on) lidx[c + __popc(bal & ((1u << threadIdx.x) - 1u))] = j;
+      c += __popc(bal);
+    }
+    if (threadIdx.x == 0) lidx[k] = c;
+  }
+  __syncthreads();
+}
+
+// Fixed-order sum of dmin[0..nrows), carried exactly in FP32 pairs (TwoSum)
+// within each warp and added up in FP64 by one thread; every thread gets the
+// result.  red holds at least 33 doubles.
+__device__ __forceinline__ double dmin_sum(const float* dmin, int nrows, double* red) {
+  float hi = 0.f, lo = 0.f;
+  for (int i = threadIdx.x; i < nrows; i += blockDim.x) two_sum_acc(hi, lo, dmin[i]);
+  warp_two_sum(hi, lo);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) red[w] = (double)hi + (double)lo;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t += red[i];
+    red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+}  // namespace bm

@@ -74,6 +74,16 @@ struct ChunkArgs {
   int32_t* blk_cnt;    // [G]
   Ctl* ctl;
   Stats* stats;
+  // tensor-core chunk kernel (rows wider than 32 features)
+  int tc_kb;              // 64-feature K blocks
+  int tc_n16;             // MMA N: k rounded up to 16
+  int tc_ncols;           // TMEM columns
+  int tc_fb;              // features per staged block of the exact passes
+  int tc_tpc;             // 128-row tiles per CTA: ceil(rows_per_cta / 128)
+  int tc_ns;              // MMA ring slots (2 or 3)
+  unsigned char* Cb;      // [tc_kb][2][tc_n16][128 B] centroid BF16 planes (hi, lo), swizzled
+  float* sqs;             // [k][ceil(npad / 8)] squared norms of 8-feature slices of C
+  unsigned char* Pb;      // [G][tc_tpc][tc_kb][2][128][128 B] own-row BF16 planes, swizzled
 };
 
 struct AssignArgs {
@@ -187,6 +197,11 @@ int assign_tc_max_grid(size_t smem);
 cudaError_t launch_assign_tc(const AssignTcArgs& a, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_chunk(const ChunkArgs& a, int grid, bool generic, int np,
                          size_t smem, cudaStream_t st);
+// tensor-core chunk kernel: shared memory for (npad, k, R, n16, fb, ring
+// slots); CTAs that can be co-resident; launch
+size_t chunk_tc_smem(int npad, int k, int R, int n16, int fb, int ns);
+int chunk_tc_max_grid(size_t smem);
+cudaError_t launch_chunk_tc(const ChunkArgs& a, int grid, size_t smem, cudaStream_t st);
 int chunk_max_grid(bool generic, int np, size_t smem);
 cudaError_t launch_assign(const AssignArgs& a, int grid, bool generic, int np,
                           size_t smem, cudaStream_t st);

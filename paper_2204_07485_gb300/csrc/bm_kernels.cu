@@ -26,6 +26,8 @@
 
 #include "bm_device.cuh"
 #include "bm_internal.h"
+#include "bm_chunk_common.cuh"
+#include "bm_kpp.cuh"
 
 namespace bm {
 
@@ -65,42 +67,6 @@ __device__ __forceinline__ Smem carve(char* base, const ChunkSmem& L) {
 }
 
 __device__ __forceinline__ float sq(float e, float acc) { return fmaf(e, e, acc); }
-
-// Phase timers of CTA 0, accumulated in shared memory during the launch and
-// added to Stats::phase_ns once at its end (a global read-modify-write per
-// tick would stall CTA 0, and through the next grid barrier every CTA).
-__device__ __forceinline__ unsigned long long* phase_slots() {
-  __shared__ unsigned long long slots[kNumPhaseTimers];
-  return slots;
-}
-
-// Thread 0 of CTA 0 adds the time since *t0 to slot i.
-__device__ __forceinline__ void phase_tick(Stats* st, int i, uint64_t* t0) {
-  (void)st;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const uint64_t t = global_timer_ns();
-    phase_slots()[i] += t - *t0;
-    *t0 = t;
-  }
-}
-
-// lidx[0..c) <- indices of the live centroids in ascending order, lidx[k] = c.
-// Called by all threads; ends with a barrier.
-__device__ __forceinline__ void build_live_list(const int* live, int* lidx, int k) {
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    int c = 0;
-    for (int base = 0; base < k; base += 32) {
-      const int j = base + (int)threadIdx.x;
-      const bool on = j < k && live[j];
-      const unsigned bal = __ballot_sync(0xffffffffu, on);
-      if (on) lidx[c + __popc(bal & ((1u << threadIdx.x) - 1u))] = j;
-      c += __popc(bal);
-    }
-    if (threadIdx.x == 0) lidx[k] = c;
-  }
-  __syncthreads();
-}
 
 // Centroid (j, f) into the shared tables of either layout (the tiled layout
 // keeps a row-major copy too unless WITH_ROW is false).
@@ -352,24 +318,9 @@ __device__ void assign_own_rows(const ChunkArgs& a, const Smem& S, int r0,
   }
 }
 
-// Fixed-order sum of S.dmin over own rows, carried exactly in FP32 pairs
-// (TwoSum) within each warp and added up in FP64 by one thread; every thread
-// gets the result.
+// Fixed-order sum of S.dmin over own rows (see dmin_sum); every thread gets it.
 __device__ __forceinline__ double own_dmin_sum(const Smem& S, int nrows) {
-  float hi = 0.f, lo = 0.f;
-  for (int i = threadIdx.x; i < nrows; i += blockDim.x) two_sum_acc(hi, lo, S.dmin[i]);
-  warp_two_sum(hi, lo);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-  __syncthreads();
-  if (l == 0) S.red[w] = (double)hi + (double)lo;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < nw; ++i) t += S.red[i];
-    S.red[32] = t;
-  }
-  __syncthreads();
-  return S.red[32];
+  return dmin_sum(S.dmin, nrows, S.red);
 }
 
 // Squared distances of own rows to the nc candidate rows in S.cand
@@ -679,8 +630,6 @@ __device__ bool phase_kpp(const ChunkArgs& a, const Smem& S, GridBarrier& gb,
   const int nlive = S.lidx[k];
   if (nlive == k) return true;
   long long nd = 0;
-  __shared__ double s_tgt[kMaxTrials], s_excl[kMaxTrials], s_total;
-  __shared__ int s_bstar[kMaxTrials], s_best;
   double* DSUM = a.part_f + (size_t)kMaxTrials * G;   // D^2 block sums region
   if (nlive > 0) {
     assign_own_rows<NP, GENERIC>(a, S, r0, nrows);
@@ -708,103 +657,8 @@ __device__ bool phase_kpp(const ChunkArgs& a, const Smem& S, GridBarrier& gb,
     const double mine = own_dmin_sum(S, nrows);
     if (threadIdx.x == 0) DSUM[b] = mine;
     if (!gb.sync()) return false;
-    // (B) total, target blocks (every CTA, identical arithmetic)
-    if (w == 0) {
-      double carry = 0.0;
-      for (int base = 0; base < G; base += 32) {
-        const double v = (base + l < G) ? __ldcg(DSUM + base + l) : 0.0;
-        carry += warp_sum_f64(v);
-      }
-      const double total = carry;
-      double tgt[kMaxTrials];
-      int found[kMaxTrials];
-      double excl[kMaxTrials];
-#pragma unroll
-      for (int t = 0; t < kMaxTrials; ++t) {
-        tgt[t] = t < a.trials
-            ? unit_double(philox_word(a.seed, (uint64_t)a.t, 2, 0,
-                                      (uint64_t)(j * a.trials + t))) * total
-            : 0.0;
-        found[t] = -1;
-        excl[t] = 0.0;
-      }
-      if (total > 0.0) {
-        double run = 0.0;
-        int last_pos = -1;
-        double last_excl = 0.0;
-        for (int base = 0; base < G; base += 32) {
-          const double v = (base + l < G) ? __ldcg(DSUM + base + l) : 0.0;
-          double x = v;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const double y = __shfl_up_sync(0xffffffffu, x, o);
-            if (l >= o) x += y;
-          }
-          const double incl = run + x;
-#pragma unroll
-          for (int t = 0; t < kMaxTrials; ++t) {
-            if (t < a.trials && found[t] < 0) {
-              const unsigned hit = __ballot_sync(0xffffffffu, base + l < G && incl > tgt[t]);
-              if (hit) {
-                const int ll = __ffs(hit) - 1;
-                found[t] = base + ll;
-                excl[t] = __shfl_sync(0xffffffffu, incl - v, ll);
-              }
-            }
-          }
-          const unsigned pos = __ballot_sync(0xffffffffu, base + l < G && v > 0.0);
-          if (pos) {
-            const int ll = 31 - __clz(pos);
-            last_pos = base + ll;
-            last_excl = __shfl_sync(0xffffffffu, incl - v, ll);
-          }
-          run = __shfl_sync(0xffffffffu, incl, 31);
-        }
-#pragma unroll
-        for (int t = 0; t < kMaxTrials; ++t)
-          if (t < a.trials && found[t] < 0) { found[t] = last_pos; excl[t] = last_excl; }
-      }
-      if (l == 0) {
-        s_total = total;
-#pragma unroll
-        for (int t = 0; t < kMaxTrials; ++t) {
-          s_tgt[t] = tgt[t];
-          s_bstar[t] = found[t];
-          s_excl[t] = excl[t];
-        }
-      }
-    }
-    __syncthreads();
-    // the CTA that owns a target finds the row inside its block
-    for (int t = 0; t < a.trials; ++t) {
-      if (s_total == 0.0) {
-        if (b == 0 && threadIdx.x == 0) {
-          const double u = unit_double(philox_word(a.seed, (uint64_t)a.t, 2, 0,
-                                                   (uint64_t)(j * a.trials + t)));
-          a.ctl->cand[t] = (int)floor(u * (double)a.s);
-        }
-      } else if (s_bstar[t] == b && w == 0) {
-        double run = s_excl[t];
-        int cand = -1, lastp = -1;
-        for (int base = 0; base < nrows && cand < 0; base += 32) {
-          const double v = base + l < nrows ? (double)S.dmin[base + l] : 0.0;
-          double x = v;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const double y = __shfl_up_sync(0xffffffffu, x, o);
-            if (l >= o) x += y;
-          }
-          const double incl = run + x;
-          const unsigned hit = __ballot_sync(0xffffffffu, base + l < nrows && incl > s_tgt[t]);
-          if (hit) cand = base + __ffs(hit) - 1;
-          const unsigned pos = __ballot_sync(0xffffffffu, base + l < nrows && v > 0.0);
-          if (pos) lastp = base + 31 - __clz(pos);
-          run = __shfl_sync(0xffffffffu, incl, 31);
-        }
-        if (cand < 0) cand = lastp;
-        if (l == 0) a.ctl->cand[t] = r0 + cand;
-      }
-    }
+    // (B) targets, the blocks that hold them and the rows inside those blocks
+    kpp_locate(a, S.dmin, r0, nrows, DSUM, j);
     if (!gb.sync()) return false;
     // (C) potentials of the candidates
     for (int t = 0; t < a.trials; ++t) load_cand_row(a, S, t, __ldcg(a.ctl->cand + t));
@@ -820,27 +674,7 @@ __device__ bool phase_kpp(const ChunkArgs& a, const Smem& S, GridBarrier& gb,
     nd += (long long)a.s * a.trials;
     if (!gb.sync()) return false;
     // (D) choose the candidate with the lowest potential
-    if (w == 0) {
-      double v[kMaxTrials];
-#pragma unroll
-      for (int t = 0; t < kMaxTrials; ++t) v[t] = 0.0;
-      for (int u = l; u < G; u += 32)
-#pragma unroll
-        for (int t = 0; t < kMaxTrials; ++t)
-          if (t < a.trials) v[t] += __ldcg(a.part_f + (size_t)t * G + u);
-      int best = 0;
-      double bestv = 0.0;
-#pragma unroll
-      for (int t = 0; t < kMaxTrials; ++t) {
-        if (t < a.trials) {
-          const double phi = warp_sum_f64(v[t]);
-          if (t == 0 || phi < bestv) { bestv = phi; best = t; }
-        }
-      }
-      if (l == 0) s_best = best;
-    }
-    __syncthreads();
-    const int bt = s_best;
+    const int bt = kpp_best(a);
     set_centroid_row<GENERIC>(S, S.cand + bt * a.npad, j, a.npad, a.kpad);
     if (threadIdx.x == 0) S.live[j] = 1;
     if (b == 0) {
