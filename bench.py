@@ -229,6 +229,53 @@ def precision_forms(bm, torch, dev, X, m, n, k, s, T, seed, steps, warmup, flush
     return out
 
 
+def traced_phases(bm, torch, Xd, cfg, stream, T):
+    """Device time per chunk phase of one extra job run with tracing on (the
+    timed steps run without it: the timer reads sit on the barrier path)."""
+    tcfg = bm.bm_config_default(**{f: getattr(cfg, f) for f, _ in cfg._fields_})
+    tcfg.trace = 1
+    ctx = bm.bm_create(tcfg, Xd, stream.cuda_stream)
+    try:
+        bm.bm_reset(ctx)
+        bm.bm_fit_chunk(ctx, T)
+        return bm.bm_trace(ctx)
+    finally:
+        bm.bm_destroy(ctx)
+
+
+def launch_latency(bm, torch, dev, jobs=10, warmup=3):
+    """m = 20,000, n = 2, k = 10, s = 2,000, 20 chunks (ten 2-D blobs): the
+    whole chunk fits one SM, so the time is launch and barrier latency.  Fit
+    time per job with the launches recorded in a CUDA graph and one by one."""
+    import bminputs
+    m, n, k, s, T = 20_000, 2, 10, 2_000, 20
+    Xd = torch.from_numpy(bminputs.mixtures.blobs_2d(0)).to(dev)
+    out = {"workload": "blobs_2d_m20000_n2_k10_s2000_T20"}
+    for graphs in (0, 1):
+        stream = torch.cuda.Stream(device=dev)
+        cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=0, graphs=graphs)
+        ctx = bm.bm_create(cfg, Xd, stream.cuda_stream)
+        try:
+            times, iters = [], 0
+            for i in range(warmup + jobs):
+                bm.bm_reset(ctx)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rep = bm.bm_fit_chunk(ctx, T)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                if i >= warmup:
+                    times.append(e0.elapsed_time(e1))
+                    iters += rep["lloyd_iters"]
+        finally:
+            bm.bm_destroy(ctx)
+        ms = float(np.mean(times))
+        out["graph" if graphs else "direct"] = {
+            "fit_ms": ms, "us_per_chunk": ms * 1e3 / T,
+            "us_per_lloyd_iter": ms * 1e3 * jobs / max(1, iters)}
+    return out
+
+
 def run_ours(args, wl):
     import torch
     rank, world, local = dist_env()
@@ -282,7 +329,7 @@ def run_ours(args, wl):
     asg_ms = [e[1].elapsed_time(e[2]) for e in events]
     step_ms = [a + b for a, b in zip(fit_ms, asg_ms)]
     rep, sse = reps[-1]
-    phases = bm.bm_trace(ctx)      # device phase times of the last step
+    phases = traced_phases(bm, torch, Xd, cfg, stream, T)
     C = np.zeros((k, n), np.float32)
     mask = np.zeros(k, np.uint8)
     f_opt = bm.bm_objective(ctx, C, mask)
@@ -381,6 +428,8 @@ def run_ours(args, wl):
             bm, torch, dev, Xg, big["m"], big["n"], big["k"], big["s"], big["chunks"],
             big["seed"], pw, 1, flush)
         del Xg
+    if rank == 0 and not args.no_precision:
+        out["launch_latency"] = launch_latency(bm, torch, dev)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(X, wl, CPU_SAMPLE_CHUNKS)
     if rank == 0:

@@ -71,6 +71,11 @@ typedef struct bm_config {
   uint64_t seed;        /* Philox key                                          */
   int32_t precision;    /* bm_precision                                        */
   double time_budget_s; /* bm_fit_chunk(chunks = 0) runs until this elapses    */
+  int32_t graphs;       /* 1: bm_fit_chunk(chunks > 0) records its launches in
+                           a CUDA graph once per launch state and replays it;
+                           0: launches one kernel at a time                    */
+  int32_t trace;        /* 1: the chunk kernel times its phases (bm_trace);
+                           costs a timer read per phase on CTA 0               */
 } bm_config;
 
 /* What one bm_fit_chunk call did. */
@@ -87,7 +92,7 @@ typedef struct bm_fit_report {
 typedef struct bm_ctx bm_ctx;
 
 /* Fills *cfg with the paper's defaults (max_iter 300, tol 1e-4, 3 trials,
- * FP32, seed 0) and zero sizes. */
+ * FP32, seed 0), graph replay on, phase tracing off, and zero sizes. */
 void bm_config_default(bm_config* cfg);
 
 /* Human-readable name of a status code (static string). */
@@ -111,7 +116,11 @@ bm_status bm_reset(bm_ctx* ctx);
  * draw sample t, gather P, K-means++ reseed of degenerate centroids, Lloyd on
  * P, keep-the-best.  chunks = 0 runs chunks until cfg.time_budget_s of wall
  * time has elapsed (the paper's CPU-time stop condition, Sec. 5).  Blocks
- * until the work is done; `out` (may be NULL) receives the report. */
+ * until the work is done; `out` (may be NULL) receives the report.  With
+ * cfg.graphs = 1 the launches of a call are recorded once per (first chunk,
+ * chunks, launch parity, sample-plan window) and replayed as one CUDA graph
+ * afterwards (a context keeps the four most recent); results are identical
+ * either way. */
 bm_status bm_fit_chunk(bm_ctx* ctx, int32_t chunks, bm_fit_report* out);
 
 /* Final step of Alg. 1: labels_dev[i] (int32, m entries, caller-owned device
@@ -141,10 +150,14 @@ bm_status bm_set_state(bm_ctx* ctx, const float* C_host,
  * [1] gather, [2] K-means++ reseed, [3] Lloyd assignment + partial sums of
  * CTA 0's rows, [4] wait at the first Lloyd grid barrier, [5] cross-CTA
  * reduction + centroid update, [6] wait at the second barrier + reload,
- * [7] keep-the-best; [8], [9], [10] split [3] into the assignment, the
- * per-warp update slices and their combination into the partial sums
- * (row-in-register kernels only).  ns_out receives min(count, 11) values.
- * Diagnostic only; it adds no synchronisation to the kernels. */
+ * [7] keep-the-best; [8], [9], [10] split [3] -- row-in-register kernels:
+ * the assignment, the per-warp update slices and their combination into the
+ * partial sums; tensor-core kernel: the tensor-core candidate pass, the
+ * multi-candidate rows plus the label sort, and the staged exact sweep.
+ * ns_out receives min(count, 11) values.  The times are collected only by
+ * contexts created with cfg.trace = 1 (each timer read sits on CTA 0's path
+ * to the next grid barrier, so tracing slows the run slightly); otherwise
+ * they stay zero. */
 bm_status bm_trace(bm_ctx* ctx, double* ns_out, int32_t count);
 
 /* One-call job on HOST memory: copies X_host (m x n) to the device, runs

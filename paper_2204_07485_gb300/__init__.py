@@ -30,7 +30,8 @@ class bm_config(ctypes.Structure):
                 ("s", ctypes.c_int64), ("max_iter", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("kpp_trials", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
-                ("time_budget_s", ctypes.c_double)]
+                ("time_budget_s", ctypes.c_double), ("graphs", ctypes.c_int32),
+                ("trace", ctypes.c_int32)]
 
 
 class bm_fit_report(ctypes.Structure):

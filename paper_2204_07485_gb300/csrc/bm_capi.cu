@@ -294,6 +294,15 @@ static bm_status check_status(Workspace& w, cudaStream_t st, long long m) {
 using namespace bm;
 
 // ====================================================================== ctx
+// A recorded bm_fit_chunk launch sequence and the launch state it starts
+// from and ends in.
+struct FitGraph {
+  long long t, chunks, parity, plan_t0, plan_n;   // state before
+  long long end_plan_t0, end_plan_n;              // sample-plan window after
+  cudaGraphExec_t exec;
+  long long stamp;                                // last use (eviction order)
+};
+
 struct bm_ctx {
   bm_config cfg;
   const float* X;
@@ -306,8 +315,13 @@ struct bm_ctx {
   long long plan_n = 0;     // chunks held by the sample plan
   long long nd_assign = 0;  // distance evaluations of bm_assign calls
   unsigned long long rescored = 0;  // rows rescored by the last tensor-core bm_assign
+  std::vector<FitGraph> graphs;     // recorded fits, at most kMaxGraphs
+  long long graph_clock = 0;
+  bool graphs_ok = true;            // cleared if recording ever fails
   std::mutex mu;
 };
+
+static constexpr size_t kMaxGraphs = 4;
 
 extern "C" {
 
@@ -320,6 +334,8 @@ void bm_config_default(bm_config* cfg) {
   cfg->seed = 0;
   cfg->precision = BM_FP32;
   cfg->time_budget_s = 0.0;
+  cfg->graphs = 1;
+  cfg->trace = 0;
 }
 
 const char* bm_status_string(int32_t s) {
@@ -365,6 +381,7 @@ bm_status bm_create(const bm_config* cfg, const float* X_dev, void* stream,
 bm_status bm_destroy(bm_ctx* c) {
   if (!c) return BM_OK;
   cudaStreamSynchronize(c->stream);
+  for (FitGraph& g : c->graphs) cudaGraphExecDestroy(g.exec);
   c->ws.release();
   delete c;
   return BM_OK;
@@ -390,6 +407,79 @@ bm_status bm_reset(bm_ctx* c) {
   return cudaStreamSynchronize(st) == cudaSuccess ? BM_OK : BM_ECUDA;
 }
 
+// Queues the launches of `chunks` chunks from c->t (sample-plan draws as
+// the chunk index leaves the drawn window, one chunk launch per chunk) and
+// advances the host-side launch state.  `left` < 0: as many as `chunks`.
+static bm_status queue_chunks(bm_ctx* c, ChunkArgs a, long long chunks, long long left) {
+  for (long long done = 0; done < chunks; ++done) {
+    // the sample plan holds chunks [plan_t0, plan_t0 + plan_n)
+    if (c->plan_t0 < 0 || c->t < c->plan_t0 || c->t >= c->plan_t0 + c->plan_n) {
+      DrawArgs d{};
+      d.m = c->cfg.m; d.s = (int)c->cfg.s; d.seed = c->cfg.seed; d.t0 = c->t;
+      d.idx = c->ws.idx; d.bitmaps = c->ws.bitmap;
+      int batch = c->ws.plan_cap;
+      if (left >= 0) batch = (int)std::min<long long>(batch, left - done);
+      if (launch_draw(d, batch, c->stream) != cudaSuccess) return BM_ECUDA;
+      c->plan_t0 = c->t;
+      c->plan_n = batch;
+    }
+    a.idx = c->ws.idx + (size_t)(c->t - c->plan_t0) * c->cfg.s;
+    a.t = c->t;
+    a.bar_sel = (int)(c->launches & 1);
+    if (launch_plan(a, c->plan, c->stream) != cudaSuccess) return BM_ECUDA;
+    ++c->launches;
+    ++c->t;
+  }
+  return BM_OK;
+}
+
+// Replays (recording first if needed) the launch sequence of `chunks`
+// chunks from the current state as one CUDA graph.  Returns false when
+// recording is not possible; the state is then unchanged.
+static bool fit_by_graph(bm_ctx* c, const ChunkArgs& a, long long chunks, bm_status* st) {
+  const long long parity = c->launches & 1;
+  FitGraph* hit = nullptr;
+  for (FitGraph& g : c->graphs)
+    if (g.t == c->t && g.chunks == chunks && g.parity == parity && g.plan_t0 == c->plan_t0 &&
+        g.plan_n == c->plan_n)
+      hit = &g;
+  if (!hit) {
+    const long long t0 = c->t, l0 = c->launches, p0 = c->plan_t0, n0 = c->plan_n;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    const bm_status qs = queue_chunks(c, a, chunks, chunks);
+    const cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
+    cudaGraphExec_t exec = nullptr;
+    const bool ok = qs == BM_OK && ce == cudaSuccess && graph &&
+                    cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    FitGraph g{t0, chunks, parity, p0, n0, c->plan_t0, c->plan_n, exec, 0};
+    c->t = t0; c->launches = l0; c->plan_t0 = p0; c->plan_n = n0;   // nothing ran yet
+    if (!ok) {
+      cudaGetLastError();
+      return false;
+    }
+    if (c->graphs.size() >= kMaxGraphs) {
+      auto old = std::min_element(c->graphs.begin(), c->graphs.end(),
+                                  [](const FitGraph& x, const FitGraph& y) { return x.stamp < y.stamp; });
+      cudaGraphExecDestroy(old->exec);
+      c->graphs.erase(old);
+    }
+    c->graphs.push_back(g);
+    hit = &c->graphs.back();
+  }
+  hit->stamp = ++c->graph_clock;
+  *st = cudaGraphLaunch(hit->exec, c->stream) == cudaSuccess ? BM_OK : BM_ECUDA;
+  c->t += chunks;
+  c->launches += chunks;
+  c->plan_t0 = hit->end_plan_t0;
+  c->plan_n = hit->end_plan_n;
+  return true;
+}
+
 bm_status bm_fit_chunk(bm_ctx* c, int32_t chunks, bm_fit_report* out) {
   if (!c || chunks < 0) return BM_EINVAL;
   if (chunks == 0 && !(c->cfg.time_budget_s > 0.0)) return BM_EINVAL;
@@ -406,32 +496,21 @@ bm_status bm_fit_chunk(bm_ctx* c, int32_t chunks, bm_fit_report* out) {
   a.tol = c->cfg.tol;
   a.trials = c->cfg.kpp_trials;
   a.phases = kPhaseGather | kPhaseKpp | kPhaseLloyd | kPhaseKeep;
-  long long done = 0;
+  a.trace = c->cfg.trace != 0;
   bm_status st = BM_OK;
-  const bool timed = chunks == 0;
-  while (true) {
-    if (!timed && done >= chunks) break;
-    // the sample plan holds chunks [plan_t0, plan_t0 + plan_cap)
-    if (c->plan_t0 < 0 || c->t < c->plan_t0 || c->t >= c->plan_t0 + c->plan_n) {
-      DrawArgs d{};
-      d.m = c->cfg.m; d.s = (int)c->cfg.s; d.seed = c->cfg.seed; d.t0 = c->t;
-      d.idx = c->ws.idx; d.bitmaps = c->ws.bitmap;
-      int batch = c->ws.plan_cap;
-      if (!timed) batch = (int)std::min<long long>(batch, chunks - done);
-      if (launch_draw(d, batch, c->stream) != cudaSuccess) { st = BM_ECUDA; break; }
-      c->plan_t0 = c->t;
-      c->plan_n = batch;
+  if (chunks > 0) {
+    // graph replay needs a capturable stream (not the legacy default stream)
+    const bool graphed = c->cfg.graphs && c->graphs_ok && c->stream != nullptr &&
+                         fit_by_graph(c, a, chunks, &st);
+    if (!graphed) {
+      if (c->cfg.graphs && c->stream != nullptr) c->graphs_ok = false;
+      st = queue_chunks(c, a, chunks, chunks);
     }
-    a.idx = c->ws.idx + (size_t)(c->t - c->plan_t0) * c->cfg.s;
-    a.t = c->t;
-    a.bar_sel = (int)(c->launches & 1);
-    cudaError_t e = launch_plan(a, c->plan, c->stream);
-    if (e != cudaSuccess) { st = BM_ECUDA; break; }
-    ++c->launches;
-    ++c->t;
-    ++done;
-    if (timed) {
-      // the paper's time budget: check between chunks
+  } else {
+    // the paper's time budget: one chunk at a time, checked between chunks
+    while (st == BM_OK) {
+      st = queue_chunks(c, a, 1, -1);
+      if (st != BM_OK) break;
       if (cudaStreamSynchronize(c->stream) != cudaSuccess) { st = BM_ECUDA; break; }
       const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       if (el >= c->cfg.time_budget_s) break;
@@ -683,7 +762,12 @@ bm_status bm_fit_host(const bm_config* cfg, const float* X_host, int32_t chunks,
   if (cudaMalloc(&X, xbytes) != cudaSuccess) { rc = BM_ENOMEM; goto done; }
   if (labels_out_host && cudaMalloc(&labels, (size_t)cfg->m * 4) != cudaSuccess) { rc = BM_ENOMEM; goto done; }
   if (cudaMemcpyAsync(X, X_host, xbytes, cudaMemcpyHostToDevice, st) != cudaSuccess) { rc = BM_ECUDA; goto done; }
-  rc = bm_create(cfg, X, st, &c);
+  {
+    // a one-shot context: recording a graph would not pay for itself
+    bm_config once = *cfg;
+    once.graphs = 0;
+    rc = bm_create(&once, X, st, &c);
+  }
   if (rc != BM_OK) goto done;
   rc = bm_fit_chunk(c, chunks, report);
   if (rc != BM_OK) goto done;

@@ -15,10 +15,15 @@ __device__ __forceinline__ unsigned long long* phase_slots() {
   return slots;
 }
 
-// Thread 0 of CTA 0 adds the time since *t0 to slot i.
-__device__ __forceinline__ void phase_tick(Stats* st, int i, uint64_t* t0) {
-  (void)st;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+// Tracing is off unless the launch asks for it: a timer read on CTA 0's
+// critical path delays every CTA at the next grid barrier.
+__device__ __forceinline__ uint64_t trace_now(const ChunkArgs& a) {
+  return a.trace ? global_timer_ns() : 0ull;
+}
+
+// Thread 0 of CTA 0 adds the time since *t0 to slot i (traced launches).
+__device__ __forceinline__ void phase_tick(const ChunkArgs& a, int i, uint64_t* t0) {
+  if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) {
     const uint64_t t = global_timer_ns();
     phase_slots()[i] += t - *t0;
     *t0 = t;

@@ -641,12 +641,12 @@ __device__ bool tcc_assign(const ChunkArgs& a, const TccS& S, int r0, int nrows,
                            const TccBound& bd, uint32_t tmem, TccPipe& pp, bool update,
                            uint64_t* tsub) {
   bool ok = tcc_pass_a(a, S, r0, nrows, bd, tmem, pp);
-  phase_tick(a.stats, 8, tsub);
+  phase_tick(a, 8, tsub);
   tcc_pass_multi(a, S, r0, nrows);
   if (update) tcc_sort(a, S, nrows);
-  phase_tick(a.stats, 9, tsub);
+  phase_tick(a, 9, tsub);
   tcc_sweep(a, S, r0, nrows, update);
-  phase_tick(a.stats, 10, tsub);
+  phase_tick(a, 10, tsub);
   return ok;
 }
 
@@ -808,9 +808,9 @@ __device__ bool tcc_lloyd(const ChunkArgs& a, const TccS& S, GridBarrier& gb, in
     const double fp = dmin_sum(S.dmin, nrows, S.red);
     if (threadIdx.x == 0) FPART[b] = fp;
     nd += (long long)a.s * nlive;
-    phase_tick(a.stats, 3, tclk);
+    phase_tick(a, 3, tclk);
     if (!ok || !gb.sync()) { ok = false; break; }
-    phase_tick(a.stats, 4, tclk);
+    phase_tick(a, 4, tclk);
     if (w == 0) {
       const double t = warp_sum_array_f64(FPART, G);
       if (l == 0) s_f = t;
@@ -820,13 +820,13 @@ __device__ bool tcc_lloyd(const ChunkArgs& a, const TccS& S, GridBarrier& gb, in
     const bool stop = (f == 0.0) || (it > 0 && f_prev - f <= a.tol * f_prev) ||
                       (it == a.max_iter);
     tcc_reduce(a, S, stop);
-    phase_tick(a.stats, 5, tclk);
+    phase_tick(a, 5, tclk);
     if (!gb.sync()) { ok = false; break; }
     for (int j = threadIdx.x; j < k; j += blockDim.x)
       S.live[j] = __ldcg(reinterpret_cast<const unsigned char*>(a.mask) + j) != 0;
     build_live_list(S.live, S.lidx, k);
     if (!stop) load_norms(a, S, &bd);
-    phase_tick(a.stats, 6, tclk);
+    phase_tick(a, 6, tclk);
     if (stop) break;
     f_prev = f;
     ++it;
@@ -950,7 +950,7 @@ __global__ void __launch_bounds__(kTccThreads, 1) chunk_tc_kernel(ChunkArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *S.holder;
-  uint64_t tclk = global_timer_ns();
+  uint64_t tclk = trace_now(a);
 
   const bool full = (a.phases & kPhaseKeep) != 0;
   const bool work = (a.phases & (kPhaseKpp | kPhaseLloyd)) != 0;
@@ -973,18 +973,18 @@ __global__ void __launch_bounds__(kTccThreads, 1) chunk_tc_kernel(ChunkArgs a) {
       for (int j = threadIdx.x; j < k; j += blockDim.x) a.mask[j] = S.live[j];
     fence_proxy_async_global();
   }
-  phase_tick(a.stats, 0, &tclk);
+  phase_tick(a, 0, &tclk);
   if (a.phases & kPhaseGather) tcc_gather(a, S, r0, nrows);
   if (work) tcc_convert_own(a, S, r0, nrows);
   if (work) {
     ok = gb.sync();
     if (ok) load_norms(a, S, &bd);
   }
-  phase_tick(a.stats, 1, &tclk);
+  phase_tick(a, 1, &tclk);
   if (ok && (a.phases & kPhaseKpp)) {
     uint64_t tsub = tclk;
     ok = tcc_kpp(a, S, gb, r0, nrows, bd, tmem, pp, &nd, &tsub);
-    phase_tick(a.stats, 2, &tclk);
+    phase_tick(a, 2, &tclk);
   }
   if (ok && (a.phases & kPhaseLloyd))
     ok = tcc_lloyd(a, S, gb, r0, nrows, bd, tmem, pp, &nd, &f, &it, &tclk);
@@ -1012,7 +1012,7 @@ __global__ void __launch_bounds__(kTccThreads, 1) chunk_tc_kernel(ChunkArgs a) {
       }
       a.stats->n_d += nd;
     }
-    phase_tick(a.stats, 7, &tclk);
+    phase_tick(a, 7, &tclk);
     if (threadIdx.x == 0)
       for (int i = 0; i < kNumPhaseTimers; ++i) a.stats->phase_ns[i] += phase_slots()[i];
   }
@@ -1046,10 +1046,7 @@ cudaError_t launch_chunk_tc(const ChunkArgs& a, int grid, size_t smem, cudaStrea
   cudaError_t e = cudaFuncSetAttribute(chunk_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  ChunkArgs copy = a;
-  void* args[] = {&copy};
-  return cudaLaunchCooperativeKernel((const void*)chunk_tc_kernel, dim3(grid),
-                                     dim3(kTccThreads), args, smem, st);
+  return launch_cooperative(chunk_tc_kernel, grid, kTccThreads, smem, st, a);
 }
 
 }  // namespace bm

@@ -93,13 +93,15 @@ struct GridBarrier {
       __threadfence();
       atomicAdd(counter, 1u);
       int ok = 1;
-      const uint64_t t0 = global_timer_ns();
+      uint64_t t0 = 0;   // read lazily: a fast barrier reads no timer
       uint32_t polls = 0;
       while (ld_acquire(counter) < target) {
         ++polls;
         if ((polls & 255u) == 0) {
+          const uint64_t now = global_timer_ns();
+          if (t0 == 0) t0 = now;
           if (ld_volatile(status) != kStatusOk || polls > kSpinLimit ||
-              global_timer_ns() - t0 > kSpinTimeoutNs) {
+              now - t0 > kSpinTimeoutNs) {
             atomicCAS(status, kStatusOk, kStatusTimeout);
             ok = 0;
             break;

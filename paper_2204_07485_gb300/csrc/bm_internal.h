@@ -60,6 +60,7 @@ struct ChunkArgs {
   int trials;
   int phases;
   int bar_sel;         // which Ctl::bar counter this launch uses
+  int trace;           // 1: CTA 0 times its phases into Stats::phase_ns
   int kpad;            // k rounded up to 32 (generic path)
   int32_t* idx;        // s
   float* P;            // s x npad
@@ -187,6 +188,24 @@ __host__ __device__ inline ChunkSmem chunk_smem(int npad, int k, int kpad, int R
   L.red = o;   o += 80 * 8;
   L.total = o;
   return L;
+}
+
+// Cooperative launch (all CTAs co-resident, as the grid barriers need) through
+// the launch-attribute API, which stream capture records into a graph.
+template <typename Kernel>
+inline cudaError_t launch_cooperative(Kernel fn, int grid, int threads, size_t smem,
+                                      cudaStream_t st, const ChunkArgs& a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, a);
 }
 
 // Host-side launch helpers (bm_kernels.cu, bm_sample.cu, bm_tc.cu).

@@ -384,7 +384,7 @@ __device__ void lloyd_own_rows(const ChunkArgs& a, const Smem& S,
                                const ChunkSmem& L, int r0, int nrows, int G) {
   const int k = a.k, n = a.n, npad = a.npad, b = blockIdx.x;
   if constexpr (!GENERIC) {
-    uint64_t tsub = global_timer_ns();
+    uint64_t tsub = trace_now(a);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
     // member counts: in the update slices' spare lane 31 when n < 32,
     // otherwise per warp by ballot during the assignment
@@ -412,7 +412,7 @@ __device__ void lloyd_own_rows(const ChunkArgs& a, const Smem& S,
       }
     }
     __syncthreads();
-    phase_tick(a.stats, 8, &tsub);
+    phase_tick(a, 8, &tsub);
     for (int fs = 0; fs < n; fs += 32) {
       if (w < L.wu) {
         float* my = S.sw + w * k * 32;
@@ -473,7 +473,7 @@ __device__ void lloyd_own_rows(const ChunkArgs& a, const Smem& S,
         }
       }
       __syncthreads();
-      phase_tick(a.stats, 9, &tsub);
+      phase_tick(a, 9, &tsub);
       for (int q = threadIdx.x; q < k * 32; q += blockDim.x) {
         const int j = q >> 5, f = fs + (q & 31);
         if (f < n) {
@@ -492,7 +492,7 @@ __device__ void lloyd_own_rows(const ChunkArgs& a, const Smem& S,
           a.part_cnt[(size_t)j * G + b] = c;
         }
       __syncthreads();
-      phase_tick(a.stats, 10, &tsub);
+      phase_tick(a, 10, &tsub);
     }
   } else {
     const int ng = L.wu;
@@ -712,9 +712,9 @@ __device__ bool phase_lloyd(const ChunkArgs& a, const Smem& S,
     const double fp = own_dmin_sum(S, nrows);
     if (threadIdx.x == 0) FPART[b] = fp;
     nd += (long long)a.s * nlive;
-    phase_tick(a.stats, 3, tclk);
+    phase_tick(a, 3, tclk);
     if (!gb.sync()) return false;
-    phase_tick(a.stats, 4, tclk);
+    phase_tick(a, 4, tclk);
     if (w == 0) {
       const double t = warp_sum_array_f64(FPART, G);
       if (l == 0) s_f = t;
@@ -747,7 +747,7 @@ __device__ bool phase_lloyd(const ChunkArgs& a, const Smem& S,
         a.C[(size_t)j * npad + ff] = c + sum / (float)cnt;
       }
     }
-    phase_tick(a.stats, 5, tclk);
+    phase_tick(a, 5, tclk);
     if (!gb.sync()) return false;
     for (int j = threadIdx.x; j < k; j += blockDim.x)
       S.live[j] = __ldcg(reinterpret_cast<const unsigned char*>(a.mask) + j) != 0;
@@ -759,7 +759,7 @@ __device__ bool phase_lloyd(const ChunkArgs& a, const Smem& S,
       }
     }
     __syncthreads();
-    phase_tick(a.stats, 6, tclk);
+    phase_tick(a, 6, tclk);
     if (stop) break;
     f_prev = f;
     ++it;
@@ -787,7 +787,7 @@ chunk_kernel(ChunkArgs a) {
   bool ok = true;
 
   if (threadIdx.x < kNumPhaseTimers) phase_slots()[threadIdx.x] = 0ull;
-  uint64_t tclk = global_timer_ns();
+  uint64_t tclk = trace_now(a);
   const bool full = (a.phases & kPhaseKeep) != 0;
   if (a.phases & (kPhaseKpp | kPhaseLloyd)) {
     // C' <- C (Alg. 1): the working copy starts from the incumbent.
@@ -801,20 +801,20 @@ chunk_kernel(ChunkArgs a) {
       for (int j = threadIdx.x; j < a.k; j += blockDim.x) a.mask[j] = S.live[j];
     }
   }
-  phase_tick(a.stats, 0, &tclk);
+  phase_tick(a, 0, &tclk);
   if (ok && (a.phases & kPhaseGather)) {
     phase_gather<NP, GENERIC>(a, S, r0, nrows);
     // Only K-means++ reads sample rows gathered by other CTAs; Lloyd reads
     // its own rows, so without a reseed no grid barrier is needed here.
     const bool reseed = (a.phases & kPhaseKpp) && S.lidx[a.k] < a.k;
     if (reseed) ok = gb.sync();
-    phase_tick(a.stats, 1, &tclk);
+    phase_tick(a, 1, &tclk);
   } else if (a.phases & (kPhaseKpp | kPhaseLloyd)) {
     if constexpr (!GENERIC) stage_own_rows<NP>(a, S, r0, nrows);   // P written by the host
   }
   if (ok && (a.phases & kPhaseKpp)) {
     ok = phase_kpp<NP, GENERIC>(a, S, gb, r0, nrows, &nd);
-    phase_tick(a.stats, 2, &tclk);
+    phase_tick(a, 2, &tclk);
   }
   if (ok && (a.phases & kPhaseLloyd))
     ok = phase_lloyd<NP, GENERIC>(a, S, L, gb, r0, nrows, &nd, &f, &it, &tclk);
@@ -843,7 +843,7 @@ chunk_kernel(ChunkArgs a) {
       }
       a.stats->n_d += nd;
     }
-    phase_tick(a.stats, 7, &tclk);
+    phase_tick(a, 7, &tclk);
     if (threadIdx.x == 0)
       for (int i = 0; i < kNumPhaseTimers; ++i) a.stats->phase_ns[i] += phase_slots()[i];
   }
@@ -941,10 +941,7 @@ static cudaError_t launch_chunk_t(const ChunkArgs& a, int grid, size_t smem,
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  ChunkArgs copy = a;
-  void* args[] = {&copy};
-  return cudaLaunchCooperativeKernel((const void*)fn, dim3(grid),
-                                     dim3(chunk_threads(GENERIC)), args, smem, st);
+  return launch_cooperative(fn, grid, chunk_threads(GENERIC), smem, st, a);
 }
 
 template <int NP, bool GENERIC>

@@ -69,3 +69,4 @@ def test_config_defaults_follow_the_paper():
     import paper_2204_07485_gb300 as bm
     cfg = bm.bm_config_default()
     assert cfg.max_iter == 300 and cfg.tol == 1e-4 and cfg.kpp_trials == 3
+    assert cfg.graphs == 1
