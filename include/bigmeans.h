@@ -248,6 +248,87 @@ bm_status bm_assign_rows_noalloc(const float* X_dev, int64_t m, int32_t n,
                                  float* dmin_dev, double* sse_out,
                                  void* stream);
 
+/* ------------------------------------------------------------------ serving
+ * A job server runs whole Big-means jobs (Alg. 1: `chunks` chunks, then the
+ * final assignment) submitted from any thread, several at a time on one GPU.
+ * Each worker thread owns a CUDA stream; a job's device state comes from a
+ * stream-ordered memory pool the server owns, so jobs allocate and free
+ * without synchronising the device.  The paper runs one job at a time; the
+ * server adds admission control and request latency on top of the same
+ * kernels, and a job's results do not depend on what else is running (every
+ * reduction has a fixed order). */
+typedef struct bm_server bm_server;
+
+typedef struct bm_server_config {
+  int32_t workers;        /* jobs run at once (threads, each with a stream), >= 1 */
+  int64_t memory_budget;  /* device bytes the admitted jobs' state may hold at
+                             once; 0 = half the device memory free at creation  */
+  int32_t max_queue;      /* admitted jobs waiting for a worker (>= 1)          */
+} bm_server_config;
+
+/* What a finished job produced (and how long it took on the host clock). */
+typedef struct bm_job_result {
+  int32_t status;         /* bm_status of the job; BM_ECANCELLED if the server
+                             shut down before it started                         */
+  double sse;             /* f(C, X) of the final assignment, float64            */
+  double f_opt;           /* incumbent sample objective                           */
+  int64_t lloyd_iters;    /* Lloyd update steps over all chunks                   */
+  int64_t accepted;       /* chunks that replaced the incumbent                   */
+  double queued_s;        /* submission -> a worker starts it                    */
+  double run_s;           /* start -> results ready                              */
+  double latency_s;       /* submission -> results ready                         */
+} bm_job_result;
+
+typedef void (*bm_job_callback)(uint64_t ticket, const bm_job_result* result, void* user);
+
+/* One job.  X_dev (m x n, device) and the output buffers are borrowed until
+ * the job completes; any output may be NULL. */
+typedef struct bm_job {
+  bm_config cfg;              /* sizes, stop rule, seed, precision (graphs ignored) */
+  const float* X_dev;
+  int32_t chunks;             /* chunks to run, > 0                                */
+  int32_t* labels_dev;        /* m labels of the final assignment (device)         */
+  float* C_out_host;          /* k x n incumbent centroids (host)                   */
+  uint8_t* mask_out_host;     /* k live flags (host)                                */
+  bm_job_callback callback;   /* called from a worker thread when the job ends     */
+  void* user;
+} bm_job;
+
+/* Counters of a server. */
+typedef struct bm_server_stats {
+  int64_t submitted, completed, failed, cancelled;
+  int64_t rejected_busy, rejected_memory;
+  int64_t queued, running;
+  int64_t memory_in_use, memory_budget;
+} bm_server_stats;
+
+/* Starts `workers` worker threads on the current device. */
+bm_status bm_server_create(const bm_server_config* cfg, bm_server** out);
+
+/* Stops accepting jobs, cancels the queued ones (their result status is
+ * BM_ECANCELLED and their callbacks run), waits for the running ones, joins
+ * the workers and frees the pool.  NULL is a no-op. */
+bm_status bm_server_destroy(bm_server* server);
+
+/* Admits a job and returns its ticket; thread-safe.  BM_EINVAL: bad
+ * arguments or shapes; BM_EUNSUPPORTED: a shape no kernel handles; BM_ENOMEM:
+ * the job alone needs more than the memory budget; BM_EBUSY: the queue is
+ * full; BM_ECANCELLED: the server is shutting down.  An admitted job waits
+ * (first in, first out) until a worker is free and its state fits in what
+ * the running jobs leave of the budget. */
+bm_status bm_submit(bm_server* server, const bm_job* job, uint64_t* ticket);
+
+/* Waits up to timeout_s seconds (< 0: no limit) for the job's result.
+ * BM_ETIMEOUT when it is still pending (the ticket stays valid); BM_OK with
+ * *out filled, after which the ticket is gone.  Jobs submitted with a
+ * callback hand their result to the callback instead and are gone once it
+ * returns; waiting for them returns BM_EINVAL after that.  A bad ticket
+ * returns BM_EINVAL. */
+bm_status bm_wait(bm_server* server, uint64_t ticket, double timeout_s, bm_job_result* out);
+
+/* Snapshot of the server's counters. */
+bm_status bm_server_stats_get(bm_server* server, bm_server_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

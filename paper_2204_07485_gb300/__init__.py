@@ -44,6 +44,41 @@ class bm_fit_report(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class bm_server_config(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("memory_budget", ctypes.c_int64),
+                ("max_queue", ctypes.c_int32)]
+
+
+class bm_job_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("sse", ctypes.c_double),
+                ("f_opt", ctypes.c_double), ("lloyd_iters", ctypes.c_int64),
+                ("accepted", ctypes.c_int64), ("queued_s", ctypes.c_double),
+                ("run_s", ctypes.c_double), ("latency_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+bm_job_callback = ctypes.CFUNCTYPE(None, ctypes.c_uint64, ctypes.POINTER(bm_job_result),
+                                   ctypes.c_void_p)
+
+
+class bm_job(ctypes.Structure):
+    _fields_ = [("cfg", bm_config), ("X_dev", ctypes.c_void_p), ("chunks", ctypes.c_int32),
+                ("labels_dev", ctypes.c_void_p), ("C_out_host", ctypes.c_void_p),
+                ("mask_out_host", ctypes.c_void_p), ("callback", bm_job_callback),
+                ("user", ctypes.c_void_p)]
+
+
+class bm_server_stats_t(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in
+                ("submitted", "completed", "failed", "cancelled", "rejected_busy",
+                 "rejected_memory", "queued", "running", "memory_in_use", "memory_budget")]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class BigMeansError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -78,6 +113,11 @@ _SIGS = {
                                    _P(_dbl), _P(ctypes.c_uint64), _vp]),
     "bm_assign_rows_noalloc": (_i32, [_vp, _i64, _i32, _vp, _vp, _i32, _vp, _vp,
                                       _P(_dbl), _vp]),
+    "bm_server_create": (_i32, [_P(bm_server_config), _P(_vp)]),
+    "bm_server_destroy": (_i32, [_vp]),
+    "bm_submit": (_i32, [_vp, _P(bm_job), _P(ctypes.c_uint64)]),
+    "bm_wait": (_i32, [_vp, ctypes.c_uint64, _dbl, _P(bm_job_result)]),
+    "bm_server_stats_get": (_i32, [_vp, _P(bm_server_stats_t)]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -253,3 +293,62 @@ def bm_assign_rows_noalloc(X_dev, m, n, C_dev, mask_dev, k, labels_dev=None,
                                        _stream(stream)),
            "bm_assign_rows_noalloc")
     return sse.value
+
+
+# ------------------------------------------------------------------ serving
+_callbacks = {}   # ticket -> ctypes callback object, alive until the job ends
+
+
+def bm_server_create(workers=2, memory_budget=0, max_queue=256):
+    cfg = bm_server_config(int(workers), int(memory_budget), int(max_queue))
+    sv = _vp()
+    _check(_lib.bm_server_create(ctypes.byref(cfg), ctypes.byref(sv)), "bm_server_create")
+    return sv.value
+
+
+def bm_server_destroy(server):
+    _check(_lib.bm_server_destroy(server), "bm_server_destroy")
+
+
+def bm_submit(server, cfg, X_dev, chunks, labels_dev=None, C_out_host=None,
+              mask_out_host=None, callback=None):
+    """Admits a job; returns its ticket.  callback(ticket, result_dict) runs on
+    a worker thread when the job ends."""
+    job = bm_job()
+    job.cfg = cfg
+    job.X_dev = _ptr(X_dev)
+    job.chunks = int(chunks)
+    job.labels_dev = _ptr(labels_dev)
+    job.C_out_host = _ptr(C_out_host)
+    job.mask_out_host = _ptr(mask_out_host)
+    holder = None
+    if callback is not None:
+        def _cb(ticket, res, user, _f=callback):
+            try:
+                _f(int(ticket), res.contents.as_dict())
+            finally:
+                _callbacks.pop(int(ticket), None)
+        holder = bm_job_callback(_cb)
+        job.callback = holder
+    ticket = ctypes.c_uint64()
+    _check(_lib.bm_submit(server, ctypes.byref(job), ctypes.byref(ticket)), "bm_submit")
+    if holder is not None:
+        _callbacks.setdefault(ticket.value, holder)
+    return ticket.value
+
+
+def bm_wait(server, ticket, timeout=-1.0):
+    """The job's result as a dict, or None if it is still pending after
+    `timeout` seconds (< 0: no limit)."""
+    res = bm_job_result()
+    st = _lib.bm_wait(server, ctypes.c_uint64(ticket), float(timeout), ctypes.byref(res))
+    if st == BM_ETIMEOUT:
+        return None
+    _check(st, "bm_wait")
+    return res.as_dict()
+
+
+def bm_server_stats(server):
+    out = bm_server_stats_t()
+    _check(_lib.bm_server_stats_get(server, ctypes.byref(out)), "bm_server_stats_get")
+    return out.as_dict()

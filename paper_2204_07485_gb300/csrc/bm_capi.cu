@@ -172,18 +172,31 @@ struct Workspace {
   float* sqs = nullptr;         // squared norms of 8-feature slices,
   unsigned char* Pb = nullptr;  // own-row BF16 planes
   std::vector<void*> owned;
+  // allocation source: cudaMalloc, or a stream-ordered memory pool (serving:
+  // no device-wide synchronisation per job, memory reused across jobs)
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t pool_stream = nullptr;
+  bool dry = false;     // only add up the bytes (footprint estimate)
+  size_t bytes = 0;
 
   template <typename T>
   cudaError_t alloc(T** p, size_t count) {
+    const size_t b = std::max<size_t>(count * sizeof(T), 16);
+    bytes += (b + 511) / 512 * 512;
+    if (dry) { *p = nullptr; return cudaSuccess; }
     void* v = nullptr;
-    cudaError_t e = cudaMalloc(&v, std::max<size_t>(count * sizeof(T), 16));
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&v, b, pool, pool_stream)
+                               : cudaMalloc(&v, b);
     if (e != cudaSuccess) return e;
     owned.push_back(v);
     *p = static_cast<T*>(v);
     return cudaSuccess;
   }
   void release() {
-    for (void* v : owned) cudaFree(v);
+    for (void* v : owned) {
+      if (pool) cudaFreeAsync(v, pool_stream);
+      else cudaFree(v);
+    }
     owned.clear();
   }
 };
@@ -229,6 +242,7 @@ static bm_status ws_create(Workspace* w, long long m, int k, long long s,
     BM_TRY(w->alloc(&w->Pb, (size_t)p.grid * p.tc_tpc * p.tc_kb * 32768));
   }
 #undef BM_TRY
+  if (w->dry) return BM_OK;
   if (p.tc) cudaMemsetAsync(w->Cb, 0, cb_bytes, st);
   cudaMemsetAsync(w->bitmap, 0, words * 4 * plan_cap, st);
   cudaMemsetAsync(w->C, 0, (size_t)k * p.npad * 4, st);
@@ -323,6 +337,62 @@ struct bm_ctx {
 
 static constexpr size_t kMaxGraphs = 4;
 
+namespace bm {
+
+static bm_status check_config(const bm_config* cfg) {
+  if (!shape_ok(cfg->m, cfg->n, cfg->k, cfg->s)) return BM_EINVAL;
+  if (cfg->kpp_trials < 1 || cfg->kpp_trials > kMaxTrials || cfg->max_iter < 0 ||
+      !(cfg->tol >= 0.0))
+    return BM_EINVAL;
+  if (cfg->precision != BM_FP32 && cfg->precision != BM_BF16_RESCORE &&
+      cfg->precision != BM_BF16X3_RESCORE)
+    return BM_EUNSUPPORTED;
+  return BM_OK;
+}
+
+static bool wants_tc(const bm_config* cfg) {
+  return cfg->precision == BM_BF16_RESCORE || cfg->precision == BM_BF16X3_RESCORE;
+}
+
+bm_status ctx_create(const bm_config* cfg, const float* X_dev, cudaStream_t stream,
+                     cudaMemPool_t pool, bm_ctx** out) {
+  if (!cfg || !out || !X_dev) return BM_EINVAL;
+  *out = nullptr;
+  bm_status st = check_config(cfg);
+  if (st != BM_OK) return st;
+  bm_ctx* c = new (std::nothrow) bm_ctx();
+  if (!c) return BM_ENOMEM;
+  c->cfg = *cfg;
+  c->X = X_dev;
+  c->stream = stream;
+  st = make_plan(cfg->n, cfg->k, cfg->s, &c->plan, wants_tc(cfg));
+  if (st != BM_OK) { delete c; return st; }
+  c->ws.pool = pool;
+  c->ws.pool_stream = stream;
+  st = ws_create(&c->ws, cfg->m, cfg->k, cfg->s, c->plan, c->stream,
+                 plan_capacity(cfg->m, cfg->s), cfg->m);
+  if (st != BM_OK) { delete c; return st; }
+  *out = c;
+  return BM_OK;
+}
+
+bm_status ctx_footprint(const bm_config* cfg, size_t* bytes) {
+  if (!cfg || !bytes) return BM_EINVAL;
+  bm_status st = check_config(cfg);
+  if (st != BM_OK) return st;
+  Plan p;
+  st = make_plan(cfg->n, cfg->k, cfg->s, &p, wants_tc(cfg));
+  if (st != BM_OK) return st;
+  Workspace w;
+  w.dry = true;
+  st = ws_create(&w, cfg->m, cfg->k, cfg->s, p, nullptr, plan_capacity(cfg->m, cfg->s), cfg->m);
+  if (st != BM_OK) return st;
+  *bytes = w.bytes;
+  return BM_OK;
+}
+
+}  // namespace bm
+
 extern "C" {
 
 void bm_config_default(bm_config* cfg) {
@@ -354,28 +424,7 @@ const char* bm_status_string(int32_t s) {
 
 bm_status bm_create(const bm_config* cfg, const float* X_dev, void* stream,
                     bm_ctx** out) {
-  if (!cfg || !out || !X_dev) return BM_EINVAL;
-  *out = nullptr;
-  if (!shape_ok(cfg->m, cfg->n, cfg->k, cfg->s)) return BM_EINVAL;
-  if (cfg->kpp_trials < 1 || cfg->kpp_trials > kMaxTrials || cfg->max_iter < 0 ||
-      !(cfg->tol >= 0.0))
-    return BM_EINVAL;
-  if (cfg->precision != BM_FP32 && cfg->precision != BM_BF16_RESCORE &&
-      cfg->precision != BM_BF16X3_RESCORE)
-    return BM_EUNSUPPORTED;
-  bm_ctx* c = new (std::nothrow) bm_ctx();
-  if (!c) return BM_ENOMEM;
-  c->cfg = *cfg;
-  c->X = X_dev;
-  c->stream = static_cast<cudaStream_t>(stream);
-  const bool tc = cfg->precision == BM_BF16_RESCORE || cfg->precision == BM_BF16X3_RESCORE;
-  bm_status st = make_plan(cfg->n, cfg->k, cfg->s, &c->plan, tc);
-  if (st != BM_OK) { delete c; return st; }
-  st = ws_create(&c->ws, cfg->m, cfg->k, cfg->s, c->plan, c->stream,
-                 plan_capacity(cfg->m, cfg->s), cfg->m);
-  if (st != BM_OK) { delete c; return st; }
-  *out = c;
-  return BM_OK;
+  return bm::ctx_create(cfg, X_dev, static_cast<cudaStream_t>(stream), nullptr, out);
 }
 
 bm_status bm_destroy(bm_ctx* c) {

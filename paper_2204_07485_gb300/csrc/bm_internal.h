@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/bigmeans.h"
+
 namespace bm {
 
 constexpr int kMaxTrials = 4;      // K-means++ candidates per centre (paper: 3)
@@ -227,4 +229,13 @@ cudaError_t launch_assign(const AssignArgs& a, int grid, bool generic, int np,
 int assign_max_grid(bool generic, int np, size_t smem);
 size_t assign_smem(int npad, int k, int kpad, bool generic);
 
+}  // namespace bm
+
+// Context construction shared by bm_create and the job server: allocations
+// from `pool` (stream-ordered on `stream`) when it is not null; and the
+// device bytes a context for cfg would hold.
+namespace bm {
+bm_status ctx_create(const bm_config* cfg, const float* X_dev, cudaStream_t stream,
+                     cudaMemPool_t pool, bm_ctx** out);
+bm_status ctx_footprint(const bm_config* cfg, size_t* bytes);
 }  // namespace bm

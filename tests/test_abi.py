@@ -70,3 +70,15 @@ def test_config_defaults_follow_the_paper():
     cfg = bm.bm_config_default()
     assert cfg.max_iter == 300 and cfg.tol == 1e-4 and cfg.kpp_trials == 3
     assert cfg.graphs == 1
+
+
+def test_server_entry_points_validate_without_a_device():
+    _ensure_built()
+    import paper_2204_07485_gb300 as bm
+    cfg = bm.bm_server_config(0, 0, 1)
+    sv = bm._vp()
+    assert bm._lib.bm_server_create(bm.ctypes.byref(cfg), bm.ctypes.byref(sv)) == bm.BM_EINVAL
+    assert bm._lib.bm_server_destroy(None) == bm.BM_OK
+    assert bm._lib.bm_submit(None, None, None) == bm.BM_EINVAL
+    assert bm._lib.bm_wait(None, 1, 0.0, None) == bm.BM_EINVAL
+    assert bm._lib.bm_server_stats_get(None, None) == bm.BM_EINVAL
