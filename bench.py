@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--chunks", type=int, default=WORKLOAD["chunks"])
     return ap.parse_args()
 
@@ -276,6 +277,127 @@ def launch_latency(bm, torch, dev, jobs=10, warmup=3):
     return out
 
 
+# 100 jobs/s: below the measured capacity of this mix on one GB300 (about
+# 117 jobs/s with 4 workers), so latency reflects service, not an
+# ever-growing queue
+SERVING = dict(requests=1000, rate=100.0, chunks=20, workers=4, seed=0,
+               n_set=(8, 28, 68, 128, 384), m_range=(1e4, 5e6), k_range=(2, 100),
+               s_max=50_000)
+
+
+def serving(bm, torch, dev, spec=SERVING):
+    """Poisson arrivals of whole jobs (m log-uniform, n from the set, k
+    uniform, s = min(m, 50k), FP32 or split-BF16 by a fair coin, 20 chunks +
+    final assignment), each job's data synthesized on the device from (seed,
+    job id) just before it is submitted.  Latency = submission -> results
+    ready, on the server's clock."""
+    rng = np.random.default_rng(spec["seed"])
+    R = spec["requests"]
+    gaps = rng.exponential(1.0 / spec["rate"], size=R)
+    arrive = np.cumsum(gaps)
+    lo, hi = np.log(spec["m_range"][0]), np.log(spec["m_range"][1])
+    ms = np.exp(rng.uniform(lo, hi, size=R)).astype(np.int64)
+    ns = rng.choice(spec["n_set"], size=R)
+    ks = rng.integers(spec["k_range"][0], spec["k_range"][1] + 1, size=R)
+    precs = np.where(rng.random(R) < 0.5, bm.BM_FP32, bm.BM_BF16X3_RESCORE)
+    # data: one seeded 100-component mixture per n, synthesized on the device
+    # before the clock starts; job j reads m rows of it from a seeded offset
+    import bminputs
+    max_off = 1 << 16
+    offs = rng.integers(0, max_off, size=R)
+    pools = {}
+    for n in spec["n_set"]:
+        sel = ns == n
+        if sel.any():
+            pools[int(n)] = bminputs.mixtures.isotropic_blobs_device(
+                int(ms[sel].max()) + max_off, int(n), 100, spec["seed"] + int(n), device=dev)
+    torch.cuda.synchronize(dev)
+    sv = bm.bm_server_create(workers=spec["workers"])
+    pending = {}            # ticket -> (job id, X kept alive until the job ends)
+    results = [None] * R
+    submit_t = np.zeros(R)
+    lock = threading.Lock()
+    finished = threading.Event()
+    count = [0]
+
+    def on_done(ticket, res):
+        with lock:
+            jid, _ = pending.pop(ticket)
+            results[jid] = res
+            count[0] += 1
+            if count[0] == R:
+                finished.set()
+
+    t0 = time.perf_counter()
+    try:
+        for j in range(R):
+            delay = arrive[j] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            m, n, k = int(ms[j]), int(ns[j]), int(ks[j])
+            X = pools[n][int(offs[j]):int(offs[j]) + m]
+            cfg = bm.bm_config_default(m=m, n=n, k=k, s=min(m, spec["s_max"]), seed=j,
+                                       precision=int(precs[j]))
+            with lock:
+                submit_t[j] = time.perf_counter() - t0
+                try:
+                    ticket = bm.bm_submit(sv, cfg, X, spec["chunks"], callback=on_done)
+                except bm.BigMeansError as e:   # refused at admission
+                    results[j] = {"status": e.status}
+                    count[0] += 1
+                    continue
+                pending[ticket] = (j, X)
+        if count[0] == R:
+            finished.set()
+        finished.wait(600.0)
+        wall = time.perf_counter() - t0
+        stats = bm.bm_server_stats(sv)
+    finally:
+        bm.bm_server_destroy(sv)
+    del pools
+    done = [r for r in results if r is not None]
+    ok = [r for r in done if r["status"] == 0]
+    failures = [{"m": int(ms[j]), "n": int(ns[j]), "k": int(ks[j]), "precision": int(precs[j]),
+                 "status": r["status"]} for j, r in enumerate(results)
+                if r is not None and r["status"] != 0][:10]
+    lat = np.array([r["latency_s"] for r in ok]) * 1e3
+    que = np.array([r["queued_s"] for r in ok]) * 1e3
+
+    def pct(a, q):
+        return float(np.percentile(a, q)) if len(a) else None
+
+    by_prec = {}
+    for name, code in (("fp32", bm.BM_FP32), ("bf16x3", bm.BM_BF16X3_RESCORE)):
+        sel = [r["latency_s"] * 1e3 for j, r in enumerate(results)
+               if r is not None and r["status"] == 0 and precs[j] == code]
+        by_prec[name] = {"jobs": len(sel), "p50_ms": pct(sel, 50), "p99_ms": pct(sel, 99)}
+    by_n = {}
+    for nv in spec["n_set"]:
+        for name, code in (("fp32", bm.BM_FP32), ("bf16x3", bm.BM_BF16X3_RESCORE)):
+            sel = [(r["run_s"] * 1e3, ms[j]) for j, r in enumerate(results)
+                   if r is not None and r["status"] == 0 and ns[j] == nv and precs[j] == code]
+            if sel:
+                by_n["n%d_%s" % (nv, name)] = {
+                    "jobs": len(sel), "run_ms_mean": float(np.mean([a for a, _ in sel])),
+                    "run_ms_max": float(np.max([a for a, _ in sel])),
+                    "mean_m": float(np.mean([b for _, b in sel]))}
+    return {"workload": "poisson_%d_per_s_%d_jobs_mixed_shapes" % (spec["rate"], R),
+            "run_by_shape": by_n,
+            "requests": R, "offered_rps": spec["rate"],
+            "submitted_rps": R / max(submit_t[-1], 1e-9), "completed": len(ok),
+            "failed": len(done) - len(ok), "wall_s": wall, "jobs_per_s": len(ok) / wall,
+            "latency_ms": {"p50": pct(lat, 50), "p90": pct(lat, 90), "p99": pct(lat, 99),
+                           "mean": float(lat.mean()) if len(lat) else None,
+                           "max": float(lat.max()) if len(lat) else None},
+            "queue_ms": {"p50": pct(que, 50), "p99": pct(que, 99)},
+            "by_precision": by_prec, "failures": failures,
+            "workers": spec["workers"], "chunks": spec["chunks"],
+            "server": stats,
+            "data": "one seeded 100-component isotropic mixture per n, synthesized on "
+                    "the device before the clock starts; job j reads m rows from a "
+                    "seeded offset"}
+
+
 def run_ours(args, wl):
     import torch
     rank, world, local = dist_env()
@@ -430,6 +552,8 @@ def run_ours(args, wl):
         del Xg
     if rank == 0 and not args.no_precision:
         out["launch_latency"] = launch_latency(bm, torch, dev)
+    if rank == 0 and not args.no_serving:
+        out["serving"] = serving(bm, torch, dev)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(X, wl, CPU_SAMPLE_CHUNKS)
     if rank == 0:

@@ -76,6 +76,9 @@ typedef struct bm_config {
                            0: launches one kernel at a time                    */
   int32_t trace;        /* 1: the chunk kernel times its phases (bm_trace);
                            costs a timer read per phase on CTA 0               */
+  int32_t max_ctas;     /* > 0: at most this many CTAs per chunk launch (and
+                           SMs' worth of final-assignment CTAs), leaving the
+                           other SMs to concurrent jobs; 0: no cap             */
 } bm_config;
 
 /* What one bm_fit_chunk call did. */
@@ -92,7 +95,8 @@ typedef struct bm_fit_report {
 typedef struct bm_ctx bm_ctx;
 
 /* Fills *cfg with the paper's defaults (max_iter 300, tol 1e-4, 3 trials,
- * FP32, seed 0), graph replay on, phase tracing off, and zero sizes. */
+ * FP32, seed 0), graph replay on, phase tracing off, no CTA cap, and zero
+ * sizes. */
 void bm_config_default(bm_config* cfg);
 
 /* Human-readable name of a status code (static string). */
@@ -284,7 +288,8 @@ typedef void (*bm_job_callback)(uint64_t ticket, const bm_job_result* result, vo
 /* One job.  X_dev (m x n, device) and the output buffers are borrowed until
  * the job completes; any output may be NULL. */
 typedef struct bm_job {
-  bm_config cfg;              /* sizes, stop rule, seed, precision (graphs ignored) */
+  bm_config cfg;              /* sizes, stop rule, seed, precision (graphs ignored;
+                                 max_ctas = 0 means SMs / workers)                 */
   const float* X_dev;
   int32_t chunks;             /* chunks to run, > 0                                */
   int32_t* labels_dev;        /* m labels of the final assignment (device)         */

@@ -31,7 +31,7 @@ class bm_config(ctypes.Structure):
                 ("tol", ctypes.c_double), ("kpp_trials", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
                 ("time_budget_s", ctypes.c_double), ("graphs", ctypes.c_int32),
-                ("trace", ctypes.c_int32)]
+                ("trace", ctypes.c_int32), ("max_ctas", ctypes.c_int32)]
 
 
 class bm_fit_report(ctypes.Structure):

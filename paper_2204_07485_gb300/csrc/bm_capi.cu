@@ -34,13 +34,21 @@ struct Plan {
   int agrid = 0;     // CTAs of the FP32 assign kernel (0: tensor cores only)
   size_t asmem = 0;
   int tc_kb = 0, tc_n16 = 0, tc_ncols = 0, tc_fb = 0, tc_ns = 0, tc_tpc = 0;
+  int cap = 0;       // CTA cap of the job (bm_config.max_ctas), 0 = none
 };
 
 static constexpr size_t kSmemLimit = 227 * 1024;
 
+static int sm_count() {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
 // Tensor-core chunk plan: one CTA per SM (TMEM, grid barrier), at least one
 // 128-row tile per CTA, the widest staged feature block that fits.
-static bm_status make_plan_tc(int n, int k, long long s, Plan* out) {
+static bm_status make_plan_tc(int n, int k, long long s, Plan* out, int cap) {
   if (k > kMaxK || n > 512) return BM_EUNSUPPORTED;
   Plan p;
   p.tc = true;
@@ -55,7 +63,9 @@ static bm_status make_plan_tc(int n, int k, long long s, Plan* out) {
   if (cudaGetDevice(&dev) != cudaSuccess) return BM_ECUDA;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int grid = (int)std::max<long long>(1, std::min<long long>((s + 127) / 128, sms));
-  for (int iter = 0; iter < 4 && p.grid == 0; ++iter) {
+  if (cap > 0) grid = std::min(grid, cap);
+  p.cap = cap;
+  for (int iter = 0; iter < 16 && p.grid == 0; ++iter) {
     const int R = (int)((s + grid - 1) / grid);
     size_t smem = 0;
     int fb = 0, ns = 0;
@@ -67,7 +77,11 @@ static bm_status make_plan_tc(int n, int k, long long s, Plan* out) {
       }
       if (fb) break;
     }
-    if (fb == 0) return BM_EUNSUPPORTED;   // sample too large per SM
+    if (fb == 0) {   // too many rows per CTA: more CTAs, past the cap if need be
+      if (grid >= sms) return BM_EUNSUPPORTED;
+      grid = std::min(grid * 2, sms);
+      continue;
+    }
     const int maxg = chunk_tc_max_grid(smem);
     if (maxg <= 0) return BM_EUNSUPPORTED;
     if (grid > maxg) { grid = maxg; continue; }
@@ -86,19 +100,21 @@ static bm_status make_plan_tc(int n, int k, long long s, Plan* out) {
   return BM_OK;
 }
 
-static bm_status make_plan_simt(int n, int k, long long s, Plan* out);
+static bm_status make_plan_simt(int n, int k, long long s, Plan* out, int cap);
 
 // Kernel family for (n, k, s): the row-in-register path for n <= 32; for
 // wider rows the tensor-core path when asked for (tc) or when the FP32
 // tables do not fit in shared memory, else the tiled FP32 path.
-static bm_status make_plan(int n, int k, long long s, Plan* out, bool tc = false) {
-  if (n > kNpMax && tc) return make_plan_tc(n, k, s, out);
-  const bm_status st = make_plan_simt(n, k, s, out);
-  if (st == BM_EUNSUPPORTED && n > kNpMax) return make_plan_tc(n, k, s, out);
+// cap > 0 limits the CTAs of a chunk launch (the job then leaves the other
+// SMs to concurrent jobs); it gives way where shared memory needs more CTAs.
+static bm_status make_plan(int n, int k, long long s, Plan* out, bool tc = false, int cap = 0) {
+  if (n > kNpMax && tc) return make_plan_tc(n, k, s, out, cap);
+  const bm_status st = make_plan_simt(n, k, s, out, cap);
+  if (st == BM_EUNSUPPORTED && n > kNpMax) return make_plan_tc(n, k, s, out, cap);
   return st;
 }
 
-static bm_status make_plan_simt(int n, int k, long long s, Plan* out) {
+static bm_status make_plan_simt(int n, int k, long long s, Plan* out, int cap) {
   Plan p;
   if (k > kMaxK) return BM_EUNSUPPORTED;
   if (n <= kNpMax) {
@@ -121,7 +137,9 @@ static bm_status make_plan_simt(int n, int k, long long s, Plan* out) {
   // grid barrier.
   const int rows_target = p.generic ? 256 : 64;
   int grid = (int)std::min<long long>((s + rows_target - 1) / rows_target, (long long)sms);
+  if (cap > 0) grid = std::min(grid, cap);
   grid = std::max(grid, 1);
+  p.cap = cap;
   for (int iter = 0; iter < 8; ++iter) {
     const int R = (int)((s + grid - 1) / grid);
     const ChunkSmem L = chunk_smem(p.npad, k, p.kpad, R, p.generic);
@@ -365,7 +383,7 @@ bm_status ctx_create(const bm_config* cfg, const float* X_dev, cudaStream_t stre
   c->cfg = *cfg;
   c->X = X_dev;
   c->stream = stream;
-  st = make_plan(cfg->n, cfg->k, cfg->s, &c->plan, wants_tc(cfg));
+  st = make_plan(cfg->n, cfg->k, cfg->s, &c->plan, wants_tc(cfg), cfg->max_ctas);
   if (st != BM_OK) { delete c; return st; }
   c->ws.pool = pool;
   c->ws.pool_stream = stream;
@@ -381,7 +399,7 @@ bm_status ctx_footprint(const bm_config* cfg, size_t* bytes) {
   bm_status st = check_config(cfg);
   if (st != BM_OK) return st;
   Plan p;
-  st = make_plan(cfg->n, cfg->k, cfg->s, &p, wants_tc(cfg));
+  st = make_plan(cfg->n, cfg->k, cfg->s, &p, wants_tc(cfg), cfg->max_ctas);
   if (st != BM_OK) return st;
   Workspace w;
   w.dry = true;
@@ -406,6 +424,7 @@ void bm_config_default(bm_config* cfg) {
   cfg->time_budget_s = 0.0;
   cfg->graphs = 1;
   cfg->trace = 0;
+  cfg->max_ctas = 0;
 }
 
 const char* bm_status_string(int32_t s) {
@@ -593,7 +612,8 @@ static bm_status assign_impl(const float* X, long long m, int n, int k,
   a.C = C; a.cstride = cstride; a.mask = mask; a.labels = labels; a.dmin = dmin;
   a.part = w.apart; a.sse = w.asse; a.ticket = &w.ctl->assign_ticket;
   const long long rows_per = p.generic ? 64 : 256;  // rows per CTA pass
-  const int grid = (int)std::max<long long>(1, std::min<long long>(p.agrid, (m + rows_per - 1) / rows_per));
+  int grid = (int)std::max<long long>(1, std::min<long long>(p.agrid, (m + rows_per - 1) / rows_per));
+  if (p.cap > 0) grid = std::min(grid, p.cap * std::max(1, p.agrid / std::max(1, sm_count())));
   if (launch_assign(a, grid, p.generic, p.np, p.asmem, st) != cudaSuccess) return BM_ECUDA;
   double sse = 0.0;
   if (cudaMemcpyAsync(&sse, w.asse, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -604,7 +624,7 @@ static bm_status assign_impl(const float* X, long long m, int n, int k,
 }
 
 // Grid autotuner of the tensor-core assignment.  The best number of CTAs per
-// SM depends on (n, k, form): more CTAs overlap one tile's loads with another
+// SM depends on (n, MMA width, form): more CTAs overlap one tile's loads with another
 // tile's MMA and epilogue, until shared memory, TMEM or the tail of the
 // tile queue costs more.  The first call of a shape on a device times every
 // candidate on the caller's own data and keeps the fastest; results do not
@@ -616,11 +636,13 @@ template <typename Launch>
 static int tc_tuned_grid(int n, int k, int terms, size_t smem, int maxg, long long tiles,
                          Launch launch, cudaStream_t st) {
   static std::mutex mu;
-  static std::map<std::tuple<int, int, int, int>, int> best;   // (dev, n, k, terms)
+  // (dev, n, MMA width, terms): k enters the kernel's cost through the MMA
+  // width (k rounded up to 16), so shapes that share it share the choice
+  static std::map<std::tuple<int, int, int, int>, int> best;
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const auto key = std::make_tuple(dev, n, k, terms);
+  const auto key = std::make_tuple(dev, n, (k + 15) / 16, terms);
   {
     std::lock_guard<std::mutex> g(mu);
     auto itr = best.find(key);
@@ -658,15 +680,17 @@ static bm_status assign_tc_impl(const float* X, long long m, int n, int k,
                                 const float* C, int cstride, const uint8_t* mask,
                                 int32_t* labels, float* dmin, Workspace& w,
                                 cudaStream_t st, double* sse_out,
-                                unsigned long long* rescored_out, int terms) {
+                                unsigned long long* rescored_out, int terms, int cap = 0) {
   if (k > kMaxK) return BM_EUNSUPPORTED;
   int stages, kb, npad16, ncols, cf;
+  // room for the kernel's static shared memory and the per-CTA reservation
+  const size_t limit = kSmemLimit - 2048;
   size_t smem = assign_tc_smem(n, k, terms, &stages, &kb, &npad16, &ncols, &cf);
-  if (smem > 227 * 1024 && terms == 3) {   // the split form does not fit: one term
+  if (smem > limit && terms == 3) {   // the split form does not fit: one term
     terms = 1;
     smem = assign_tc_smem(n, k, terms, &stages, &kb, &npad16, &ncols, &cf);
   }
-  if (smem > 227 * 1024) return BM_EUNSUPPORTED;
+  if (smem > limit) return BM_EUNSUPPORTED;
   int maxg = assign_tc_max_grid(smem);
   if (maxg <= 0) return BM_EUNSUPPORTED;
   int sms = 0, dev = 0;
@@ -685,6 +709,7 @@ static bm_status assign_tc_impl(const float* X, long long m, int n, int k,
     t.terms = terms; t.cf = cf;
     return launch_assign_tc(t, g, smem, st);
   }, st);
+  const int launch_grid = cap > 0 ? std::min(grid, cap * std::max(1, maxg / sms)) : grid;
   AssignTcArgs a{};
   a.X = X; a.m = m; a.n = n; a.C = C; a.cstride = cstride; a.mask = mask; a.k = k;
   a.labels = labels; a.dmin = dmin; a.part = reinterpret_cast<float2*>(w.apart);
@@ -695,7 +720,7 @@ static bm_status assign_tc_impl(const float* X, long long m, int n, int k,
   a.terms = terms;
   a.cf = cf;
   if (cudaMemsetAsync(w.rescored, 0, sizeof(unsigned long long), st) != cudaSuccess) return BM_ECUDA;
-  if (launch_assign_tc(a, grid, smem, st) != cudaSuccess) return BM_ECUDA;
+  if (launch_assign_tc(a, launch_grid, smem, st) != cudaSuccess) return BM_ECUDA;
   double sse = 0.0;
   unsigned long long resc = 0;
   if (cudaMemcpyAsync(&sse, w.asse, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -730,7 +755,8 @@ bm_status bm_assign(bm_ctx* c, int32_t* labels_dev, double* sse_out) {
       c->plan.agrid == 0)
     st = assign_tc_impl(c->X, c->cfg.m, c->cfg.n, c->cfg.k, c->ws.Cinc, c->plan.npad,
                         c->ws.mask_inc, labels_dev, nullptr, c->ws, c->stream, sse_out,
-                        &c->rescored, c->cfg.precision == BM_BF16_RESCORE ? 1 : 3);
+                        &c->rescored, c->cfg.precision == BM_BF16_RESCORE ? 1 : 3,
+                        c->plan.cap);
   else
     st = assign_impl(c->X, c->cfg.m, c->cfg.n, c->cfg.k, c->plan, c->ws.Cinc,
                      c->plan.npad, c->ws.mask_inc, labels_dev, nullptr, c->ws,

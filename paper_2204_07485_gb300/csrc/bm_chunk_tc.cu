@@ -1030,9 +1030,7 @@ size_t chunk_tc_smem(int npad, int k, int R, int n16, int fb, int ns) {
 }
 
 int chunk_tc_max_grid(size_t smem) {
-  if (cudaFuncSetAttribute(chunk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
-    return 0;
+  if (allow_max_smem(chunk_tc_kernel) != cudaSuccess) return 0;
   int per_sm = 0, dev = 0, sms = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chunk_tc_kernel, kTccThreads,
                                                     smem) != cudaSuccess)
@@ -1043,8 +1041,7 @@ int chunk_tc_max_grid(size_t smem) {
 }
 
 cudaError_t launch_chunk_tc(const ChunkArgs& a, int grid, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(chunk_tc_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(chunk_tc_kernel);
   if (e != cudaSuccess) return e;
   return launch_cooperative(chunk_tc_kernel, grid, kTccThreads, smem, st, a);
 }

@@ -192,6 +192,23 @@ __host__ __device__ inline ChunkSmem chunk_smem(int npad, int k, int kpad, int R
   return L;
 }
 
+// Lets launches of fn use up to the device's opt-in shared memory (minus the
+// kernel's static shared memory).  Every caller sets the same value, so
+// threads preparing launches of different sizes at once cannot lower the
+// limit under each other's feet (setting the launch's own size would).
+template <typename Kernel>
+inline cudaError_t allow_max_smem(Kernel fn) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes);
+}
+
 // Cooperative launch (all CTAs co-resident, as the grid barriers need) through
 // the launch-attribute API, which stream capture records into a graph.
 template <typename Kernel>

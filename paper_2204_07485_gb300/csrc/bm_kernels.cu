@@ -938,8 +938,7 @@ template <int NP, bool GENERIC>
 static cudaError_t launch_chunk_t(const ChunkArgs& a, int grid, size_t smem,
                                   cudaStream_t st) {
   auto fn = chunk_kernel<NP, GENERIC>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = allow_max_smem(fn);
   if (e != cudaSuccess) return e;
   return launch_cooperative(fn, grid, chunk_threads(GENERIC), smem, st, a);
 }
@@ -947,9 +946,7 @@ static cudaError_t launch_chunk_t(const ChunkArgs& a, int grid, size_t smem,
 template <int NP, bool GENERIC>
 static int chunk_max_grid_t(size_t smem) {
   auto fn = chunk_kernel<NP, GENERIC>;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
-    return 0;
+  if (allow_max_smem(fn) != cudaSuccess) return 0;
   int per_sm = 0, dev = 0, sms = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, chunk_threads(GENERIC),
                                                     smem) != cudaSuccess)
@@ -991,9 +988,7 @@ size_t assign_smem(int npad, int k, int kpad, bool generic) {
 
 template <typename F>
 static int max_grid_of(F fn, size_t smem) {
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
-    return 0;
+  if (allow_max_smem(fn) != cudaSuccess) return 0;
   int per_sm = 0, dev = 0, sms = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess)
     return 0;
@@ -1016,29 +1011,28 @@ int assign_max_grid(bool generic, int np, size_t smem) {
 cudaError_t launch_assign(const AssignArgs& a, int grid, bool generic, int np,
                           size_t smem, cudaStream_t st) {
   if (generic) {
-    cudaFuncSetAttribute(assign_generic_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    allow_max_smem(assign_generic_kernel);
     assign_generic_kernel<<<grid, kThreads, smem, st>>>(a);
   } else {
     switch (np) {
       case 4:
-        cudaFuncSetAttribute(assign_np_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_smem(assign_np_kernel<4>);
         assign_np_kernel<4><<<grid, kThreads, smem, st>>>(a);
         break;
       case 8:
-        cudaFuncSetAttribute(assign_np_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_smem(assign_np_kernel<8>);
         assign_np_kernel<8><<<grid, kThreads, smem, st>>>(a);
         break;
       case 16:
-        cudaFuncSetAttribute(assign_np_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_smem(assign_np_kernel<16>);
         assign_np_kernel<16><<<grid, kThreads, smem, st>>>(a);
         break;
       case 28:
-        cudaFuncSetAttribute(assign_np_kernel<28>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_smem(assign_np_kernel<28>);
         assign_np_kernel<28><<<grid, kThreads, smem, st>>>(a);
         break;
       default:
-        cudaFuncSetAttribute(assign_np_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_smem(assign_np_kernel<32>);
         assign_np_kernel<32><<<grid, kThreads, smem, st>>>(a);
         break;
     }

@@ -7,7 +7,11 @@
 // is refused (BM_ENOMEM), a submission beyond max_queue waiting jobs is
 // refused (BM_EBUSY).  Dispatch: first in, first out; a worker takes the
 // head job once the head's footprint fits in what the running jobs leave of
-// the budget.  Each worker thread owns a non-blocking stream; job state is
+// the budget.  A job's chunk kernels use at most SMs / workers CTAs unless
+// the job asks otherwise, so the workers' jobs run side by side on disjoint
+// SMs instead of queueing behind each other's cooperative launches (each
+// would otherwise span the whole GPU).  Each worker thread owns a
+// non-blocking stream; job state is
 // allocated from the server's stream-ordered memory pool, which keeps freed
 // memory for the next job, so no job synchronises the device.  Results are
 // those of the same job run alone: the kernels' reductions have a fixed
@@ -61,6 +65,7 @@ struct DeviceScope {
 struct bm_server {
   bm_server_config cfg{};
   int device = 0;
+  int cap = 0;                  // default CTA cap of a job: SMs / workers
   cudaMemPool_t pool = nullptr;
   std::mutex mu;
   std::condition_variable cv;   // any change: job queued or finished, memory freed, stop
@@ -82,6 +87,7 @@ void run_job(bm_server* sv, cudaStream_t st, Job& job) {
   bm_config cfg = job.spec.cfg;
   cfg.graphs = 0;   // a context per job: recording would not pay for itself
   cfg.trace = 0;
+  if (cfg.max_ctas <= 0) cfg.max_ctas = sv->cap;
   bm_ctx* ctx = nullptr;
   bm_fit_report rep{};
   double sse = 0.0, f_opt = 0.0;
@@ -164,6 +170,9 @@ bm_status bm_server_create(const bm_server_config* cfg, bm_server** out) {
   if (!sv) return BM_ENOMEM;
   sv->cfg = *cfg;
   sv->device = dev;
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  sv->cap = (sms + cfg->workers - 1) / cfg->workers;
   if (sv->cfg.memory_budget == 0) {
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { delete sv; return BM_ECUDA; }
@@ -219,7 +228,9 @@ bm_status bm_submit(bm_server* sv, const bm_job* job, uint64_t* ticket) {
   {
     DeviceScope ds(sv->device);
     size_t bytes = 0;
-    const bm_status rc = bm::ctx_footprint(&job->cfg, &bytes);
+    bm_config cfg = job->cfg;
+    if (cfg.max_ctas <= 0) cfg.max_ctas = sv->cap;
+    const bm_status rc = bm::ctx_footprint(&cfg, &bytes);
     if (rc != BM_OK) return rc;
     fp = (int64_t)bytes;
   }

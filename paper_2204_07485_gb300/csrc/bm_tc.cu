@@ -411,9 +411,7 @@ size_t assign_tc_smem(int n, int k, int terms, int* stages_out, int* kb_out,
 // single CTA per SM for this TMEM-allocating kernel, but more co-reside; the
 // host additionally caps the count by TMEM columns).
 int assign_tc_max_grid(size_t smem) {
-  if (cudaFuncSetAttribute(assign_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
-    return 0;
+  if (allow_max_smem(assign_tc_kernel) != cudaSuccess) return 0;
   cudaFuncSetAttribute(assign_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                        cudaSharedmemCarveoutMaxShared);
   cudaFuncAttributes fa;
@@ -432,8 +430,7 @@ int assign_tc_max_grid(size_t smem) {
 }
 
 cudaError_t launch_assign_tc(const AssignTcArgs& a, int grid, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(assign_tc_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(assign_tc_kernel);
   if (e != cudaSuccess) return e;
   assign_tc_kernel<<<grid, kTcThreads, smem, st>>>(a);
   return cudaGetLastError();

@@ -44,7 +44,9 @@ def _alone(bm, X, cfg, chunks):
 def test_mix_results_equal_jobs_run_alone(bm):
     data = [dev(bi.mixtures.isotropic_blobs(m, n, max(2 * k, 4), i)[0])
             for i, (m, n, k, s, p, T) in enumerate(MIX)]
-    cfgs = [bm.bm_config_default(m=m, n=n, k=k, s=s, seed=10 + i, precision=p)
+    # the server caps a job's CTAs at SMs / workers; run alone with that cap
+    cap = -(-torch.cuda.get_device_properties(0).multi_processor_count // 3)
+    cfgs = [bm.bm_config_default(m=m, n=n, k=k, s=s, seed=10 + i, precision=p, max_ctas=cap)
             for i, (m, n, k, s, p, T) in enumerate(MIX)]
     sv = bm.bm_server_create(workers=3)
     try:
@@ -134,3 +136,26 @@ def test_callbacks_report_completed_jobs(bm):
     assert sorted(t for t, _, _ in got) == sorted(tickets)
     assert all(st == 0 for _, st, _ in got)
     assert len({sse for _, _, sse in got}) == 1   # same job, same result
+
+
+@pytest.mark.parametrize("m,n,k,s,seed,T,prec,cap", [
+    (3000, 64, 33, 1000, 0, 3, 3, 3),     # tensor-core chunk kernel on 3 SMs
+    (20000, 2, 10, 2000, 0, 4, 0, 5),     # row-in-register kernel on 5 SMs
+])
+def test_capped_jobs_match_the_oracle(bm, m, n, k, s, seed, T, prec, cap):
+    import oracle as o
+    from gpu_helpers import CEN_REL, OBJ_REL, centroids_close, rel
+    from test_gpu_parity import _assert_decisive
+    if n == 2:
+        X = bi.mixtures.blobs_2d(seed)
+    else:
+        X, _ = bi.mixtures.isotropic_blobs(m, n, max(k, 2), seed, box=8.0)
+    draws = [bi.chunk_draws(seed, t, m, s, k) for t in range(T)]
+    st, recs = o.big_means(X, k, draws)
+    _assert_decisive(recs)
+    cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=seed, precision=prec, max_ctas=cap)
+    sse, f_opt, iters, C, mask, lab = _alone(bm, dev(X), cfg, T)
+    assert iters == sum(r.iters for r in recs)
+    assert np.array_equal(mask.astype(bool), st.live)
+    assert rel(f_opt, st.f_opt) <= OBJ_REL
+    assert centroids_close(C, st.C, st.live) <= CEN_REL
