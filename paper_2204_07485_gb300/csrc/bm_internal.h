@@ -110,6 +110,7 @@ struct DrawArgs {
   long long t0;        // first chunk of the batch; CTA b draws chunk t0 + b
   int32_t* idx;        // [batch][s] sorted sample rows
   uint32_t* bitmaps;   // [batch][ceil(m / 32)], all zero between launches
+  int smem_bitmap;     // set by launch_draw: the bitmap fits in shared memory
 };
 
 struct AssignTcArgs {

@@ -6,12 +6,13 @@
 // parallel, off the per-chunk critical path.  Per chunk t:
 //   round r draws (target - |S|) Philox words (purpose 0, counter
 //   (i / 4, r, t, 0)), maps each to a row by the high word of w * m, and adds
-//   it to S with atomicOr on the chunk's bitmap; a value is new when its bit
-//   was clear.  Rounds continue until |S| = target (64 rounds at most; the
+//   it to S with atomicOr on the chunk's bitmap (in shared memory when it
+//   fits); |S| after round 0 is a popcount of the bitmap, after later rounds
+//   the count of bits that were clear.  Rounds continue until |S| = target (64 rounds at most; the
 //   smallest absent rows complete S after that, which never happens in
 //   practice for target <= m / 2).  target = s, or m - s rows to leave out
 //   when 2s > m.  A fixed-order scan of the bitmap then writes the sample's
-//   rows in ascending order and clears the bitmap for the next use.
+//   rows in ascending order (and clears a global bitmap for the next use).
 // Nothing here waits on another CTA.
 #include <cuda_runtime.h>
 
@@ -45,17 +46,39 @@ __device__ __forceinline__ int block_excl_scan_i32(int v, int* buf, int* total) 
 }
 
 __global__ void __launch_bounds__(kDrawThreads) draw_kernel(DrawArgs a) {
+  extern __shared__ uint32_t sbits[];   // the chunk's bitmap, when it fits
   __shared__ int red[32];
   __shared__ int scan[32];
   const long long W = (a.m + 31) / 32;
   const long long t = a.t0 + blockIdx.x;
-  uint32_t* bm = a.bitmaps + (size_t)blockIdx.x * W;
+  const bool in_smem = a.smem_bitmap != 0;
+  uint32_t* bm = in_smem ? sbits : a.bitmaps + (size_t)blockIdx.x * W;
   int32_t* out = a.idx + (size_t)blockIdx.x * a.s;
   const bool complement = 2 * (long long)a.s > a.m;
   const uint32_t target = complement ? (uint32_t)(a.m - a.s) : (uint32_t)a.s;
+  if (in_smem) {
+    for (long long w = threadIdx.x; w < W; w += blockDim.x) sbits[w] = 0u;
+    __syncthreads();
+  }
 
+  // Round 0 sets its bits without waiting for the old values, then counts
+  // the set bits; the set after a round does not depend on the order of the
+  // atomics, so neither does anything below.  Later rounds (a few draws)
+  // count new bits from the atomics' old values.
   uint32_t have = 0;
-  for (int r = 0; r < kRoundSlots && have < target; ++r) {
+  if (target > 0) {
+    for (uint32_t i = threadIdx.x; i < target; i += blockDim.x) {
+      const uint64_t w = philox_word(a.seed, (uint64_t)t, 0, 0, i);
+      const uint64_t v = __umul64hi(w, (uint64_t)a.m);
+      atomicOr(bm + (v >> 5), 1u << (v & 31));   // result unused: a reduction
+    }
+    __syncthreads();
+    int c = 0;
+    for (long long w = threadIdx.x; w < W; w += blockDim.x)
+      c += __popc(in_smem ? bm[w] : __ldcg(bm + w));
+    have = (uint32_t)block_sum_i32(c, red);
+  }
+  for (int r = 1; r < kRoundSlots && have < target; ++r) {
     const uint32_t need = target - have;
     int got = 0;
     for (uint32_t i = threadIdx.x; i < need; i += blockDim.x) {
@@ -69,7 +92,7 @@ __global__ void __launch_bounds__(kDrawThreads) draw_kernel(DrawArgs a) {
   }
   if (have < target && threadIdx.x == 0) {
     for (long long w = 0; w < W && have < target; ++w) {
-      uint32_t word = __ldcg(bm + w);
+      uint32_t word = in_smem ? bm[w] : __ldcg(bm + w);
       for (int bpos = 0; bpos < 32 && have < target; ++bpos) {
         if (w * 32 + bpos >= a.m) break;
         if (!(word & (1u << bpos))) { word |= 1u << bpos; ++have; }
@@ -91,14 +114,14 @@ __global__ void __launch_bounds__(kDrawThreads) draw_kernel(DrawArgs a) {
       const long long w = wb + u;
       uint32_t v = 0u;
       if (w < W) {
-        const uint32_t raw = __ldcg(bm + w);
+        const uint32_t raw = in_smem ? bm[w] : __ldcg(bm + w);
         v = raw;
         if (complement) {
           v = ~raw;
           const long long lo = w * 32;
           if (lo + 32 > a.m) v &= (1u << (a.m - lo)) - 1u;
         }
-        bm[w] = 0u;
+        if (!in_smem) bm[w] = 0u;   // ready for the next draw
       }
       words[u] = v;
       c += __popc(v);
@@ -119,8 +142,18 @@ __global__ void __launch_bounds__(kDrawThreads) draw_kernel(DrawArgs a) {
   }
 }
 
+// Bitmaps up to this size live in shared memory (m up to 1.6 million rows).
+constexpr size_t kDrawSmemBitmap = 200 * 1024;
+
 cudaError_t launch_draw(const DrawArgs& a, int chunks, cudaStream_t st) {
-  draw_kernel<<<chunks, kDrawThreads, 0, st>>>(a);
+  DrawArgs d = a;
+  const size_t bytes = (size_t)((a.m + 31) / 32) * 4;
+  d.smem_bitmap = bytes <= kDrawSmemBitmap ? 1 : 0;
+  if (d.smem_bitmap) {
+    const cudaError_t e = allow_max_smem(draw_kernel);
+    if (e != cudaSuccess) return e;
+  }
+  draw_kernel<<<chunks, kDrawThreads, d.smem_bitmap ? bytes : 0, st>>>(d);
   return cudaGetLastError();
 }
 
