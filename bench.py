@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--profile", choices=["chunk_np", "chunk_tc", "assign_tc"], default=None,
+                    help="run one short job of a kernel family (for ncu captures) and exit")
     ap.add_argument("--chunks", type=int, default=WORKLOAD["chunks"])
     return ap.parse_args()
 
@@ -66,6 +68,10 @@ def peaks():
     except OSError:
         return 6800.0, "fallback"
 
+
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one chunk_kernel<28, 0>
+# launch on the default workload (a typical chunk: gather + Lloyd)
+CHUNK_NP28_DRAM_BYTES = 11_242_496
 
 # FP32 ALU peak of GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz.
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -486,8 +492,11 @@ def run_ours(args, wl):
         "share": asg_per_step / (fit_per_step + asg_per_step), "algorithmic_bytes": abytes}
     assign_kernel["frac"] = assign_kernel["achieved"] / assign_kernel["peak"]
     dom = chunk_kernel if chunk_kernel["share"] >= assign_kernel["share"] else assign_kernel
+    # DRAM bytes per chunk launch from ncu (dram__bytes_read + write of one
+    # typical chunk, profiles/chunk_kernel_np28_hepmass_like.md)
+    traffic = CHUNK_NP28_DRAM_BYTES if dom is chunk_kernel else None
     roofline = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
-                "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
+                "unit": dom["unit"], "frac": dom["frac"], "traffic": traffic,
                 "kernel": dom["kernel"],
                 "peak_source": ("derived FP32 FMA peak (152 SMs x 128 lanes x 2 x 2.07 GHz)"
                                 if dom["bound"] == "alu" else peak_src)}
@@ -561,8 +570,42 @@ def run_ours(args, wl):
     return 0
 
 
+PROFILE_CASES = {
+    # kernel family: (m, n, k, s, precision, chunks); small jobs for ncu captures
+    "chunk_np": (1_000_000, 28, 25, 50_000, 0, 4),     # chunk_kernel<28, 0>
+    "chunk_tc": (1_000_000, 128, 50, 50_000, 3, 3),    # chunk_tc_kernel
+    "assign_tc": (2_000_000, 128, 50, 50_000, 3, 1),   # assign_tc_kernel (final assignment)
+}
+
+
+def profile_case(name):
+    """One short job of the named kernel family (for ncu; prints one line)."""
+    import torch
+    import bminputs
+    import paper_2204_07485_gb300 as bm
+    m, n, k, s, prec, T = PROFILE_CASES[name]
+    dev = torch.device("cuda", 0)
+    if n == 28:
+        X = torch.from_numpy(bminputs.mixtures.hepmass_like(0, m=m)).to(dev)
+    else:
+        X = bminputs.mixtures.isotropic_blobs_device(m, n, 100, 0, alpha=0.5, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=0, precision=prec, graphs=0)
+    ctx = bm.bm_create(cfg, X, stream.cuda_stream)
+    try:
+        rep = bm.bm_fit_chunk(ctx, T)
+        sse = bm.bm_assign(ctx, None)
+    finally:
+        bm.bm_destroy(ctx)
+    print(json.dumps({"profile": name, "chunks": rep["chunks"], "lloyd_iters": rep["lloyd_iters"],
+                      "sse": sse}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile:
+        return profile_case(args.profile)
     wl = dict(WORKLOAD)
     if args.impl == "reference":
         return run_reference(args, wl)
