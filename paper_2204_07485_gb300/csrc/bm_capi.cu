@@ -633,7 +633,7 @@ static bm_status assign_impl(const float* X, long long m, int n, int k,
 }  // extern "C"
 
 template <typename Launch>
-static int tc_tuned_grid(int n, int k, int terms, size_t smem, int maxg, long long tiles,
+static int tc_tuned_grid(int n, int k, int terms, int stages, size_t smem, int maxg, long long tiles,
                          Launch launch, cudaStream_t st) {
   static std::mutex mu;
   // (dev, n, MMA width, terms): k enters the kernel's cost through the MMA
@@ -642,7 +642,7 @@ static int tc_tuned_grid(int n, int k, int terms, size_t smem, int maxg, long lo
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const auto key = std::make_tuple(dev, n, (k + 15) / 16, terms);
+  const auto key = std::make_tuple(dev, n, (k + 15) / 16, terms * 4 + stages);
   {
     std::lock_guard<std::mutex> g(mu);
     auto itr = best.find(key);
@@ -685,10 +685,12 @@ static bm_status assign_tc_impl(const float* X, long long m, int n, int k,
   int stages, kb, npad16, ncols, cf;
   // room for the kernel's static shared memory and the per-CTA reservation
   const size_t limit = kSmemLimit - 2048;
-  size_t smem = assign_tc_smem(n, k, terms, &stages, &kb, &npad16, &ncols, &cf);
+  // bulk copies of row tiles need a 16-byte aligned X
+  const bool bulk_ok = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  size_t smem = assign_tc_smem(n, k, terms, &stages, &kb, &npad16, &ncols, &cf, bulk_ok, limit);
   if (smem > limit && terms == 3) {   // the split form does not fit: one term
     terms = 1;
-    smem = assign_tc_smem(n, k, terms, &stages, &kb, &npad16, &ncols, &cf);
+    smem = assign_tc_smem(n, k, terms, &stages, &kb, &npad16, &ncols, &cf, bulk_ok, limit);
   }
   if (smem > limit) return BM_EUNSUPPORTED;
   int maxg = assign_tc_max_grid(smem);
@@ -699,7 +701,7 @@ static bm_status assign_tc_impl(const float* X, long long m, int n, int k,
   maxg = std::min(maxg, sms * std::max(1, 512 / ncols));   // TMEM columns per SM
   const long long tiles = (m + 127) / 128;
   if (tiles > w.apart_cap) return BM_EUNSUPPORTED;
-  const int grid = tc_tuned_grid(n, k, terms, smem, maxg, tiles, [&](int g) {
+  const int grid = tc_tuned_grid(n, k, terms, stages, smem, maxg, tiles, [&](int g) {
     AssignTcArgs t{};
     t.X = X; t.m = m; t.n = n; t.C = C; t.cstride = cstride; t.mask = mask; t.k = k;
     t.labels = labels; t.dmin = dmin; t.part = reinterpret_cast<float2*>(w.apart);

@@ -131,7 +131,7 @@ struct AssignTcArgs {
   int kb;              // K blocks of 64 BF16
   int npad16;          // MMA N: k rounded up to 16 (<= 128)
   int ncols;           // TMEM columns allocated
-  int stages;          // FP32 tile ring depth
+  int stages;          // FP32 row tiles filled ahead by bulk copies (0: thread loads)
   int use_bulk;        // X is 16-byte aligned: bulk copies for full tiles
   int terms;           // 1: BF16 products; 3: split BF16 (hi*hi + hi*lo + lo*hi)
   int cf;              // FP32 centroid copy kept in shared memory
@@ -231,7 +231,7 @@ inline cudaError_t launch_cooperative(Kernel fn, int grid, int threads, size_t s
 // Host-side launch helpers (bm_kernels.cu, bm_sample.cu, bm_tc.cu).
 cudaError_t launch_draw(const DrawArgs& a, int chunks, cudaStream_t st);
 size_t assign_tc_smem(int n, int k, int terms, int* stages, int* kb, int* npad16,
-                      int* ncols, int* cf);
+                      int* ncols, int* cf, bool bulk_ok, size_t limit);
 int assign_tc_max_grid(size_t smem);
 cudaError_t launch_assign_tc(const AssignTcArgs& a, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_chunk(const ChunkArgs& a, int grid, bool generic, int np,

@@ -45,23 +45,26 @@ constexpr int kTcRows = 128;       // MMA M: rows per tile, one thread per row
 constexpr int kTcThreads = 128;
 
 struct TcLayout {
-  int sB, sA, xF, cF, cc, xx, red, bars, holder, total;
+  int sB, sA, stg, xF, cF, cc, xx, red, bars, holder, total;
 };
 
-// planes = 1 (BF16) or 2 (hi and lo BF16 parts of the split form); cF (FP32
+// planes = 1 (BF16) or 2 (hi and lo BF16 parts of the split form); stages:
+// FP32 row tiles that bulk copies fill ahead (0: rows are loaded by the
+// threads, with an FP32 copy for the exact distances when n <= 64); cF (FP32
 // centroids for the exact distances) only when it fits.
 __host__ __device__ inline TcLayout tc_layout(int n, int kb, int npad16, int k, int planes,
-                                              bool cf) {
+                                              bool cf, int stages) {
   TcLayout L;
   int o = 0;
   L.sB = o;    o += planes * kb * npad16 * 128;         // centroids, BF16 swizzled
   L.sA = o;    o += planes * kb * kTcRows * 128;        // row tile, BF16 swizzled
-  L.xF = o;    o += n <= 64 ? kTcRows * align_up(n, 4) * 4 : 0;   // row tile, FP32
+  L.stg = o;   o += stages * kTcRows * n * 4;           // FP32 row tiles (bulk copies)
+  L.xF = o;    o += (stages == 0 && n <= 64) ? kTcRows * align_up(n, 4) * 4 : 0;
   L.cF = o;    o += cf ? align_up(k * n * 4, 16) : 0;   // FP32 centroids
   L.cc = o;    o += align_up(npad16 * 4, 16);           // ||c_j||^2, +inf if not live
   L.xx = o;    o += kTcRows * 4;                        // ||x||^2 of the tile's rows
   L.red = o;   o += 40 * 8;
-  L.bars = o;  o += 8;                                  // MMA completion
+  L.bars = o;  o += 8 * 3;                              // MMA completion, stage arrivals
   L.holder = o; o += 16;
   L.total = o;
   return L;
@@ -110,12 +113,15 @@ assign_tc_kernel(AssignTcArgs a) {
   const int n = a.n, k = a.k, kb = a.kb, N = a.npad16;
   const int planes = a.terms == 3 ? 2 : 1;
   const bool cf = a.cf != 0;
-  const TcLayout L = tc_layout(n, kb, N, k, planes, cf);
+  const int S = a.stages;   // FP32 row tiles in flight (0: thread loads)
+  const TcLayout L = tc_layout(n, kb, N, k, planes, cf, S);
   unsigned char* sB = smem_tc + L.sB;
   unsigned char* sA = smem_tc + L.sA;
   float* cF = reinterpret_cast<float*>(smem_tc + L.cF);
   // the FP32 rows of the tile for the exact distances (rows padded to 4)
-  const bool xf = n <= 64;
+  const bool xf = S == 0 && n <= 64;
+  float* stg = reinterpret_cast<float*>(smem_tc + L.stg);
+  uint64_t* sbar = reinterpret_cast<uint64_t*>(smem_tc + L.bars) + 1;
   const int xs = align_up(n, 4);
   float* xF = reinterpret_cast<float*>(smem_tc + L.xF);
   float* cc = reinterpret_cast<float*>(smem_tc + L.cc);
@@ -167,6 +173,7 @@ assign_tc_kernel(AssignTcArgs a) {
   for (int r = tid; r < kTcRows; r += kTcThreads) xx[r] = 0.f;
   if (tid == 0) {
     mbar_init(mma_bar, 1);
+    for (int i = 0; i < S; ++i) mbar_init(sbar + i, 1);
     mbar_init_fence();
   }
   if (warp == 0) tmem_alloc(holder, (uint32_t)a.ncols);
@@ -195,14 +202,28 @@ assign_tc_kernel(AssignTcArgs a) {
 
   unsigned rescored = 0;
   bool ok = true;
+  // bulk copy of this CTA's i-th tile into stage i % S (thread 0)
+  auto issue = [&](long long i) {
+    const long long tt = (long long)blockIdx.x + i * gridDim.x;
+    if (tt >= ntiles) return;
+    const int sidx = (int)(i % S);
+    const int rr = (int)min((long long)kTcRows, a.m - tt * kTcRows);
+    const uint32_t bytes = (uint32_t)(rr * n * 4);
+    mbar_expect_tx(sbar + sidx, bytes);
+    bulk_g2s(stg + (size_t)sidx * kTcRows * n, a.X + (size_t)tt * kTcRows * n, bytes, sbar + sidx);
+  };
+  if (tid == 0)
+    for (long long i = 0; i < S; ++i) issue(i);
   for (long long it = 0;; ++it) {
     const long long t = (long long)blockIdx.x + it * gridDim.x;
     if (t >= ntiles) break;
     const long long r0 = t * kTcRows;
     const int rows = (int)min((long long)kTcRows, a.m - r0);
     const float* src = a.X + (size_t)r0 * n;
-    // pull my next tile into L2 while this one is processed
-    if (tid == 0 && xvec) {
+    const float* tile = S ? stg + (size_t)(it % S) * kTcRows * n : nullptr;
+    if (S) {
+      if (!mbar_wait(sbar + (it % S), (uint32_t)((it / S) & 1))) ok = false;
+    } else if (tid == 0 && xvec) {   // pull my next tile into L2 while this one is processed
       const long long tn = t + gridDim.x;
       if ((tn + 1) * kTcRows <= a.m)
         prefetch_l2(a.X + (size_t)tn * kTcRows * n, (uint32_t)(kTcRows * n * 4));
@@ -215,7 +236,15 @@ assign_tc_kernel(AssignTcArgs a) {
 #pragma unroll
       for (int u = 0; u < 8; ++u) v[u] = 0.f;
       const int f0 = ch * 8;
-      if (r < rows && ch < nch) {
+      if (S && r < rows && ch < nch) {   // from the staged tile (n % 4 == 0)
+        const float4* p = reinterpret_cast<const float4*>(tile + (size_t)r * n + f0);
+        const float4 x0 = p[0];
+        v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+        if (f0 + 8 <= n) {
+          const float4 x1 = p[1];
+          v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+        }
+      } else if (r < rows && ch < nch) {
         const float* p = src + (size_t)r * n + f0;
         if (xvec && f0 + 8 <= n) {
           const float4 x0 = __ldg(reinterpret_cast<const float4*>(p));
@@ -269,6 +298,9 @@ assign_tc_kernel(AssignTcArgs a) {
     fence_proxy_async_smem();
     __syncthreads();
     BM_TC_TICK(0);
+    // one stage: it is converted, so the next tile can start arriving now
+    // (the epilogue then reads this tile's rows from global memory / L2)
+    if (S == 1 && tid == 0) issue(it + 1);
     if (tid == 0) {
       tc_fence_after();
       const uint64_t da = sdesc_sw128(smem_u32(sA));
@@ -296,7 +328,7 @@ assign_tc_kernel(AssignTcArgs a) {
     // ---- epilogue: one thread per row
     const int r = tid;
     const bool valid = r < rows;
-    const float* xrow = xf ? xF + r * xs : src + (size_t)r * n;
+    const float* xrow = S == 2 ? tile + (size_t)r * n : xf ? xF + r * xs : src + (size_t)r * n;
     const float xq = xx[r] * 1.00002f;
     const float E1 = fmaf(sqrtf(xq), s_bound[0], s_bound[1]);
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
@@ -352,6 +384,11 @@ assign_tc_kernel(AssignTcArgs a) {
         p.y = __fadd_rn(p.y, s_pair[w].y);
       }
       a.part[t] = p;
+      // two stages: this tile's stage has been read for the last time
+      if (S == 2) {
+        fence_proxy_async_smem();
+        issue(it + 2);
+      }
     }
     BM_TC_TICK(4);
   }
@@ -391,15 +428,24 @@ assign_tc_kernel(AssignTcArgs a) {
 }
 
 size_t assign_tc_smem(int n, int k, int terms, int* stages_out, int* kb_out,
-                      int* npad16_out, int* ncols_out, int* cf_out) {
+                      int* npad16_out, int* ncols_out, int* cf_out, bool bulk_ok,
+                      size_t limit) {
   const int kb = (n + 63) / 64;
   const int npad16 = (k + 15) / 16 * 16;
   const int planes = terms == 3 ? 2 : 1;
   int ncols = 32;
   while (ncols < npad16) ncols <<= 1;
   const bool cf = k * n * 4 <= 24 * 1024;
-  const TcLayout L = tc_layout(n, kb, npad16, k, planes, cf);
-  *stages_out = 0;
+  // two staged tiles when they fit, else thread loads: with a single stage
+  // the CTA has to read the rows back from L2 for the exact distances, and
+  // the larger footprint leaves fewer CTAs per SM to hide that latency
+  // (measured slower than thread loads at n = 128)
+  int stages = 0;
+  if (bulk_ok && n % 4 == 0 &&
+      (size_t)tc_layout(n, kb, npad16, k, planes, cf, 2).total + 1024 <= limit)
+    stages = 2;
+  const TcLayout L = tc_layout(n, kb, npad16, k, planes, cf, stages);
+  *stages_out = stages;
   *kb_out = kb;
   *npad16_out = npad16;
   *ncols_out = ncols;
