@@ -135,6 +135,19 @@ bm_status bm_fit_chunk(bm_ctx* ctx, int32_t chunks, bm_fit_report* out);
  * bm_assign_rows_prec).  Blocks until done. */
 bm_status bm_assign(bm_ctx* ctx, int32_t* labels_dev, double* sse_out);
 
+/* Full-data Lloyd polish (the further SSE reduction Sec. 3.4 suggests after
+ * Big-means): Lloyd iterations on all of X starting from the incumbent, with
+ * the chunks' stop rule (after an assignment: stop if f = 0, or it > 0 and
+ * f_prev - f <= tol * f_prev, or it = max_iter; centroids left without
+ * members become degenerate).  The resulting centroids and mask replace the
+ * incumbent; f_opt keeps its sample value.  *f_out (may be NULL) = f(C, X) of
+ * the last assignment (the returned centroids), *iters_out = update steps.
+ * Each iteration streams X twice (assignment, then the update's per-CTA
+ * partial sums over fixed row ranges); every sum has a fixed order.  Needs
+ * a live incumbent (else BM_EINVAL).  Blocks until done. */
+bm_status bm_polish(bm_ctx* ctx, int32_t max_iter, double tol, double* f_out,
+                    int32_t* iters_out);
+
 /* Reads the incumbent: f_opt (its sample objective), C (k x n, host) and the
  * mask (k bytes, host).  Any output may be NULL. */
 bm_status bm_objective(bm_ctx* ctx, double* f_opt_out, float* C_out_host,
@@ -251,6 +264,14 @@ bm_status bm_assign_rows_noalloc(const float* X_dev, int64_t m, int32_t n,
                                  int32_t k, int32_t* labels_dev,
                                  float* dmin_dev, double* sse_out,
                                  void* stream);
+
+/* Failure-detection self-test: runs one wait of the grid barrier that the
+ * chunk kernels use between phases, with a participant that never arrives
+ * and a limit of timeout_ms (1 .. 2000).  The wait gives up, records the
+ * timeout in its status word and returns; the call returns BM_ETIMEOUT (any
+ * other status means the bounded wait is broken) and the device stays usable.
+ * Nothing faults, traps or hangs.  BM_EINVAL for a limit out of range. */
+bm_status bm_selftest_wait_timeout(int32_t timeout_ms, void* stream);
 
 /* ------------------------------------------------------------------ serving
  * A job server runs whole Big-means jobs (Alg. 1: `chunks` chunks, then the

@@ -101,6 +101,7 @@ _SIGS = {
     "bm_get_state": (_i32, [_vp, _vp, _vp, _P(_dbl), _P(_i64)]),
     "bm_set_state": (_i32, [_vp, _vp, _vp, _dbl, _i64]),
     "bm_trace": (_i32, [_vp, _P(_dbl), _i32]),
+    "bm_polish": (_i32, [_vp, _i32, _dbl, _P(_dbl), _P(_i32)]),
     "bm_fit_host": (_i32, [_P(bm_config), _vp, _i32, _vp, _vp, _vp, _P(_dbl),
                            _P(bm_fit_report)]),
     "bm_draw_chunk": (_i32, [_i64, _i64, _u64, _i64, _vp, _vp]),
@@ -113,6 +114,7 @@ _SIGS = {
                                    _P(_dbl), _P(ctypes.c_uint64), _vp]),
     "bm_assign_rows_noalloc": (_i32, [_vp, _i64, _i32, _vp, _vp, _i32, _vp, _vp,
                                       _P(_dbl), _vp]),
+    "bm_selftest_wait_timeout": (_i32, [_i32, _vp]),
     "bm_server_create": (_i32, [_P(bm_server_config), _P(_vp)]),
     "bm_server_destroy": (_i32, [_vp]),
     "bm_submit": (_i32, [_vp, _P(bm_job), _P(ctypes.c_uint64)]),
@@ -190,6 +192,15 @@ def bm_assign(ctx, labels_dev=None):
     sse = _dbl()
     _check(_lib.bm_assign(ctx, _ptr(labels_dev), ctypes.byref(sse)), "bm_assign")
     return sse.value
+
+
+def bm_polish(ctx, max_iter=300, tol=1e-4):
+    """Full-data Lloyd from the incumbent; returns (f, iterations)."""
+    f = _dbl()
+    it = _i32()
+    _check(_lib.bm_polish(ctx, int(max_iter), float(tol), ctypes.byref(f), ctypes.byref(it)),
+           "bm_polish")
+    return f.value, it.value
 
 
 def bm_objective(ctx, C_out_host=None, mask_out_host=None):
@@ -293,6 +304,11 @@ def bm_assign_rows_noalloc(X_dev, m, n, C_dev, mask_dev, k, labels_dev=None,
                                        _stream(stream)),
            "bm_assign_rows_noalloc")
     return sse.value
+
+
+def bm_selftest_wait_timeout(timeout_ms=100, stream=None):
+    """Status of one grid-barrier wait that runs out (BM_ETIMEOUT expected)."""
+    return _lib.bm_selftest_wait_timeout(int(timeout_ms), _stream(stream))
 
 
 # ------------------------------------------------------------------ serving

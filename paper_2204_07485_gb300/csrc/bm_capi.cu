@@ -347,6 +347,11 @@ struct bm_ctx {
   long long plan_n = 0;     // chunks held by the sample plan
   long long nd_assign = 0;  // distance evaluations of bm_assign calls
   unsigned long long rescored = 0;  // rows rescored by the last tensor-core bm_assign
+  // full-data Lloyd polish: labels and per-CTA partials, allocated on first use
+  int32_t* pol_labels = nullptr;
+  float* pol_sum = nullptr;
+  int32_t* pol_cnt = nullptr;
+  int pol_grid = 0;
   std::vector<FitGraph> graphs;     // recorded fits, at most kMaxGraphs
   long long graph_clock = 0;
   bool graphs_ok = true;            // cleared if recording ever fails
@@ -450,6 +455,9 @@ bm_status bm_destroy(bm_ctx* c) {
   if (!c) return BM_OK;
   cudaStreamSynchronize(c->stream);
   for (FitGraph& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  if (c->pol_labels) cudaFree(c->pol_labels);
+  if (c->pol_sum) cudaFree(c->pol_sum);
+  if (c->pol_cnt) cudaFree(c->pol_cnt);
   c->ws.release();
   delete c;
   return BM_OK;
@@ -765,6 +773,81 @@ bm_status bm_assign(bm_ctx* c, int32_t* labels_dev, double* sse_out) {
                      c->stream, sse_out);
   if (st == BM_OK) c->nd_assign += c->cfg.m * (long long)live;
   return st;
+}
+
+bm_status bm_polish(bm_ctx* c, int32_t max_iter, double tol, double* f_out,
+                    int32_t* iters_out) {
+  if (!c || max_iter < 0 || !(tol >= 0.0)) return BM_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  const int k = c->cfg.k, n = c->cfg.n, npad = c->plan.npad;
+  const long long m = c->cfg.m;
+  cudaStream_t st = c->stream;
+  const int live = count_live_host(c->ws.mask_inc, k, st);
+  if (live < 0) return BM_ECUDA;
+  if (live == 0) return BM_EINVAL;   // no incumbent yet
+  // update-pass shape: one CTA per SM; the widest feature block (up to 256)
+  // that leaves room for at least four private warp slices, else one
+  const size_t budget = kSmemLimit - 8 * 1024;
+  int fw = 0, wu = 0;
+  for (int need : {4, 1}) {
+    for (int cand : {256, 128, 64, 32}) {
+      const int w = std::min(cand, npad);
+      int u = 8;
+      while (u > need && polish_smem(k, w, u) > budget) --u;
+      if (polish_smem(k, w, u) <= budget) { fw = w; wu = u; break; }
+    }
+    if (fw) break;
+  }
+  if (fw == 0) return BM_EUNSUPPORTED;
+  const size_t psmem = polish_smem(k, fw, wu);
+  const int G = sm_count();
+  if (!c->pol_labels) {
+    if (cudaMalloc(&c->pol_labels, (size_t)m * 4) != cudaSuccess ||
+        cudaMalloc(&c->pol_sum, (size_t)G * k * npad * 4) != cudaSuccess ||
+        cudaMalloc(&c->pol_cnt, (size_t)G * k * 4) != cudaSuccess)
+      return BM_ENOMEM;
+    c->pol_grid = G;
+  }
+  // work on the working copy (C, mask), starting from the incumbent
+  if (cudaMemcpyAsync(c->ws.C, c->ws.Cinc, (size_t)k * npad * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(c->ws.mask, c->ws.mask_inc, k, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return BM_ECUDA;
+  PolishArgs pa{};
+  pa.X = c->X; pa.m = m; pa.n = n; pa.npad = npad; pa.k = k;
+  pa.C = c->ws.C; pa.cstride = npad; pa.mask = c->ws.mask; pa.labels = c->pol_labels;
+  pa.part_sum = c->pol_sum; pa.part_cnt = c->pol_cnt;
+  pa.rows_per_cta = (m + c->pol_grid - 1) / c->pol_grid;
+  pa.wu = wu;
+  pa.fw = fw;
+  double f = 0.0, f_prev = 0.0;
+  int it = 0;
+  while (true) {
+    const int nl = count_live_host(c->ws.mask, k, st);
+    if (nl <= 0) return nl < 0 ? BM_ECUDA : BM_EINVAL;
+    bm_status rc;
+    if (c->plan.agrid == 0)
+      rc = assign_tc_impl(c->X, m, n, k, c->ws.C, npad, c->ws.mask, c->pol_labels, nullptr,
+                          c->ws, st, &f, nullptr, 3, c->plan.cap);
+    else
+      rc = assign_impl(c->X, m, n, k, c->plan, c->ws.C, npad, c->ws.mask, c->pol_labels,
+                       nullptr, c->ws, st, &f);
+    if (rc != BM_OK) return rc;
+    c->nd_assign += m * (long long)nl;
+    const bool stop = (f == 0.0) || (it > 0 && f_prev - f <= tol * f_prev) || (it == max_iter);
+    if (launch_polish_update(pa, c->pol_grid, psmem, stop ? 1 : 0, st) != cudaSuccess)
+      return BM_ECUDA;
+    if (stop) break;
+    f_prev = f;
+    ++it;
+  }
+  // the polished centroids become the incumbent (f_opt keeps its sample value)
+  if (cudaMemcpyAsync(c->ws.Cinc, c->ws.C, (size_t)k * npad * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(c->ws.mask_inc, c->ws.mask, k, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return BM_ECUDA;
+  if (f_out) *f_out = f;
+  if (iters_out) *iters_out = it;
+  return BM_OK;
 }
 
 bm_status bm_trace(bm_ctx* c, double* ns_out, int32_t count) {

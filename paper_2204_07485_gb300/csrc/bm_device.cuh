@@ -83,13 +83,15 @@ struct GridBarrier {
   uint32_t* counter;
   int* status;
   uint32_t epoch;
+  uint32_t expected = 0;                  // arrivals per barrier (0: every CTA of the grid)
+  uint64_t timeout_ns = kSpinTimeoutNs;
 
   __device__ bool sync() {
     __shared__ int s_ok;
     __syncthreads();
     ++epoch;
     if (threadIdx.x == 0) {
-      const uint32_t target = epoch * gridDim.x;
+      const uint32_t target = epoch * (expected ? expected : gridDim.x);
       __threadfence();
       atomicAdd(counter, 1u);
       int ok = 1;
@@ -101,7 +103,7 @@ struct GridBarrier {
           const uint64_t now = global_timer_ns();
           if (t0 == 0) t0 = now;
           if (ld_volatile(status) != kStatusOk || polls > kSpinLimit ||
-              now - t0 > kSpinTimeoutNs) {
+              now - t0 > timeout_ns) {
             atomicCAS(status, kStatusOk, kStatusTimeout);
             ok = 0;
             break;

@@ -137,6 +137,22 @@ struct AssignTcArgs {
   int cf;              // FP32 centroid copy kept in shared memory
 };
 
+// Full-data Lloyd update (bm_polish): per-CTA partials over fixed row ranges.
+struct PolishArgs {
+  const float* X;          // m x n, row stride n
+  long long m;
+  int n, npad, k;
+  float* C;                // k x cstride working centroids (updated in place)
+  int cstride;
+  uint8_t* mask;           // k live flags (cleared for centroids without members)
+  const int32_t* labels;   // m labels of the last assignment
+  float* part_sum;         // [G][k][npad]
+  int32_t* part_cnt;       // [G][k]
+  long long rows_per_cta;
+  int wu;                  // warps with a private slice
+  int f0, fw;              // feature block of one update pass (fw <= 256)
+};
+
 // Shared-memory layout of the chunk kernel (bytes), identical on host/device.
 struct ChunkSmem {
   int cen, crow, live, lidx, sw, cw, lab, dmin, dc, cand, stage, prow, red, total;
@@ -241,6 +257,9 @@ cudaError_t launch_chunk(const ChunkArgs& a, int grid, bool generic, int np,
 size_t chunk_tc_smem(int npad, int k, int R, int n16, int fb, int ns);
 int chunk_tc_max_grid(size_t smem);
 cudaError_t launch_chunk_tc(const ChunkArgs& a, int grid, size_t smem, cudaStream_t st);
+size_t polish_smem(int k, int fw, int wu);
+cudaError_t launch_polish_update(const PolishArgs& a, int grid, size_t smem, int stop,
+                                 cudaStream_t st);
 int chunk_max_grid(bool generic, int np, size_t smem);
 cudaError_t launch_assign(const AssignArgs& a, int grid, bool generic, int np,
                           size_t smem, cudaStream_t st);

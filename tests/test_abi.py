@@ -82,3 +82,10 @@ def test_server_entry_points_validate_without_a_device():
     assert bm._lib.bm_submit(None, None, None) == bm.BM_EINVAL
     assert bm._lib.bm_wait(None, 1, 0.0, None) == bm.BM_EINVAL
     assert bm._lib.bm_server_stats_get(None, None) == bm.BM_EINVAL
+
+
+def test_selftest_rejects_out_of_range_limits_without_a_device():
+    _ensure_built()
+    import paper_2204_07485_gb300 as bm
+    assert bm.bm_selftest_wait_timeout(0) == bm.BM_EINVAL
+    assert bm.bm_selftest_wait_timeout(5000) == bm.BM_EINVAL
