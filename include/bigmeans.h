@@ -135,6 +135,22 @@ bm_status bm_fit_chunk(bm_ctx* ctx, int32_t chunks, bm_fit_report* out);
  * bm_assign_rows_prec).  Blocks until done. */
 bm_status bm_assign(bm_ctx* ctx, int32_t* labels_dev, double* sse_out);
 
+/* Parallel Big-means workers on one GPU (the paper's parallelisation modes
+ * 2 and 3, Sec. 3.5).  `workers` worker contexts run side by side on their own
+ * streams (each capped at cfg.max_ctas CTAs, default SMs / workers); in round
+ * r worker w processes chunk t + r * workers + w of this context's chunk
+ * sequence (its own sample).  BM_WORKERS_COMPETITIVE: each worker keeps its
+ * own incumbent, starting from this context's, and after the last round the
+ * best one (lowest f_opt, lowest worker on ties) replaces this context's when
+ * strictly better.  BM_WORKERS_COLLECTIVE: every round starts all workers
+ * from this context's incumbent, and the best of their results (same order)
+ * replaces it when strictly better.  The chunk counter advances by
+ * rounds * workers.  `out` (may be NULL) sums the workers' chunks, accepted
+ * chunks and Lloyd steps.  Blocks until done. */
+enum { BM_WORKERS_COMPETITIVE = 0, BM_WORKERS_COLLECTIVE = 1 };
+bm_status bm_fit_workers(bm_ctx* ctx, int32_t workers, int32_t rounds, int32_t mode,
+                         bm_fit_report* out);
+
 /* Full-data Lloyd polish (the further SSE reduction Sec. 3.4 suggests after
  * Big-means): Lloyd iterations on all of X starting from the incumbent, with
  * the chunks' stop rule (after an assignment: stop if f = 0, or it > 0 and

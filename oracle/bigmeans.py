@@ -37,6 +37,11 @@ design notes):
       sum_i min(D^2_i, ||p_i - cand||^2) (lowest trial index on ties).
   R8  The sample is drawn without replacement (indices are an input here).
   R9  Argmin ties go to the lowest centroid index.
+  R12 Parallel modes 2 and 3 (Sec. 3.5): in round r worker w draws chunk
+      r * workers + w; "best" means lowest f_opt, lowest worker index on
+      ties, and a shared incumbent changes only when strictly improved (as
+      R2).  The paper gives no round structure for mode 3; rounds are
+      synchronous here.
 """
 import math
 
@@ -275,6 +280,42 @@ def big_means(X, k, draws, tol=1e-4, max_iter=300, trials=3, state=None,
     for q, (idx, u_first, u) in enumerate(draws):
         records.append(big_means_chunk(X, state, idx, u_first, u, tol,
                                        max_iter, trials, t=t0 + q))
+    return state, records
+
+
+def big_means_workers(X, k, draws_of, workers, rounds, mode, tol=1e-4, max_iter=300,
+                      trials=3, state=None, t0=0):
+    """The paper's parallel modes (Sec. 3.5), simulated in sequence: in round r
+    worker w processes chunk t0 + r * workers + w (draws_of(t) gives its draws).
+
+    mode "competitive" (mode 2): every worker keeps its own incumbent, starting
+    from ``state``; after the last round the best worker incumbent (lowest
+    f_opt, lowest worker on ties) replaces ``state`` when strictly better.
+    mode "collective" (mode 3): every round starts all workers from ``state``;
+    the round's best result (same order) replaces ``state`` when strictly
+    better.  Returns (state, records of every worker chunk, in (r, w) order).
+    """
+    X = np.asarray(X, dtype=np.float32)
+    if state is None:
+        state = BigMeansState(k, X.shape[1])
+    mine = [state.copy() for _ in range(workers)]
+    records = []
+    for r in range(rounds):
+        if mode == "collective":
+            mine = [state.copy() for _ in range(workers)]
+        for w in range(workers):
+            t = t0 + r * workers + w
+            idx, u_first, u = draws_of(t)
+            records.append(big_means_chunk(X, mine[w], idx, u_first, u, tol, max_iter,
+                                           trials, t=t))
+        if mode == "collective":
+            best = min(range(workers), key=lambda w: (mine[w].f_opt, w))
+            if mine[best].f_opt < state.f_opt:
+                state = mine[best].copy()
+    if mode == "competitive":
+        best = min(range(workers), key=lambda w: (mine[w].f_opt, w))
+        if mine[best].f_opt < state.f_opt:
+            state = mine[best].copy()
     return state, records
 
 

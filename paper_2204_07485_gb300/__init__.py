@@ -102,6 +102,7 @@ _SIGS = {
     "bm_set_state": (_i32, [_vp, _vp, _vp, _dbl, _i64]),
     "bm_trace": (_i32, [_vp, _P(_dbl), _i32]),
     "bm_polish": (_i32, [_vp, _i32, _dbl, _P(_dbl), _P(_i32)]),
+    "bm_fit_workers": (_i32, [_vp, _i32, _i32, _i32, _P(bm_fit_report)]),
     "bm_fit_host": (_i32, [_P(bm_config), _vp, _i32, _vp, _vp, _vp, _P(_dbl),
                            _P(bm_fit_report)]),
     "bm_draw_chunk": (_i32, [_i64, _i64, _u64, _i64, _vp, _vp]),
@@ -192,6 +193,17 @@ def bm_assign(ctx, labels_dev=None):
     sse = _dbl()
     _check(_lib.bm_assign(ctx, _ptr(labels_dev), ctypes.byref(sse)), "bm_assign")
     return sse.value
+
+
+BM_WORKERS_COMPETITIVE, BM_WORKERS_COLLECTIVE = 0, 1
+
+
+def bm_fit_workers(ctx, workers, rounds, mode=BM_WORKERS_COLLECTIVE):
+    """The paper's parallel modes: `workers` concurrent workers, `rounds` rounds."""
+    rep = bm_fit_report()
+    _check(_lib.bm_fit_workers(ctx, int(workers), int(rounds), int(mode), ctypes.byref(rep)),
+           "bm_fit_workers")
+    return rep.as_dict()
 
 
 def bm_polish(ctx, max_iter=300, tol=1e-4):

@@ -378,7 +378,7 @@ static bool wants_tc(const bm_config* cfg) {
 }
 
 bm_status ctx_create(const bm_config* cfg, const float* X_dev, cudaStream_t stream,
-                     cudaMemPool_t pool, bm_ctx** out) {
+                     cudaMemPool_t pool, bm_ctx** out, int plan_cap) {
   if (!cfg || !out || !X_dev) return BM_EINVAL;
   *out = nullptr;
   bm_status st = check_config(cfg);
@@ -393,7 +393,7 @@ bm_status ctx_create(const bm_config* cfg, const float* X_dev, cudaStream_t stre
   c->ws.pool = pool;
   c->ws.pool_stream = stream;
   st = ws_create(&c->ws, cfg->m, cfg->k, cfg->s, c->plan, c->stream,
-                 plan_capacity(cfg->m, cfg->s), cfg->m);
+                 plan_cap > 0 ? plan_cap : plan_capacity(cfg->m, cfg->s), cfg->m);
   if (st != BM_OK) { delete c; return st; }
   *out = c;
   return BM_OK;
@@ -773,6 +773,120 @@ bm_status bm_assign(bm_ctx* c, int32_t* labels_dev, double* sse_out) {
                      c->stream, sse_out);
   if (st == BM_OK) c->nd_assign += c->cfg.m * (long long)live;
   return st;
+}
+
+// The paper's parallel modes 2 and 3 (Sec. 3.5) on one GPU: W worker
+// contexts on their own streams, each capped at SMs / W CTAs so the workers
+// run side by side; worker w processes chunk t0 + r W + w in round r (one
+// sample each; a worker's sample plan holds one chunk).  Competitive: every
+// worker keeps its own incumbent (starting from the context's) and the best
+// incumbent -- lowest f_opt, lowest worker on ties -- becomes the context's
+// at the end.  Collective: every round starts all workers from the context's
+// incumbent and the best of their results replaces it when strictly better.
+bm_status bm_fit_workers(bm_ctx* c, int32_t workers, int32_t rounds, int32_t mode,
+                         bm_fit_report* out) {
+  if (!c || workers < 1 || rounds < 0 || (mode != BM_WORKERS_COMPETITIVE &&
+                                          mode != BM_WORKERS_COLLECTIVE))
+    return BM_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  const auto t_begin = std::chrono::steady_clock::now();
+  const int k = c->cfg.k, npad = c->plan.npad;
+  const size_t cbytes = (size_t)k * npad * 4;
+  bm_config wcfg = c->cfg;
+  wcfg.graphs = 0;
+  wcfg.trace = 0;
+  if (wcfg.max_ctas <= 0) wcfg.max_ctas = (sm_count() + workers - 1) / workers;
+  std::vector<bm_ctx*> w(workers, nullptr);
+  std::vector<cudaStream_t> ws(workers, nullptr);
+  bm_status rc = BM_OK;
+  auto cleanup = [&]() {
+    for (int i = 0; i < workers; ++i) {
+      if (w[i]) bm_destroy(w[i]);
+      if (ws[i]) cudaStreamDestroy(ws[i]);
+    }
+  };
+  // copies of (C_inc, mask_inc, f_opt) between contexts, on `st`
+  auto copy_inc = [&](bm_ctx* dst, const bm_ctx* src, cudaStream_t st) {
+    return cudaMemcpyAsync(dst->ws.Cinc, src->ws.Cinc, cbytes, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+           cudaMemcpyAsync(dst->ws.mask_inc, src->ws.mask_inc, k, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+           cudaMemcpyAsync(dst->ws.f_opt, src->ws.f_opt, 8, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+  };
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return BM_ECUDA;
+  for (int i = 0; i < workers && rc == BM_OK; ++i) {
+    if (cudaStreamCreateWithFlags(&ws[i], cudaStreamNonBlocking) != cudaSuccess) rc = BM_ECUDA;
+    else rc = ctx_create(&wcfg, c->X, ws[i], nullptr, &w[i], 1);
+    if (rc == BM_OK && !copy_inc(w[i], c, ws[i])) rc = BM_ECUDA;
+  }
+  if (rc != BM_OK) { cleanup(); return rc; }
+  const long long t0 = c->t;
+  std::vector<double> fo(workers);
+  for (int r = 0; r < rounds && rc == BM_OK; ++r) {
+    for (int i = 0; i < workers && rc == BM_OK; ++i) {
+      bm_ctx* x = w[i];
+      if (mode == BM_WORKERS_COLLECTIVE && r > 0 && !copy_inc(x, c, x->stream)) rc = BM_ECUDA;
+      ChunkArgs a = chunk_args(x->ws, x->plan, x->X, x->cfg.m, x->cfg.n, k, x->cfg.s);
+      a.seed = x->cfg.seed; a.max_iter = x->cfg.max_iter; a.tol = x->cfg.tol;
+      a.trials = x->cfg.kpp_trials;
+      a.phases = kPhaseGather | kPhaseKpp | kPhaseLloyd | kPhaseKeep;
+      x->t = t0 + (long long)r * workers + i;
+      if (rc == BM_OK) rc = queue_chunks(x, a, 1, 1);
+    }
+    for (int i = 0; i < workers; ++i) {
+      const bm_status s2 = check_status(w[i]->ws, w[i]->stream, 0);
+      if (rc == BM_OK) rc = s2;
+    }
+    if (rc != BM_OK || mode != BM_WORKERS_COLLECTIVE) continue;
+    // the round's best result replaces the shared incumbent when strictly better
+    double f_best = 0.0;
+    if (cudaMemcpy(&f_best, c->ws.f_opt, 8, cudaMemcpyDeviceToHost) != cudaSuccess) { rc = BM_ECUDA; break; }
+    int best = -1;
+    for (int i = 0; i < workers; ++i) {
+      if (cudaMemcpy(&fo[i], w[i]->ws.f_opt, 8, cudaMemcpyDeviceToHost) != cudaSuccess) { rc = BM_ECUDA; break; }
+      if (fo[i] < f_best && (best < 0 || fo[i] < fo[best])) best = i;
+    }
+    if (rc == BM_OK && best >= 0 &&
+        (!copy_inc(c, w[best], c->stream) || cudaStreamSynchronize(c->stream) != cudaSuccess))
+      rc = BM_ECUDA;
+  }
+  if (rc == BM_OK && mode == BM_WORKERS_COMPETITIVE) {
+    int best = -1;
+    for (int i = 0; i < workers && rc == BM_OK; ++i) {
+      if (cudaMemcpy(&fo[i], w[i]->ws.f_opt, 8, cudaMemcpyDeviceToHost) != cudaSuccess) rc = BM_ECUDA;
+      else if (best < 0 || fo[i] < fo[best]) best = i;
+    }
+    double f_c = 0.0;
+    if (rc == BM_OK && cudaMemcpy(&f_c, c->ws.f_opt, 8, cudaMemcpyDeviceToHost) != cudaSuccess) rc = BM_ECUDA;
+    if (rc == BM_OK && best >= 0 && fo[best] < f_c &&
+        (!copy_inc(c, w[best], c->stream) || cudaStreamSynchronize(c->stream) != cudaSuccess))
+      rc = BM_ECUDA;
+  }
+  Stats tot{};
+  for (int i = 0; i < workers && rc == BM_OK; ++i) {
+    Stats h{};
+    if (cudaMemcpy(&h, w[i]->ws.stats, sizeof(Stats), cudaMemcpyDeviceToHost) != cudaSuccess) { rc = BM_ECUDA; break; }
+    tot.chunks += h.chunks;
+    tot.accepted += h.accepted;
+    tot.lloyd_iters += h.lloyd_iters;
+    tot.n_d += h.n_d;
+  }
+  cleanup();
+  if (rc != BM_OK) return rc;
+  c->t = t0 + (long long)rounds * workers;
+  c->nd_assign += tot.n_d;   // the workers' distance evaluations count for this context
+  if (out) {
+    double f_opt = 0.0;
+    cudaMemcpy(&f_opt, c->ws.f_opt, 8, cudaMemcpyDeviceToHost);
+    Stats mine{};
+    cudaMemcpy(&mine, c->ws.stats, sizeof(Stats), cudaMemcpyDeviceToHost);
+    out->chunks = tot.chunks;
+    out->accepted = tot.accepted;
+    out->lloyd_iters = tot.lloyd_iters;
+    out->n_d = mine.n_d + c->nd_assign;
+    out->chunk_counter = c->t;
+    out->f_opt = f_opt;
+    out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_begin).count();
+  }
+  return BM_OK;
 }
 
 bm_status bm_polish(bm_ctx* c, int32_t max_iter, double tol, double* f_out,

@@ -273,6 +273,6 @@ size_t assign_smem(int npad, int k, int kpad, bool generic);
 // device bytes a context for cfg would hold.
 namespace bm {
 bm_status ctx_create(const bm_config* cfg, const float* X_dev, cudaStream_t stream,
-                     cudaMemPool_t pool, bm_ctx** out);
+                     cudaMemPool_t pool, bm_ctx** out, int plan_cap = 0);
 bm_status ctx_footprint(const bm_config* cfg, size_t* bytes);
 }  // namespace bm

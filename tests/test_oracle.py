@@ -318,3 +318,37 @@ def test_n_d_counter_convention():
     # then s x 10 per assignment step (no centroid emptied on blobs).
     assert r.lloyd.live.all()
     assert r.n_d == 500 + 9 * 3 * 500 + (r.iters + 1) * 500 * 10
+
+
+def test_workers_with_one_worker_are_sequential_big_means():
+    # both parallel modes with a single worker reduce to Alg. 1
+    X, _ = bi.mixtures.isotropic_blobs(3000, 3, 6, 4)
+    k, s, T = 5, 400, 6
+    draws_of = lambda t: bi.chunk_draws(4, t, 3000, s, k)
+    ref, recs = o.big_means(X, k, [draws_of(t) for t in range(T)])
+    for mode in ("competitive", "collective"):
+        st, recs_w = o.big_means_workers(X, k, draws_of, 1, T, mode)
+        assert st.f_opt == ref.f_opt and np.array_equal(st.C, ref.C)
+        assert [r.accepted for r in recs_w] == [r.accepted for r in recs]
+
+
+def test_competitive_workers_are_independent_runs():
+    # mode 2: worker w runs Alg. 1 on chunks w, w + W, ...; the best wins
+    X, _ = bi.mixtures.isotropic_blobs(3000, 3, 6, 5)
+    k, s, W, R = 5, 300, 3, 4
+    draws_of = lambda t: bi.chunk_draws(5, t, 3000, s, k)
+    st, _ = o.big_means_workers(X, k, draws_of, W, R, "competitive")
+    runs = [o.big_means(X, k, [draws_of(r * W + w) for r in range(R)])[0] for w in range(W)]
+    best = min(range(W), key=lambda w: (runs[w].f_opt, w))
+    assert st.f_opt == runs[best].f_opt and np.array_equal(st.C, runs[best].C)
+
+
+def test_collective_incumbent_never_worsens():
+    X, _ = bi.mixtures.isotropic_blobs(3000, 3, 6, 6)
+    k, s, W = 5, 300, 3
+    draws_of = lambda t: bi.chunk_draws(6, t, 3000, s, k)
+    prev = math.inf
+    for R in range(1, 5):
+        st, _ = o.big_means_workers(X, k, draws_of, W, R, "collective")
+        assert st.f_opt <= prev
+        prev = st.f_opt
