@@ -59,6 +59,15 @@ typedef enum bm_precision {
                            distances, FP32 rescore of the few remaining ties  */
 } bm_precision;
 
+/* Reinitialisation of degenerate centroids at the start of a chunk. */
+typedef enum bm_init {
+  BM_INIT_KMEANSPP = 0, /* K-means++ with kpp_trials candidates, lowest potential
+                           (the paper's choice, Sec. 3.3 and 5)               */
+  BM_INIT_FORGY = 1     /* Forgy (Sec. 2): each degenerate slot j takes the sample
+                           row floor(u_j * s), u_j its first K-means++ uniform;
+                           no distance evaluations                           */
+} bm_init;
+
 /* Parameters of one Big-means job (Alg. 1 inputs X, k, s and the stop rule). */
 typedef struct bm_config {
   int64_t m;            /* number of points                                    */
@@ -79,6 +88,7 @@ typedef struct bm_config {
   int32_t max_ctas;     /* > 0: at most this many CTAs per chunk launch (and
                            SMs' worth of final-assignment CTAs), leaving the
                            other SMs to concurrent jobs; 0: no cap             */
+  int32_t init;         /* bm_init: how degenerate centroids are reinitialised */
 } bm_config;
 
 /* What one bm_fit_chunk call did. */
@@ -95,8 +105,8 @@ typedef struct bm_fit_report {
 typedef struct bm_ctx bm_ctx;
 
 /* Fills *cfg with the paper's defaults (max_iter 300, tol 1e-4, 3 trials,
- * FP32, seed 0), graph replay on, phase tracing off, no CTA cap, and zero
- * sizes. */
+ * FP32, seed 0, K-means++ reinitialisation), graph replay on, phase tracing
+ * off, no CTA cap, and zero sizes. */
 void bm_config_default(bm_config* cfg);
 
 /* Human-readable name of a status code (static string). */

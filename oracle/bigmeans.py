@@ -37,6 +37,9 @@ design notes):
       sum_i min(D^2_i, ||p_i - cand||^2) (lowest trial index on ties).
   R8  The sample is drawn without replacement (indices are an input here).
   R9  Argmin ties go to the lowest centroid index.
+  R13 Forgy (Sec. 2: a uniform sample of the data as initial centres) as the
+      alternative reinitialisation: each degenerate slot independently takes
+      the sample row floor(u * s), u the slot's first K-means++ uniform.
   R12 Parallel modes 2 and 3 (Sec. 3.5): in round r worker w draws chunk
       r * workers + w; "best" means lowest f_opt, lowest worker index on
       ties, and a shared incumbent changes only when strictly improved (as
@@ -98,6 +101,21 @@ class KppPick:
         self.potentials = potentials
         self.chosen = chosen
         self.boundary_margin = boundary_margin
+
+
+def forgy_reseed(P, C, live, u):
+    """Forgy reinitialisation (Sec. 2; R13): every degenerate slot j, in
+    ascending order, takes the sample row floor(u[j][0] * s), a uniform pick
+    from the sample (independent per slot).  Returns new (C, live) copies."""
+    P = np.asarray(P, dtype=np.float64)
+    C = np.array(C, dtype=np.float64, copy=True)
+    live = np.array(live, dtype=bool, copy=True)
+    s = P.shape[0]
+    for j in range(C.shape[0]):
+        if not live[j]:
+            C[j] = P[min(s - 1, int(math.floor(u[j][0] * s)))]
+            live[j] = True
+    return C, live
 
 
 def kmeanspp_reseed(P, C, live, u_first, u, trials=3, picks=None):
@@ -239,8 +257,10 @@ class BigMeansState:
 
 
 def big_means_chunk(X, state, idx, u_first, u, tol=1e-4, max_iter=300,
-                    trials=3, t=0):
-    """One pass of Alg. 1's loop body on the sample X[idx]; updates ``state``."""
+                    trials=3, t=0, init="kmeans++"):
+    """One pass of Alg. 1's loop body on the sample X[idx]; updates ``state``.
+    ``init`` chooses the reinitialisation of degenerate centroids: K-means++
+    (the paper's choice, R7) or Forgy (R13)."""
     P = np.asarray(X, dtype=np.float32)[np.asarray(idx)].astype(np.float64)
     picks = []
     s = P.shape[0]
@@ -248,13 +268,16 @@ def big_means_chunk(X, state, idx, u_first, u, tol=1e-4, max_iter=300,
     reseeded = state.live.shape[0] - live0
     # n_d of the reseed (Sec. 5 counter): the D^2 of the first centre or of
     # the live set, then `trials` candidate distances per further slot.
-    if reseeded == 0:
+    if reseeded == 0 or init == "forgy":
         nd_kpp = 0
     elif live0 == 0:
         nd_kpp = s + (reseeded - 1) * s * trials
     else:
         nd_kpp = s * live0 + reseeded * s * trials
-    C1, live1 = kmeanspp_reseed(P, state.C, state.live, u_first, u, trials, picks)
+    if init == "forgy":
+        C1, live1 = forgy_reseed(P, state.C, state.live, u)
+    else:
+        C1, live1 = kmeanspp_reseed(P, state.C, state.live, u_first, u, trials, picks)
     res = lloyd(P, C1, live1, tol, max_iter)
     accepted = res.f < state.f_opt
     keep_margin = (abs(res.f - state.f_opt) / state.f_opt
@@ -268,7 +291,7 @@ def big_means_chunk(X, state, idx, u_first, u, tol=1e-4, max_iter=300,
 
 
 def big_means(X, k, draws, tol=1e-4, max_iter=300, trials=3, state=None,
-              t0=0):
+              t0=0, init="kmeans++"):
     """Alg. 1 over the given chunk draws [(idx, u_first, u), ...].
 
     Returns (state, records).  The final assignment is ``final_assignment``.
@@ -279,7 +302,7 @@ def big_means(X, k, draws, tol=1e-4, max_iter=300, trials=3, state=None,
     records = []
     for q, (idx, u_first, u) in enumerate(draws):
         records.append(big_means_chunk(X, state, idx, u_first, u, tol,
-                                       max_iter, trials, t=t0 + q))
+                                       max_iter, trials, t=t0 + q, init=init))
     return state, records
 
 

@@ -23,6 +23,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 BM_OK, BM_EINVAL, BM_ENOMEM, BM_ECUDA, BM_ETIMEOUT, BM_EBUSY, BM_ECANCELLED, \
     BM_EUNSUPPORTED = range(8)
 BM_FP32, BM_BF16_RESCORE, BM_FP8_RESCORE, BM_BF16X3_RESCORE = range(4)
+BM_INIT_KMEANSPP, BM_INIT_FORGY = 0, 1
 
 
 class bm_config(ctypes.Structure):
@@ -31,7 +32,8 @@ class bm_config(ctypes.Structure):
                 ("tol", ctypes.c_double), ("kpp_trials", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
                 ("time_budget_s", ctypes.c_double), ("graphs", ctypes.c_int32),
-                ("trace", ctypes.c_int32), ("max_ctas", ctypes.c_int32)]
+                ("trace", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
+                ("init", ctypes.c_int32)]
 
 
 class bm_fit_report(ctypes.Structure):

@@ -370,6 +370,7 @@ static bm_status check_config(const bm_config* cfg) {
   if (cfg->precision != BM_FP32 && cfg->precision != BM_BF16_RESCORE &&
       cfg->precision != BM_BF16X3_RESCORE)
     return BM_EUNSUPPORTED;
+  if (cfg->init != BM_INIT_KMEANSPP && cfg->init != BM_INIT_FORGY) return BM_EINVAL;
   return BM_OK;
 }
 
@@ -430,6 +431,7 @@ void bm_config_default(bm_config* cfg) {
   cfg->graphs = 1;
   cfg->trace = 0;
   cfg->max_ctas = 0;
+  cfg->init = BM_INIT_KMEANSPP;
 }
 
 const char* bm_status_string(int32_t s) {
@@ -573,6 +575,7 @@ bm_status bm_fit_chunk(bm_ctx* c, int32_t chunks, bm_fit_report* out) {
   a.trials = c->cfg.kpp_trials;
   a.phases = kPhaseGather | kPhaseKpp | kPhaseLloyd | kPhaseKeep;
   a.trace = c->cfg.trace != 0;
+  a.init = c->cfg.init;
   bm_status st = BM_OK;
   if (chunks > 0) {
     // graph replay needs a capturable stream (not the legacy default stream)
@@ -827,6 +830,7 @@ bm_status bm_fit_workers(bm_ctx* c, int32_t workers, int32_t rounds, int32_t mod
       ChunkArgs a = chunk_args(x->ws, x->plan, x->X, x->cfg.m, x->cfg.n, k, x->cfg.s);
       a.seed = x->cfg.seed; a.max_iter = x->cfg.max_iter; a.tol = x->cfg.tol;
       a.trials = x->cfg.kpp_trials;
+      a.init = x->cfg.init;
       a.phases = kPhaseGather | kPhaseKpp | kPhaseLloyd | kPhaseKeep;
       x->t = t0 + (long long)r * workers + i;
       if (rc == BM_OK) rc = queue_chunks(x, a, 1, 1);

@@ -739,6 +739,22 @@ __device__ bool tcc_kpp(const ChunkArgs& a, const TccS& S, GridBarrier& gb, int 
   const int k = a.k, G = gridDim.x, b = blockIdx.x, R = a.rows_per_cta;
   const int nlive = S.lidx[k];
   if (nlive == k) return true;
+  if (a.init == kInitForgy) {
+    // Forgy: slot j <- sample row floor(u_j * s), u_j its first K-means++
+    // uniform; no distances, every CTA applies the same picks
+    for (int j = 0; j < k; ++j) {
+      if (S.live[j]) continue;
+      const double u = unit_double(philox_word(a.seed, (uint64_t)a.t, 2, 0,
+                                               (uint64_t)(j * a.trials)));
+      tcc_load_cand(a, S, 0, min(a.s - 1, (int)floor(u * (double)a.s)));
+      __syncthreads();
+      tcc_set_centroid(a, S, j, S.cand);
+    }
+    build_live_list(S.live, S.lidx, k);
+    if (!gb.sync()) return false;
+    load_norms(a, S, &bd);
+    return true;
+  }
   long long nd = 0;
   double* DSUM = a.part_f + (size_t)kMaxTrials * G;
   bool ok = true;

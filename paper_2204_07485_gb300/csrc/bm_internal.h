@@ -15,6 +15,10 @@ constexpr int kRoundSlots = 64;    // per-round draw counters (== kMaxRounds)
 constexpr int kNpMax = 32;         // widest row kept in registers
 constexpr int kNumPhaseTimers = 11;  // see Stats::phase_ns
 
+// Reinitialisation of degenerate centroids (bm_config.init).
+constexpr int kInitKmeanspp = 0;
+constexpr int kInitForgy = 1;
+
 // Phases of the chunk kernel (Alg. 1 loop body).
 enum Phase : int {
   kPhaseGather = 2,   // P = X[idx] (idx drawn ahead by the sample plan)
@@ -63,6 +67,7 @@ struct ChunkArgs {
   int phases;
   int bar_sel;         // which Ctl::bar counter this launch uses
   int trace;           // 1: CTA 0 times its phases into Stats::phase_ns
+  int init;            // reinitialisation of degenerate centroids: kInitKmeanspp / kInitForgy
   int kpad;            // k rounded up to 32 (generic path)
   int32_t* idx;        // s
   float* P;            // s x npad

@@ -629,6 +629,28 @@ __device__ bool phase_kpp(const ChunkArgs& a, const Smem& S, GridBarrier& gb,
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int nlive = S.lidx[k];
   if (nlive == k) return true;
+  if (a.init == kInitForgy) {
+    // Forgy: slot j <- sample row floor(u_j * s), u_j its first K-means++
+    // uniform; no distances, every CTA applies the same picks
+    for (int j = 0; j < k; ++j) {
+      if (S.live[j]) continue;
+      const double u = unit_double(philox_word(a.seed, (uint64_t)a.t, 2, 0,
+                                               (uint64_t)(j * a.trials)));
+      const int row = min(a.s - 1, (int)floor(u * (double)a.s));
+      load_cand_row(a, S, 0, row);
+      __syncthreads();
+      set_centroid_row<GENERIC>(S, S.cand, j, a.npad, a.kpad);
+      if (threadIdx.x == 0) S.live[j] = 1;
+      if (b == 0) {
+        for (int f = threadIdx.x; f < a.npad; f += blockDim.x)
+          a.C[(size_t)j * a.npad + f] = S.cand[f];
+        if (threadIdx.x == 0) a.mask[j] = 1;
+      }
+      __syncthreads();
+    }
+    build_live_list(S.live, S.lidx, k);
+    return gb.sync();
+  }
   long long nd = 0;
   double* DSUM = a.part_f + (size_t)kMaxTrials * G;   // D^2 block sums region
   if (nlive > 0) {

@@ -45,7 +45,8 @@ def test_invalid_shapes_rejected_before_any_device_work():
     import paper_2204_07485_gb300 as bm
     bad = [dict(m=10, n=2, k=3, s=20), dict(m=10, n=2, k=11, s=10),
            dict(m=10, n=0, k=1, s=5), dict(m=10, n=2, k=0, s=5),
-           dict(m=2**31, n=2, k=2, s=5), dict(m=10, n=2, k=2, s=5, kpp_trials=0)]
+           dict(m=2**31, n=2, k=2, s=5), dict(m=10, n=2, k=2, s=5, kpp_trials=0),
+           dict(m=10, n=2, k=2, s=5, init=7)]
     for kw in bad:
         cfg = bm.bm_config_default(**kw)
         with pytest.raises(bm.BigMeansError) as e:

@@ -352,3 +352,23 @@ def test_collective_incumbent_never_worsens():
         st, _ = o.big_means_workers(X, k, draws_of, W, R, "collective")
         assert st.f_opt <= prev
         prev = st.f_opt
+
+
+def test_forgy_reseed_picks_uniform_rows_in_slot_order():
+    P = np.arange(20, dtype=np.float64).reshape(10, 2)
+    C = np.full((4, 2), -7.0)
+    live = np.array([False, True, False, False])
+    u = np.array([[0.05, 0.9, 0.9], [0.5, 0.5, 0.5], [0.999, 0.1, 0.1], [0.31, 0.0, 0.0]])
+    C2, live2 = o.forgy_reseed(P, C, live, u)
+    assert live2.all()
+    assert np.array_equal(C2[0], P[0]) and np.array_equal(C2[2], P[9])
+    assert np.array_equal(C2[3], P[3]) and np.array_equal(C2[1], C[1])   # live slot kept
+
+
+def test_forgy_big_means_counts_no_reseed_distances():
+    X, _ = bi.mixtures.isotropic_blobs(2000, 3, 5, 8)
+    k, s = 4, 500
+    draws = [bi.chunk_draws(8, t, 2000, s, k) for t in range(3)]
+    st, recs = o.big_means(X, k, draws, init="forgy")
+    assert st.live.all() and math.isfinite(st.f_opt)
+    assert recs[0].n_d == recs[0].lloyd.n_d              # Forgy evaluates no distances
