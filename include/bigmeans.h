@@ -145,6 +145,19 @@ bm_status bm_fit_chunk(bm_ctx* ctx, int32_t chunks, bm_fit_report* out);
  * bm_assign_rows_prec).  Blocks until done. */
 bm_status bm_assign(bm_ctx* ctx, int32_t* labels_dev, double* sse_out);
 
+/* Streaming (stream processing of newly arriving data portions, Sec. 1 and
+ * 7): a context without a resident dataset.  cfg.s is the largest portion;
+ * cfg.m is ignored.  Each bm_stream_push treats the pushed rows (device,
+ * rows x n row-major, k <= rows <= cfg.s, borrowed for the call) as the next
+ * chunk's sample: K-means++ (or Forgy) reseed, Lloyd, keep-the-best against
+ * the incumbent, with the chunk counter advancing by one.  bm_get_state /
+ * bm_set_state / bm_objective / bm_reset work as for any context;
+ * bm_fit_chunk, bm_assign, bm_polish and bm_fit_workers need a dataset and
+ * return BM_EINVAL (assign other data with bm_assign_rows and the incumbent).
+ * Release with bm_destroy. */
+bm_status bm_stream_create(const bm_config* cfg, void* stream, bm_ctx** out);
+bm_status bm_stream_push(bm_ctx* ctx, const float* P_dev, int64_t rows, bm_fit_report* out);
+
 /* Parallel Big-means workers on one GPU (the paper's parallelisation modes
  * 2 and 3, Sec. 3.5).  `workers` worker contexts run side by side on their own
  * streams (each capped at cfg.max_ctas CTAs, default SMs / workers); in round

@@ -105,6 +105,8 @@ _SIGS = {
     "bm_trace": (_i32, [_vp, _P(_dbl), _i32]),
     "bm_polish": (_i32, [_vp, _i32, _dbl, _P(_dbl), _P(_i32)]),
     "bm_fit_workers": (_i32, [_vp, _i32, _i32, _i32, _P(bm_fit_report)]),
+    "bm_stream_create": (_i32, [_P(bm_config), _vp, _P(_vp)]),
+    "bm_stream_push": (_i32, [_vp, _vp, _i64, _P(bm_fit_report)]),
     "bm_fit_host": (_i32, [_P(bm_config), _vp, _i32, _vp, _vp, _vp, _P(_dbl),
                            _P(bm_fit_report)]),
     "bm_draw_chunk": (_i32, [_i64, _i64, _u64, _i64, _vp, _vp]),
@@ -195,6 +197,22 @@ def bm_assign(ctx, labels_dev=None):
     sse = _dbl()
     _check(_lib.bm_assign(ctx, _ptr(labels_dev), ctypes.byref(sse)), "bm_assign")
     return sse.value
+
+
+def bm_stream_create(cfg, stream=None):
+    """A streaming context (no dataset): portions pushed with bm_stream_push."""
+    ctx = _vp()
+    _check(_lib.bm_stream_create(ctypes.byref(cfg), _stream(stream), ctypes.byref(ctx)),
+           "bm_stream_create")
+    return ctx.value
+
+
+def bm_stream_push(ctx, P_dev, rows):
+    """One chunk on the pushed rows (the sample); returns the report."""
+    rep = bm_fit_report()
+    _check(_lib.bm_stream_push(ctx, _ptr(P_dev), int(rows), ctypes.byref(rep)),
+           "bm_stream_push")
+    return rep.as_dict()
 
 
 BM_WORKERS_COMPETITIVE, BM_WORKERS_COLLECTIVE = 0, 1

@@ -380,7 +380,7 @@ static bool wants_tc(const bm_config* cfg) {
 
 bm_status ctx_create(const bm_config* cfg, const float* X_dev, cudaStream_t stream,
                      cudaMemPool_t pool, bm_ctx** out, int plan_cap) {
-  if (!cfg || !out || !X_dev) return BM_EINVAL;
+  if (!cfg || !out || (!X_dev && plan_cap >= 0)) return BM_EINVAL;   // plan_cap < 0: no X
   *out = nullptr;
   bm_status st = check_config(cfg);
   if (st != BM_OK) return st;
@@ -394,7 +394,8 @@ bm_status ctx_create(const bm_config* cfg, const float* X_dev, cudaStream_t stre
   c->ws.pool = pool;
   c->ws.pool_stream = stream;
   st = ws_create(&c->ws, cfg->m, cfg->k, cfg->s, c->plan, c->stream,
-                 plan_cap > 0 ? plan_cap : plan_capacity(cfg->m, cfg->s), cfg->m);
+                 plan_cap > 0 ? plan_cap : plan_cap < 0 ? 1 : plan_capacity(cfg->m, cfg->s),
+                 cfg->m);
   if (st != BM_OK) { delete c; return st; }
   *out = c;
   return BM_OK;
@@ -559,7 +560,7 @@ static bool fit_by_graph(bm_ctx* c, const ChunkArgs& a, long long chunks, bm_sta
 }
 
 bm_status bm_fit_chunk(bm_ctx* c, int32_t chunks, bm_fit_report* out) {
-  if (!c || chunks < 0) return BM_EINVAL;
+  if (!c || chunks < 0 || !c->X) return BM_EINVAL;   // streaming contexts have no X
   if (chunks == 0 && !(c->cfg.time_budget_s > 0.0)) return BM_EINVAL;
   std::lock_guard<std::mutex> g(c->mu);
   const auto t0 = std::chrono::steady_clock::now();
@@ -756,7 +757,7 @@ static int count_live_host(const uint8_t* mask_dev, int k, cudaStream_t st) {
 }
 
 bm_status bm_assign(bm_ctx* c, int32_t* labels_dev, double* sse_out) {
-  if (!c) return BM_EINVAL;
+  if (!c || !c->X) return BM_EINVAL;
   std::lock_guard<std::mutex> g(c->mu);
   const int live = count_live_host(c->ws.mask_inc, c->cfg.k, c->stream);
   if (live < 0) return BM_ECUDA;
@@ -788,7 +789,7 @@ bm_status bm_assign(bm_ctx* c, int32_t* labels_dev, double* sse_out) {
 // incumbent and the best of their results replaces it when strictly better.
 bm_status bm_fit_workers(bm_ctx* c, int32_t workers, int32_t rounds, int32_t mode,
                          bm_fit_report* out) {
-  if (!c || workers < 1 || rounds < 0 || (mode != BM_WORKERS_COMPETITIVE &&
+  if (!c || !c->X || workers < 1 || rounds < 0 || (mode != BM_WORKERS_COMPETITIVE &&
                                           mode != BM_WORKERS_COLLECTIVE))
     return BM_EINVAL;
   std::lock_guard<std::mutex> g(c->mu);
@@ -893,9 +894,72 @@ bm_status bm_fit_workers(bm_ctx* c, int32_t workers, int32_t rounds, int32_t mod
   return BM_OK;
 }
 
+// Streaming (no resident X): each pushed portion of rows is one chunk's
+// sample.  The context is a normal one sized for portions of up to cfg.s
+// rows, whose sample buffer P receives the portion instead of a gather.
+bm_status bm_stream_create(const bm_config* cfg, void* stream, bm_ctx** out) {
+  if (!cfg || !out) return BM_EINVAL;
+  bm_config c2 = *cfg;
+  c2.m = cfg->s;   // sizes the per-chunk state only
+  c2.graphs = 0;
+  bm_status st = ctx_create(&c2, nullptr, static_cast<cudaStream_t>(stream), nullptr, out, -1);
+  if (st != BM_OK) return st;
+  bm_ctx* c = *out;
+  // P's padding columns stay zero: portions fill only the first n columns
+  if (cudaMemsetAsync(c->ws.P, 0, (size_t)c->cfg.s * c->plan.npad * 4, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    bm_destroy(c);
+    *out = nullptr;
+    return BM_ECUDA;
+  }
+  return BM_OK;
+}
+
+bm_status bm_stream_push(bm_ctx* c, const float* P_dev, int64_t rows, bm_fit_report* out) {
+  if (!c || c->X || !P_dev || rows < c->cfg.k || rows > c->cfg.s) return BM_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  const auto t0 = std::chrono::steady_clock::now();
+  const int n = c->cfg.n, npad = c->plan.npad;
+  cudaStream_t st = c->stream;
+  Stats before{};
+  if (cudaMemcpyAsync(&before, c->ws.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpy2DAsync(c->ws.P, npad * 4, P_dev, n * 4, n * 4, rows, cudaMemcpyDeviceToDevice, st) !=
+          cudaSuccess)
+    return BM_ECUDA;
+  ChunkArgs a = chunk_args(c->ws, c->plan, nullptr, rows, n, c->cfg.k, rows);
+  a.rows_per_cta = c->plan.R;   // the plan's shape, fewer rows
+  a.seed = c->cfg.seed; a.max_iter = c->cfg.max_iter; a.tol = c->cfg.tol;
+  a.trials = c->cfg.kpp_trials; a.init = c->cfg.init; a.trace = c->cfg.trace != 0;
+  a.phases = kPhaseKpp | kPhaseLloyd | kPhaseKeep;
+  a.t = c->t;
+  a.bar_sel = (int)(c->launches & 1);
+  bm_status rc = launch_plan(a, c->plan, st) == cudaSuccess ? BM_OK : BM_ECUDA;
+  if (rc == BM_OK) {
+    ++c->launches;
+    ++c->t;
+  }
+  const bm_status s2 = check_status(c->ws, st, rows);
+  if (rc == BM_OK) rc = s2;
+  if (rc != BM_OK) return rc;
+  if (out) {
+    Stats after{};
+    double f_opt = 0.0;
+    cudaMemcpy(&after, c->ws.stats, sizeof(Stats), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&f_opt, c->ws.f_opt, sizeof(double), cudaMemcpyDeviceToHost);
+    out->chunks = after.chunks - before.chunks;
+    out->accepted = after.accepted - before.accepted;
+    out->lloyd_iters = after.lloyd_iters - before.lloyd_iters;
+    out->n_d = after.n_d;
+    out->chunk_counter = c->t;
+    out->f_opt = f_opt;
+    out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return BM_OK;
+}
+
 bm_status bm_polish(bm_ctx* c, int32_t max_iter, double tol, double* f_out,
                     int32_t* iters_out) {
-  if (!c || max_iter < 0 || !(tol >= 0.0)) return BM_EINVAL;
+  if (!c || !c->X || max_iter < 0 || !(tol >= 0.0)) return BM_EINVAL;
   std::lock_guard<std::mutex> g(c->mu);
   const int k = c->cfg.k, n = c->cfg.n, npad = c->plan.npad;
   const long long m = c->cfg.m;
