@@ -200,11 +200,28 @@ __device__ __forceinline__ void warp_two_sum(float& hi, float& lo) {
 
 // Sum of x[0..len) (L2-coherent loads) by one warp in a fixed order; every
 // lane gets the result.
-__device__ __forceinline__ double warp_sum_array_f64(const double* x, int len) {
+// Lane l's sum of x[l], x[l + 32], x[l + 64], ... (in that order) from L2;
+// the loads of up to eight terms go out together, so a grid's worth of
+// partials (up to 256 CTAs) costs one round trip.  Absent terms add +0.
+template <typename T>
+__device__ __forceinline__ T lane_sum_ldcg(const T* x, int len) {
   const int l = threadIdx.x & 31;
-  double v = 0.0;
-  for (int i = l; i < len; i += 32) v += __ldcg(x + i);
-  return warp_sum_f64(v);
+  T v = T(0);
+  for (int i0 = 0; i0 < len; i0 += 256) {
+    T t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + 32 * u + l;
+      t[u] = i < len ? __ldcg(x + i) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v += t[u];
+  }
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_array_f64(const double* x, int len) {
+  return warp_sum_f64(lane_sum_ldcg(x, len));
 }
 
 // (d, j) argmin with the lowest index winning ties.

@@ -161,8 +161,7 @@ struct PolishArgs {
 // Shared-memory layout of the chunk kernel (bytes), identical on host/device.
 struct ChunkSmem {
   int cen, crow, live, lidx, sw, cw, lab, dmin, dc, cand, stage, prow, red, total;
-  int wu;              // update accumulators: warps (row-in-register path) or
-                       // row groups (tiled path) that own a private copy
+  int wu;              // tiled path: row groups that own a private update accumulator
 };
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
@@ -186,21 +185,20 @@ __host__ __device__ inline ChunkSmem chunk_smem(int npad, int k, int kpad, int R
   L.crow = o;  o += generic ? align_up(k * npad * 4, 16) : 0;   // row-major copy
   L.live = o;  o += align_up(k * 4, 16);
   L.lidx = o;  o += align_up((k + 1) * 4, 16);   // live list, count at [k]
-  int wu;
-  if (!generic) {
-    // one 32-feature slice [k][32] per update warp, as many as fit in 64 KB
-    wu = (64 * 1024) / (k * 32 * 4);
-    if (wu > nthreads / 32) wu = nthreads / 32;
-  } else {
+  int wu = 1;
+  if (generic) {
     // one [k][npad] accumulator per row group, threads = groups x features
     wu = nthreads / npad;
     const int cap = (64 * 1024) / (k * npad * 4);
     if (wu > cap) wu = cap;
     if (wu > 8) wu = 8;
+    if (wu < 1) wu = 1;
   }
-  if (wu < 1) wu = 1;
   L.wu = wu;
-  L.sw = o;    o += align_up((generic ? wu * k * npad : wu * k * 32) * 4, 16);
+  // tiled path: update accumulators [wu][k][npad] and counts [wu][k];
+  // row-in-register path: the label sort -- order[R], start[k + 1], cur[k]
+  // -- and per-warp label counts [warps][k]
+  L.sw = o;    o += align_up((generic ? wu * k * npad : R + 2 * k + 1) * 4, 16);
   L.cw = o;    o += align_up((generic ? wu : nthreads / 32) * k * 4, 16);
   L.lab = o;   o += align_up(R * 4, 16);
   L.dmin = o;  o += align_up(R * 4, 16);

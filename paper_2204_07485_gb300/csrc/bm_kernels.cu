@@ -37,8 +37,8 @@ struct Smem {
   float* crow;  // generic: [k][npad] row-major copy of the centroids
   int* live;    // [k]
   int* lidx;    // [k + 1]: live centroid indices ascending, count at [k]
-  float* sw;    // update accumulators (np: [wu][k][32], generic: [wu][k][npad])
-  int* cw;      // [wu][k] member counts
+  float* sw;    // generic: update accumulators [wu][k][npad]; np: label sort (ints)
+  int* cw;      // generic: [wu][k] member counts; np: per-warp label counts [warps][k]
   int* lab;     // [R] labels of own rows
   float* dmin;  // [R] nearest squared distance / K-means++ D^2 of own rows
   float* dc;    // [kMaxTrials][R] candidate distances of own rows
@@ -133,49 +133,110 @@ __device__ __forceinline__ void load_row_smem(float (&p)[NP], const float* row) 
   }
 }
 
-// Squared distance of a register-held row to centroid row c (NP floats in
-// shared memory): four independent partial sums (features f mod 4),
+// Squared distances of two register-held rows to a register-held centroid
+// row c.  Each row keeps four independent partial sums (features f mod 4),
 // combined as (s0 + s1) + (s2 + s3).
 template <int NP>
-__device__ __forceinline__ float dist_np(const float (&p)[NP], const float* c) {
-  const float4* c4 = reinterpret_cast<const float4*>(c);
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+__device__ __forceinline__ void dist2_np(const float (&pa)[NP], const float (&pb)[NP],
+                                         const float4 (&c)[NP / 4], float& da, float& db) {
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  float b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
 #pragma unroll
   for (int u = 0; u < NP / 4; ++u) {
-    const float4 v = c4[u];
-    s0 = sq(p[4 * u] - v.x, s0);
-    s1 = sq(p[4 * u + 1] - v.y, s1);
-    s2 = sq(p[4 * u + 2] - v.z, s2);
-    s3 = sq(p[4 * u + 3] - v.w, s3);
+    const float4 v = c[u];
+    a0 = sq(pa[4 * u] - v.x, a0);
+    a1 = sq(pa[4 * u + 1] - v.y, a1);
+    a2 = sq(pa[4 * u + 2] - v.z, a2);
+    a3 = sq(pa[4 * u + 3] - v.w, a3);
+    b0 = sq(pb[4 * u] - v.x, b0);
+    b1 = sq(pb[4 * u + 1] - v.y, b1);
+    b2 = sq(pb[4 * u + 2] - v.z, b2);
+    b3 = sq(pb[4 * u + 3] - v.w, b3);
   }
-  return (s0 + s1) + (s2 + s3);
+  da = (a0 + a1) + (a2 + a3);
+  db = (b0 + b1) + (b2 + b3);
 }
 
-// Nearest live centroid of one register-held row.  Two centroids per step
-// keep eight independent chains in flight; centroids are compared in
-// ascending index order with strict <, so the lowest index wins ties.  bj
-// stays out of range when no centroid is live.
+// Nearest centroid among live-list positions [q0, q1) for two rows, in
+// ascending index order with strict <; a label stays out of range when the
+// range holds no centroid.  The next centroid's row is loaded from shared
+// memory while the current one is scored, so the loads' latency overlaps
+// the arithmetic.
 template <int NP>
-__device__ __forceinline__ void nearest_np(const float (&p)[NP],
-                                           const float* cen, const int* lidx,
-                                           int k, int& bj, float& bd) {
-  bd = INFINITY;
-  bj = INT_MAX;
-  const int nl = lidx[k];
-  int q = 0;
+__device__ __forceinline__ void nearest2_np(const float (&pa)[NP], const float (&pb)[NP],
+                                            const float* cen, const int* lidx, int q0,
+                                            int q1, int& ja, float& da, int& jb,
+                                            float& db) {
+  da = db = INFINITY;
+  ja = jb = INT_MAX;
+  if (q0 >= q1) return;
+  float4 cv[NP / 4];
+  int j = lidx[q0];
+#pragma unroll
+  for (int u = 0; u < NP / 4; ++u) cv[u] = reinterpret_cast<const float4*>(cen + j * NP)[u];
 #pragma unroll 1
-  for (; q + 2 <= nl; q += 2) {
-    const int j0 = lidx[q], j1 = lidx[q + 1];
-    const float d0 = dist_np<NP>(p, cen + j0 * NP);
-    const float d1 = dist_np<NP>(p, cen + j1 * NP);
-    if (bj == INT_MAX || d0 < bd) { bd = d0; bj = j0; }
-    if (d1 < bd) { bd = d1; bj = j1; }
+  for (int q = q0; q < q1; ++q) {
+    const int jn = lidx[min(q + 1, q1 - 1)];   // the last step reloads its own row
+    float4 nv[NP / 4];
+#pragma unroll
+    for (int u = 0; u < NP / 4; ++u) nv[u] = reinterpret_cast<const float4*>(cen + jn * NP)[u];
+    float d0, d1;
+    dist2_np<NP>(pa, pb, cv, d0, d1);
+    if (ja == INT_MAX || d0 < da) { da = d0; ja = j; }
+    if (jb == INT_MAX || d1 < db) { db = d1; jb = j; }
+#pragma unroll
+    for (int u = 0; u < NP / 4; ++u) cv[u] = nv[u];
+    j = jn;
   }
-  if (q < nl) {
-    const int j0 = lidx[q];
-    const float d0 = dist_np<NP>(p, cen + j0 * NP);
-    if (bj == INT_MAX || d0 < bd) { bd = d0; bj = j0; }
+}
+
+// Nearest live centroid of every own row (resident in S.prow) -> S.lab /
+// S.dmin.  The shared-memory reads of the
+// centroid table, not the arithmetic, limit a one-row-per-thread scan, so
+// each thread takes two rows and each half of the CTA scans one half of the
+// live list: the lower half writes its winners to S.lab / S.dmin, the upper
+// half to `spare` ([R] distances, then [R] labels), and the halves merge in
+// index order -- the upper half's winner replaces the lower's only when
+// strictly nearer (or when the lower half found none), so the lowest index
+// still wins ties.
+static_assert(kMaxTrials >= 2, "nearest_own_rows keeps 2 x R words in S.dc");
+
+template <int NP>
+__device__ void nearest_own_rows(const Smem& S, float* spare, int R, int k, int nrows) {
+  const int H = blockDim.x >> 1;
+  const bool upper = threadIdx.x >= H;
+  const int u = threadIdx.x - (upper ? H : 0);
+  const int nl = S.lidx[k], h = (nl + 1) >> 1;
+  const int q0 = upper ? h : 0, q1 = upper ? nl : h;
+  int* spare_lab = reinterpret_cast<int*>(spare + R);
+  for (int base = 0; base < nrows; base += 2 * H) {
+    const int ia = base + u, ib = base + H + u;
+    if (ia >= nrows) break;
+    float pa[NP], pb[NP];
+    load_row_smem<NP>(pa, S.prow + ia * NP);
+    load_row_smem<NP>(pb, S.prow + (ib < nrows ? ib : ia) * NP);
+    int ja, jb;
+    float da, db;
+    nearest2_np<NP>(pa, pb, S.cen, S.lidx, q0, q1, ja, da, jb, db);
+    if (upper) {
+      spare[ia] = da;
+      spare_lab[ia] = ja;
+      if (ib < nrows) { spare[ib] = db; spare_lab[ib] = jb; }
+    } else {
+      S.dmin[ia] = da;
+      S.lab[ia] = ja;
+      if (ib < nrows) { S.dmin[ib] = db; S.lab[ib] = jb; }
+    }
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+    const float dh = spare[i];
+    if (S.lab[i] == INT_MAX || dh < S.dmin[i]) {
+      S.dmin[i] = dh;
+      S.lab[i] = spare_lab[i];
+    }
+  }
+  __syncthreads();
 }
 
 // -------------------------------------------------------- generic path rows
@@ -291,16 +352,7 @@ template <int NP, bool GENERIC>
 __device__ void assign_own_rows(const ChunkArgs& a, const Smem& S, int r0,
                                 int nrows) {
   if constexpr (!GENERIC) {
-    for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-      float p[NP];
-      load_row_smem<NP>(p, S.prow + i * NP);
-      int j;
-      float d;
-      nearest_np<NP>(p, S.cen, S.lidx, a.k, j, d);
-      S.lab[i] = j;
-      S.dmin[i] = d;
-    }
-    __syncthreads();
+    nearest_own_rows<NP>(S, S.dc, a.rows_per_cta, a.k, nrows);
   } else {
     for (int t0 = 0; t0 < nrows; t0 += 64) {
       const int rows = min(64, nrows - t0);
@@ -386,114 +438,83 @@ __device__ void lloyd_own_rows(const ChunkArgs& a, const Smem& S,
   if constexpr (!GENERIC) {
     uint64_t tsub = trace_now(a);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    // member counts: in the update slices' spare lane 31 when n < 32,
-    // otherwise per warp by ballot during the assignment
-    const bool count_lane = n < 32;
-    for (int q = threadIdx.x; q < nw * k; q += blockDim.x) S.cw[q] = 0;
+    (void)L;
+    // assignment (S.dc, the K-means++ candidate distances, is free here)
+    nearest_own_rows<NP>(S, S.dc, a.rows_per_cta, k, nrows);
+    phase_tick(a, 8, &tsub);
+    // stable counting sort of own rows by label: order[start[j] ..) lists
+    // centroid j's rows in ascending row order
+    int* order = reinterpret_cast<int*>(S.sw);
+    int* start = order + a.rows_per_cta;   // [k + 1]
+    int* cur = start + k + 1;              // [k]
+    int* wc = S.cw;                        // [warps][k]
+    for (int j = threadIdx.x; j < k; j += blockDim.x) cur[j] = 0;
+    for (int q = threadIdx.x; q < nw * k; q += blockDim.x) wc[q] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+      const int j = S.lab[i];
+      if (j < k) atomicAdd(cur + j, 1);
+    }
+    __syncthreads();
+    if (w == 0) {
+      int run = 0;
+      for (int base = 0; base < k; base += 32) {
+        const int j = base + l;
+        const int c = j < k ? cur[j] : 0;
+        int x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, x, o);
+          if (l >= o) x += y;
+        }
+        if (j < k) start[j] = run + x - c;
+        run += __shfl_sync(0xffffffffu, x, 31);
+      }
+      if (l == 0) start[k] = run;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += blockDim.x) cur[j] = start[j];
     __syncthreads();
     for (int i0 = 0; i0 < nrows; i0 += blockDim.x) {
       const int i = i0 + threadIdx.x;
-      int j = INT_MAX;
-      if (i < nrows) {
-        float p[NP];
-        load_row_smem<NP>(p, S.prow + i * NP);
-        float d;
-        nearest_np<NP>(p, S.cen, S.lidx, k, j, d);
-        S.lab[i] = j;
-        S.dmin[i] = d;
+      int j = i < nrows ? S.lab[i] : k;
+      if (j > k) j = k;
+      const unsigned peers = __match_any_sync(0xffffffffu, j);
+      const int rank = __popc(peers & ((1u << l) - 1u));
+      if (j < k && rank == 0) wc[w * k + j] = __popc(peers);
+      __syncthreads();
+      if (j < k) {
+        int pos = cur[j] + rank;
+        for (int u = 0; u < w; ++u) pos += wc[u * k + j];
+        order[pos] = i;
       }
-      if (!count_lane) {
-        const int nl = S.lidx[k];
-        for (int q = 0; q < nl; ++q) {
-          const int jj = S.lidx[q];
-          const unsigned bal = __ballot_sync(0xffffffffu, j == jj);
-          if (l == 0 && bal) S.cw[w * k + jj] += __popc(bal);
+      __syncthreads();
+      for (int jj = threadIdx.x; jj < k; jj += blockDim.x) {
+        int add = 0;
+        for (int u = 0; u < nw; ++u) {
+          add += wc[u * k + jj];
+          wc[u * k + jj] = 0;
         }
+        cur[jj] += add;
       }
+      __syncthreads();
     }
+    phase_tick(a, 9, &tsub);
+    // partial sums of (p - c_j) over each centroid's rows, in row order
+    for (int q = threadIdx.x; q < k * NP; q += blockDim.x) {
+      const int j = q / NP, f = q - j * NP;
+      if (f >= n) continue;
+      const float c = S.cen[q];
+      const int e0 = start[j], e1 = start[j + 1];
+      float sum = 0.f;
+#pragma unroll 4
+      for (int e = e0; e < e1; ++e) sum += S.prow[order[e] * NP + f] - c;
+      a.part_sum[((size_t)j * npad + f) * G + b] = sum;
+    }
+    for (int j = threadIdx.x; j < k; j += blockDim.x)
+      a.part_cnt[(size_t)j * G + b] = start[j + 1] - start[j];
     __syncthreads();
-    phase_tick(a, 8, &tsub);
-    for (int fs = 0; fs < n; fs += 32) {
-      if (w < L.wu) {
-        float* my = S.sw + w * k * 32;
-        for (int q = l; q < k * 32; q += 32) my[q] = 0.f;
-        __syncwarp();
-        const int f = fs + l;
-        const bool feat = f < n;
-        const bool cnt = count_lane && fs == 0 && l == 31;   // adds 1 per member
-        const bool on = feat || cnt;
-        const int fc = feat ? f : 0;
-        const int step = L.wu;
-        int i = w;
-        // four rows at a time: when their labels differ the four
-        // read-modify-writes are independent and overlap; otherwise they run
-        // in row order.  Either way each slice entry sums its rows in row
-        // order, so the result does not depend on the batching.
-        for (; i + 3 * step < nrows; i += 4 * step) {
-          const int j0 = S.lab[i], j1 = S.lab[i + step];
-          const int j2 = S.lab[i + 2 * step], j3 = S.lab[i + 3 * step];
-          if ((j0 | j1 | j2 | j3) >= k) {   // a row without a live centroid
-            for (int u = 0; u < 4; ++u) {
-              const int ju = S.lab[i + u * step];
-              if (ju < k && on)
-                my[ju * 32 + l] += feat ? S.prow[(i + u * step) * NP + fc] - S.cen[ju * NP + fc]
-                                        : 1.f;
-            }
-            continue;
-          }
-          float v0 = 1.f, v1 = 1.f, v2 = 1.f, v3 = 1.f;
-          if (feat) {
-            v0 = S.prow[i * NP + f] - S.cen[j0 * NP + f];
-            v1 = S.prow[(i + step) * NP + f] - S.cen[j1 * NP + f];
-            v2 = S.prow[(i + 2 * step) * NP + f] - S.cen[j2 * NP + f];
-            v3 = S.prow[(i + 3 * step) * NP + f] - S.cen[j3 * NP + f];
-          } else if (!cnt) {
-            v0 = v1 = v2 = v3 = 0.f;
-          }
-          const bool distinct = j0 != j1 && j0 != j2 && j0 != j3 && j1 != j2 &&
-                                j1 != j3 && j2 != j3;
-          if (distinct) {
-            const float o0 = my[j0 * 32 + l], o1 = my[j1 * 32 + l];
-            const float o2 = my[j2 * 32 + l], o3 = my[j3 * 32 + l];
-            my[j0 * 32 + l] = o0 + v0;
-            my[j1 * 32 + l] = o1 + v1;
-            my[j2 * 32 + l] = o2 + v2;
-            my[j3 * 32 + l] = o3 + v3;
-          } else {
-            my[j0 * 32 + l] += v0;
-            my[j1 * 32 + l] += v1;
-            my[j2 * 32 + l] += v2;
-            my[j3 * 32 + l] += v3;
-          }
-        }
-        for (; i < nrows; i += step) {
-          const int j = S.lab[i];
-          if (j < k && on)
-            my[j * 32 + l] += feat ? S.prow[i * NP + fc] - S.cen[j * NP + fc] : 1.f;
-        }
-      }
-      __syncthreads();
-      phase_tick(a, 9, &tsub);
-      for (int q = threadIdx.x; q < k * 32; q += blockDim.x) {
-        const int j = q >> 5, f = fs + (q & 31);
-        if (f < n) {
-          float sum = 0.f;
-          for (int u = 0; u < L.wu; ++u) sum += S.sw[u * k * 32 + q];
-          a.part_sum[((size_t)j * npad + f) * G + b] = sum;
-        }
-      }
-      if (fs == 0)
-        for (int j = threadIdx.x; j < k; j += blockDim.x) {
-          int c = 0;
-          if (count_lane)
-            for (int u = 0; u < L.wu; ++u) c += (int)S.sw[u * k * 32 + j * 32 + 31];
-          else
-            for (int u = 0; u < nw; ++u) c += S.cw[u * k + j];
-          a.part_cnt[(size_t)j * G + b] = c;
-        }
-      __syncthreads();
-      phase_tick(a, 10, &tsub);
-    }
+    phase_tick(a, 10, &tsub);
   } else {
     const int ng = L.wu;
     for (int q = threadIdx.x; q < ng * k * npad; q += blockDim.x) S.sw[q] = 0.f;
@@ -737,33 +758,77 @@ __device__ bool phase_lloyd(const ChunkArgs& a, const Smem& S,
     phase_tick(a, 3, tclk);
     if (!gb.sync()) return false;
     phase_tick(a, 4, tclk);
-    if (w == 0) {
-      const double t = warp_sum_array_f64(FPART, G);
-      if (l == 0) s_f = t;
+    // Centroid (j, f) of the update belongs to warp q of the grid.  Its
+    // member count and partial sums over the CTAs are fetched before the
+    // stop decision (which only gates the write), and warp 0 fetches the
+    // objective's partials at the same time, so the whole step costs about
+    // one round trip to L2.
+    const int nwb = blockDim.x >> 5;
+    const int gw = b * nwb + w, nw = G * nwb;
+    const int q1st = gw < k * n ? gw : -1;   // the common case: one (j, f) per warp
+    int cnt1 = 0;
+    float sum1 = 0.f;
+    {
+      const int j1 = q1st >= 0 ? q1st / n : 0, f1 = q1st >= 0 ? q1st - j1 * n : 0;
+      const bool item = q1st >= 0 && S.live[j1] != 0;
+      const int* pc = a.part_cnt + (size_t)j1 * G;
+      const float* ps = a.part_sum + ((size_t)j1 * npad + f1) * G;
+      if (G <= 256) {
+        // one batch of loads: the item's counts and sums, and (warp 0) the
+        // objective's partials; each lane adds its terms in CTA order
+        int tc[8];
+        float ts[8];
+        double tf[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = 32 * u + l;
+          tc[u] = item && i < G ? __ldcg(pc + i) : 0;
+          ts[u] = item && i < G ? __ldcg(ps + i) : 0.f;
+          tf[u] = w == 0 && i < G ? __ldcg(FPART + i) : 0.0;
+        }
+        double fl = 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          cnt1 += tc[u];
+          sum1 += ts[u];
+          fl += tf[u];
+        }
+        cnt1 = warp_sum_i32(cnt1);
+        sum1 = warp_sum_f32(sum1);
+        fl = warp_sum_f64(fl);
+        if (w == 0 && l == 0) s_f = fl;
+      } else {
+        if (item) {
+          cnt1 = warp_sum_i32(lane_sum_ldcg(pc, G));
+          sum1 = warp_sum_f32(lane_sum_ldcg(ps, G));
+        }
+        if (w == 0) {
+          const double t = warp_sum_array_f64(FPART, G);
+          if (l == 0) s_f = t;
+        }
+      }
     }
     __syncthreads();
     f = s_f;
     const bool stop = (f == 0.0) || (it > 0 && f_prev - f <= a.tol * f_prev) ||
                       (it == a.max_iter);
-    const int nwb = blockDim.x >> 5;
-    const int gw = b * nwb + w, nw = G * nwb;
     for (int q = gw; q < k * n; q += nw) {
       const int j = q / n, ff = q - j * n;
       if (!S.live[j]) continue;
-      int cnt = 0;
-      float sum = 0.f;
-      const float* ps = a.part_sum + ((size_t)j * npad + ff) * G;
-      for (int u = l; u < G; u += 32) {
-        cnt += __ldcg(a.part_cnt + (size_t)j * G + u);
-        sum += __ldcg(ps + u);
+      int cnt;
+      float sum;
+      if (q == q1st) {
+        cnt = cnt1;
+        sum = sum1;
+      } else {
+        cnt = warp_sum_i32(lane_sum_ldcg(a.part_cnt + (size_t)j * G, G));
+        sum = warp_sum_f32(lane_sum_ldcg(a.part_sum + ((size_t)j * npad + ff) * G, G));
       }
-      cnt = warp_sum_i32(cnt);
       if (cnt == 0) {
         if (ff == 0 && l == 0) a.mask[j] = 0;
         continue;
       }
       if (stop) continue;
-      sum = warp_sum_f32(sum);
       if (l == 0) {
         const float c = GENERIC ? S.crow[j * npad + ff] : S.cen[j * npad + ff];
         a.C[(size_t)j * npad + ff] = c + sum / (float)cnt;
@@ -771,16 +836,24 @@ __device__ bool phase_lloyd(const ChunkArgs& a, const Smem& S,
     }
     phase_tick(a, 5, tclk);
     if (!gb.sync()) return false;
+    // the new centroids and mask: four centroid values per thread and step,
+    // all loads of a step in flight together
+    if (!stop) {
+      const int kn = k * npad, T = blockDim.x;
+      for (int q0 = threadIdx.x; q0 < kn; q0 += 4 * T) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = q0 + u * T < kn ? __ldcg(a.C + q0 + u * T) : 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = q0 + u * T;
+          if (q < kn) put_centroid<GENERIC>(S.cen, S.crow, q / npad, q % npad, v[u], npad, a.kpad);
+        }
+      }
+    }
     for (int j = threadIdx.x; j < k; j += blockDim.x)
       S.live[j] = __ldcg(reinterpret_cast<const unsigned char*>(a.mask) + j) != 0;
     build_live_list(S.live, S.lidx, k);
-    if (!stop) {
-      for (int q = threadIdx.x; q < k * npad; q += blockDim.x) {
-        const int j = q / npad, ff = q - j * npad;
-        put_centroid<GENERIC>(S.cen, S.crow, j, ff, __ldcg(a.C + q), npad, a.kpad);
-      }
-    }
-    __syncthreads();
     phase_tick(a, 6, tclk);
     if (stop) break;
     f_prev = f;
@@ -908,17 +981,28 @@ assign_np_kernel(AssignArgs a) {
   load_centroids<false>(cen, nullptr, live, a.C, a.cstride, a.mask, a.k, a.n, NP, 0, false);
   build_live_list(live, lidx, a.k);
   const bool vec4 = (a.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.X) & 15) == 0);
+  // two rows per thread, a grid stride apart: each centroid load from
+  // shared memory serves both
   double acc = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.m;
-       i += (long long)gridDim.x * blockDim.x) {
-    float p[NP];
-    load_row_np<NP>(p, a.X + (size_t)i * a.n, a.n, vec4, false);
-    int j;
-    float d;
-    nearest_np<NP>(p, cen, lidx, a.k, j, d);
-    if (a.labels) a.labels[i] = j;
-    if (a.dmin) a.dmin[i] = d;
-    acc += (double)d;
+       i += 2 * stride) {
+    const long long i2 = i + stride;
+    const bool two = i2 < a.m;
+    float pa[NP], pb[NP];
+    load_row_np<NP>(pa, a.X + (size_t)i * a.n, a.n, vec4, false);
+    load_row_np<NP>(pb, a.X + (size_t)(two ? i2 : i) * a.n, a.n, vec4, false);
+    int ja, jb;
+    float da, db;
+    nearest2_np<NP>(pa, pb, cen, lidx, 0, lidx[a.k], ja, da, jb, db);
+    if (a.labels) a.labels[i] = ja;
+    if (a.dmin) a.dmin[i] = da;
+    acc += (double)da;
+    if (two) {
+      if (a.labels) a.labels[i2] = jb;
+      if (a.dmin) a.dmin[i2] = db;
+      acc += (double)db;
+    }
   }
   assign_finish(a, acc, red);
 }
