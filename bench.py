@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-grouped", action="store_true")
     ap.add_argument("--profile", choices=["chunk_np", "chunk_tc", "assign_tc"], default=None,
                     help="run one short job of a kernel family (for ncu captures) and exit")
     ap.add_argument("--chunks", type=int, default=WORKLOAD["chunks"])
@@ -280,6 +281,82 @@ def launch_latency(bm, torch, dev, jobs=10, warmup=3):
         out["graph" if graphs else "direct"] = {
             "fit_ms": ms, "us_per_chunk": ms * 1e3 / T,
             "us_per_lloyd_iter": ms * 1e3 * jobs / max(1, iters)}
+    return out
+
+
+def grouped(bm, torch, dev, count=256, runs=3, warmup=1):
+    """256 independent chunks (s ~ U[4000, 64000], n ~ U{16, 32, 64, 128},
+    k ~ U{5, 10, 25, 50}, chunk i a mixture of k_i isotropic components drawn
+    with seed i; about 2 GB of float32 rows, more than L2) run to convergence
+    by the grouped Lloyd launches from a seeded Forgy start.  Reports the time
+    per run, per Lloyd step of the whole group, the distance throughput
+    (2 n flops per point-centroid distance), the same with one CTA per
+    problem (a fixed, untuned partition), and parity of sampled problems
+    against the same problem run alone (bm_lloyd)."""
+    import bminputs
+    spec = bminputs.mixtures.grouped_chunks_spec(0, count)
+    probs, starts = [], []
+    for q in spec:
+        P = bminputs.mixtures.isotropic_blobs_device(q["s"], q["n"], q["k"], q["seed"],
+                                                     device=dev)
+        rows = torch.from_numpy(bminputs.mixtures.forgy_rows(q["s"], q["k"], q["seed"])).to(dev)
+        C0 = P[rows].contiguous()
+        C = C0.clone()
+        mask = torch.ones(q["k"], dtype=torch.uint8, device=dev)
+        probs.append(dict(P=P, s=q["s"], n=q["n"], k=q["k"], C=C, mask=mask))
+        starts.append(C0)
+    torch.cuda.synchronize(dev)
+    rows_total = sum(q["s"] for q in spec)
+    bytes_total = sum(4 * q["s"] * q["n"] for q in spec)
+    out = {"workload": "grouped_256_chunks_s4k-64k_n16-128_k5-50",
+           "problems": count, "rows": rows_total, "bytes": bytes_total}
+    stream = torch.cuda.Stream(device=dev)
+
+    def reset():
+        with torch.cuda.stream(stream):
+            for p, C0 in zip(probs, starts):
+                p["C"].copy_(C0)
+                p["mask"].fill_(1)
+
+    for balance in (1, 0):
+        g = bm.bm_group_create(probs, balance=bool(balance), stream=stream)
+        try:
+            info = bm.bm_group_info(g)
+            times, res, steps = [], None, 0
+            for i in range(warmup + runs):
+                reset()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                res, steps = bm.bm_group_run(g, count)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                if i >= warmup:
+                    times.append(e0.elapsed_time(e1))
+        finally:
+            bm.bm_group_destroy(g)
+        ms = float(np.median(times))
+        flops = sum(2.0 * q["n"] * r["n_d"] for q, r in zip(spec, res))
+        iters = [r["iters"] for r in res]
+        entry = {"ms_per_run": ms, "steps": steps, "ms_per_step": ms / steps,
+                 "max_iters": max(iters), "mean_iters": float(np.mean(iters)),
+                 "dist_tflops": flops / (ms / 1e3) / 1e12, "grid": info["grid"],
+                 "segments": info["segments"]}
+        out["balanced" if balance else "one_cta_per_problem"] = entry
+        if balance:
+            balanced_res = res
+    # parity per problem against the same problem alone
+    worst, same = 0.0, True
+    for i in (0, count // 2, count - 1):
+        q = spec[i]
+        C = starts[i].clone()
+        mask = torch.ones(q["k"], dtype=torch.uint8, device=dev)
+        f, it = bm.bm_lloyd(probs[i]["P"], q["s"], q["n"], q["k"], C, mask)
+        r = balanced_res[i]
+        same = same and it == r["iters"]
+        worst = max(worst, abs(f - r["f"]) / max(abs(r["f"]), 1e-300))
+    out["alone_parity"] = {"sampled": 3, "same_iters": same, "max_rel_f": worst}
+    del probs, starts
+    torch.cuda.empty_cache()
     return out
 
 
@@ -561,6 +638,8 @@ def run_ours(args, wl):
         del Xg
     if rank == 0 and not args.no_precision:
         out["launch_latency"] = launch_latency(bm, torch, dev)
+    if rank == 0 and not args.no_grouped:
+        out["grouped"] = grouped(bm, torch, dev)
     if rank == 0 and not args.no_serving:
         out["serving"] = serving(bm, torch, dev)
     if rank == 0 and not args.no_cpu_baseline:

@@ -135,3 +135,21 @@ def isotropic_blobs_device(m, n, comps, seed, sigma=1.0, box=10.0, alpha=None,
 def gas_sensor_like_device(seed=0, m=10_000_000, n=128, device="cuda"):
     """m = 1e7, n = 128, 100 isotropic components, Dirichlet(0.5) (k = 50), on device."""
     return isotropic_blobs_device(m, n, 100, seed, alpha=0.5, device=device)
+
+
+def grouped_chunks_spec(seed=0, count=256):
+    """Shapes of `count` independent chunks for the grouped Lloyd workload:
+    s ~ U[4000, 64000], n ~ U{16, 32, 64, 128}, k ~ U{5, 10, 25, 50}.  Chunk i
+    is a mixture of k_i isotropic components (sigma 1, means U[-10, 10]^n)
+    drawn with seed i.  Returns a list of dicts (s, n, k, seed)."""
+    rng = np.random.default_rng(seed)
+    s = rng.integers(4000, 64001, size=count)
+    n = rng.choice([16, 32, 64, 128], size=count)
+    k = rng.choice([5, 10, 25, 50], size=count)
+    return [dict(s=int(s[i]), n=int(n[i]), k=int(k[i]), seed=i) for i in range(count)]
+
+
+def forgy_rows(s, k, seed):
+    """k distinct row indices of an s-row chunk (a seeded Forgy start), ascending."""
+    rng = np.random.default_rng(10_000 + seed)
+    return np.sort(rng.choice(s, size=k, replace=False))

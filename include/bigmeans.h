@@ -312,6 +312,60 @@ bm_status bm_assign_rows_noalloc(const float* X_dev, int64_t m, int32_t n,
  * Nothing faults, traps or hangs.  BM_EINVAL for a limit out of range. */
 bm_status bm_selftest_wait_timeout(int32_t timeout_ms, void* stream);
 
+/* ------------------------------------------------------------ grouped Lloyd
+ * Many independent Lloyd problems (Sec. 2, stop rule of Sec. 5) -- the
+ * chunks of many Big-means jobs, say -- advanced together: each Lloyd step
+ * of every unfinished problem is one launch that assigns all their rows and
+ * one launch that updates all their centroids, and a recorded CUDA graph
+ * replays the steps.  The rows of all problems are cut into per-CTA ranges
+ * of equal cost, so one large problem spreads over many SMs and small ones
+ * share an SM.  Each problem ends where bm_lloyd alone would: the same stop
+ * rule, the same degenerate-cluster handling (live centroids that lose every
+ * member become degenerate), objectives and centroids equal to rounding
+ * (the sums run over a different row partition). */
+typedef struct bm_group bm_group;
+
+typedef struct bm_group_problem {
+  const float* P_dev;     /* s x n rows, row-major float32, device (borrowed)    */
+  int64_t s;              /* rows, >= k                                           */
+  int32_t n;              /* features, 1 .. 512                                   */
+  int32_t k;              /* centroid slots, 1 .. 128                             */
+  float* C_dev;           /* k x n row-major centroids, device: the start on
+                             entry to bm_group_run, the result after it          */
+  uint8_t* mask_dev;      /* k live flags (1 = live), device, in and out         */
+  int32_t* labels_dev;    /* s labels of the last assignment (device, may be NULL) */
+} bm_group_problem;
+
+typedef struct bm_group_result {
+  double f;               /* objective of the last assignment (float64)          */
+  int64_t n_d;            /* point-centroid distance evaluations                  */
+  int32_t iters;          /* update steps                                         */
+  int32_t live;           /* live centroids at the end                            */
+} bm_group_result;
+
+/* Plans a group: validates the problems (BM_EINVAL: NULL buffers, s < k,
+ * n < 1, k < 1, count < 1, max_iter < 0, tol < 0; BM_EUNSUPPORTED: k > 128,
+ * n > 512, or tables beyond shared memory), partitions their rows over the
+ * GPU (balance = 1; balance = 0 gives each problem a single CTA of its own)
+ * and allocates the partial results.  The problems' buffers are borrowed
+ * until bm_group_destroy.  Work goes to `stream` (NULL: the legacy stream,
+ * without graph replay). */
+bm_status bm_group_create(const bm_group_problem* problems, int32_t count,
+                          int32_t max_iter, double tol, int32_t balance,
+                          void* stream, bm_group** out);
+
+/* Runs every problem from its current C and mask to its stop; blocks until
+ * done.  results_host (count entries, may be NULL) receives each problem's
+ * outcome, *steps_out (may be NULL) the Lloyd steps launched. */
+bm_status bm_group_run(bm_group* group, bm_group_result* results_host, int32_t* steps_out);
+
+/* The plan: CTAs of the assignment launch, segments, dynamic shared memory. */
+bm_status bm_group_info(bm_group* group, int32_t* grid_out, int32_t* segments_out,
+                        int64_t* smem_out);
+
+/* Frees the group (NULL is a no-op). */
+bm_status bm_group_destroy(bm_group* group);
+
 /* ------------------------------------------------------------------ serving
  * A job server runs whole Big-means jobs (Alg. 1: `chunks` chunks, then the
  * final assignment) submitted from any thread, several at a time on one GPU.

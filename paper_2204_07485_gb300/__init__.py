@@ -81,6 +81,20 @@ class bm_server_stats_t(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class bm_group_problem(ctypes.Structure):
+    _fields_ = [("P_dev", ctypes.c_void_p), ("s", ctypes.c_int64), ("n", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("C_dev", ctypes.c_void_p), ("mask_dev", ctypes.c_void_p),
+                ("labels_dev", ctypes.c_void_p)]
+
+
+class bm_group_result(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_double), ("n_d", ctypes.c_int64), ("iters", ctypes.c_int32),
+                ("live", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class BigMeansError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -125,6 +139,10 @@ _SIGS = {
     "bm_submit": (_i32, [_vp, _P(bm_job), _P(ctypes.c_uint64)]),
     "bm_wait": (_i32, [_vp, ctypes.c_uint64, _dbl, _P(bm_job_result)]),
     "bm_server_stats_get": (_i32, [_vp, _P(bm_server_stats_t)]),
+    "bm_group_create": (_i32, [_P(bm_group_problem), _i32, _i32, _dbl, _i32, _vp, _P(_vp)]),
+    "bm_group_run": (_i32, [_vp, _P(bm_group_result), _P(_i32)]),
+    "bm_group_info": (_i32, [_vp, _P(_i32), _P(_i32), _P(_i64)]),
+    "bm_group_destroy": (_i32, [_vp]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -301,6 +319,40 @@ def bm_lloyd(P_dev, s, n, k, C_dev, mask_dev, max_iter=300, tol=1e-4, stream=Non
                          _ptr(mask_dev), int(max_iter), float(tol), ctypes.byref(f),
                          ctypes.byref(it), _stream(stream)), "bm_lloyd")
     return f.value, it.value
+
+
+def bm_group_create(problems, max_iter=300, tol=1e-4, balance=True, stream=None):
+    """problems: sequence of dicts with P (s x n device rows), s, n, k, C (k x n
+    device centroids, the start), mask (k device uint8) and optionally labels
+    (s device int32).  Returns a group handle."""
+    arr = (bm_group_problem * len(problems))()
+    for i, q in enumerate(problems):
+        arr[i] = bm_group_problem(_ptr(q["P"]), int(q["s"]), int(q["n"]), int(q["k"]),
+                                  _ptr(q["C"]), _ptr(q["mask"]), _ptr(q.get("labels")))
+    out = _vp()
+    _check(_lib.bm_group_create(arr, len(problems), int(max_iter), float(tol),
+                                1 if balance else 0, _stream(stream), ctypes.byref(out)),
+           "bm_group_create")
+    return out.value
+
+
+def bm_group_run(group, count):
+    """Runs the group to convergence; returns (list of result dicts, steps)."""
+    res = (bm_group_result * count)()
+    steps = _i32()
+    _check(_lib.bm_group_run(group, res, ctypes.byref(steps)), "bm_group_run")
+    return [r.as_dict() for r in res], steps.value
+
+
+def bm_group_info(group):
+    grid, segs, smem = _i32(), _i32(), _i64()
+    _check(_lib.bm_group_info(group, ctypes.byref(grid), ctypes.byref(segs),
+                              ctypes.byref(smem)), "bm_group_info")
+    return {"grid": grid.value, "segments": segs.value, "smem": smem.value}
+
+
+def bm_group_destroy(group):
+    _check(_lib.bm_group_destroy(group), "bm_group_destroy")
 
 
 def bm_assign_rows(X_dev, m, n, C_dev, mask_dev, k, labels_dev=None, dmin_dev=None,

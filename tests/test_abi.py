@@ -90,3 +90,26 @@ def test_selftest_rejects_out_of_range_limits_without_a_device():
     import paper_2204_07485_gb300 as bm
     assert bm.bm_selftest_wait_timeout(0) == bm.BM_EINVAL
     assert bm.bm_selftest_wait_timeout(5000) == bm.BM_EINVAL
+
+
+def test_group_entry_points_validate_without_a_device():
+    _ensure_built()
+    import paper_2204_07485_gb300 as bm
+    ok = dict(P=0x1000, s=100, n=4, k=3, C=0x2000, mask=0x3000)
+    bad = [dict(ok, s=2), dict(ok, n=0), dict(ok, k=0), dict(ok, P=None), dict(ok, C=None),
+           dict(ok, mask=None)]
+    for q in bad:
+        with pytest.raises(bm.BigMeansError) as e:
+            bm.bm_group_create([q])
+        assert e.value.status == bm.BM_EINVAL
+    for q in (dict(ok, k=129, s=1000), dict(ok, n=513)):
+        with pytest.raises(bm.BigMeansError) as e:
+            bm.bm_group_create([q])
+        assert e.value.status == bm.BM_EUNSUPPORTED
+    with pytest.raises(bm.BigMeansError) as e:
+        bm.bm_group_create([ok], max_iter=-1)
+    assert e.value.status == bm.BM_EINVAL
+    out = bm._vp()
+    assert bm._lib.bm_group_create(None, 1, 300, 1e-4, 1, None, bm.ctypes.byref(out)) == bm.BM_EINVAL
+    assert bm._lib.bm_group_run(None, None, None) == bm.BM_EINVAL
+    assert bm._lib.bm_group_destroy(None) == bm.BM_OK
