@@ -563,7 +563,7 @@ def run_ours(args, wl):
     chunk_kernel["frac"] = chunk_kernel["achieved"] / chunk_kernel["peak"]
     abytes = m * n * 4 + m * 4
     assign_kernel = {
-        "kernel": "assign_np_kernel<32> (final assignment + FP64 SSE)", "bound": "hbm",
+        "kernel": "assign_np_kernel<28> (final assignment + FP64 SSE)", "bound": "hbm",
         "achieved": abytes / (asg_per_step / 1e3) / 1e9, "peak": hbm_peak,
         "unit": "GB/s", "launch_ms": asg_per_step,
         "share": asg_per_step / (fit_per_step + asg_per_step), "algorithmic_bytes": abytes}

@@ -697,6 +697,45 @@ static bm_status assign_tc_impl(const float* X, long long m, int n, int k,
   int stages, kb, npad16, ncols, cf;
   // room for the kernel's static shared memory and the per-CTA reservation
   const size_t limit = kSmemLimit - 2048;
+  {
+    // rows of at most 128 features: the streaming kernel, one persistent CTA
+    // per SM (TMA column boxes, rows held in registers)
+    int sstages = 0, sncols = 0;
+    const size_t ssmem = assign_tcs_plan(n, k, terms, limit, &sstages, &sncols);
+    const long long tiles = (m + 127) / 128;
+    if (ssmem > 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 && tiles <= w.apart_cap &&
+        m < (1LL << 31)) {
+      int sms = 0, dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      int grid = (int)std::min<long long>(tiles, sms);
+      if (cap > 0) grid = std::min(grid, cap);
+      if (cudaMemsetAsync(w.rescored, 0, sizeof(unsigned long long), st) != cudaSuccess)
+        return BM_ECUDA;
+      const cudaError_t e = launch_assign_tcs(
+          X, m, n, C, cstride, mask, k, labels, dmin, reinterpret_cast<float2*>(w.apart), w.asse,
+          &w.ctl->assign_ticket, w.rescored, &w.ctl->status, terms, sstages, sncols, ssmem, grid,
+          st);
+      if (e == cudaSuccess) {
+        double sse = 0.0;
+        unsigned long long resc = 0;
+        if (cudaMemcpyAsync(&sse, w.asse, sizeof(double), cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(&resc, w.rescored, sizeof(resc), cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess)
+          return BM_ECUDA;
+        const bm_status rc = check_status(w, st, 0);
+        if (rc != BM_OK) return rc;
+        if (sse_out) *sse_out = sse;
+        if (rescored_out) *rescored_out = resc;
+        return BM_OK;
+      }
+      if (e != cudaErrorNotSupported && e != cudaErrorInvalidValue &&
+          e != cudaErrorLaunchOutOfResources)
+        return BM_ECUDA;
+      cudaGetLastError();   // no tensor-map encoder: the tiled kernel below
+    }
+  }
   // bulk copies of row tiles need a 16-byte aligned X
   const bool bulk_ok = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
   size_t smem = assign_tc_smem(n, k, terms, &stages, &kb, &npad16, &ncols, &cf, bulk_ok, limit);

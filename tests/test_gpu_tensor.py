@@ -59,7 +59,9 @@ def test_bf16_rescore_equals_fp32_path_bitwise(bm, m, n, k, seed, prec):
 @pytest.mark.parametrize("m,n,k,seed", [(6000, 128, 50, 0), (2050, 384, 20, 1),
                                         (3001, 33, 100, 2), (1500, 64, 7, 3),
                                         (777, 127, 64, 4), (129, 200, 9, 5),
-                                        (1100, 384, 100, 6)])
+                                        (1100, 384, 100, 6), (4100, 100, 33, 7),
+                                        (2000, 96, 16, 8), (9999, 124, 100, 9),
+                                        (300, 4, 5, 10), (70_001, 128, 50, 11)])
 def test_bf16_rescore_matches_oracle(bm, m, n, k, seed, prec):
     X, C, live = _case(m, n, k, seed)
     lab = torch.empty(m, dtype=torch.int32, device="cuda:0")
