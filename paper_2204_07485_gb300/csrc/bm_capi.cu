@@ -700,8 +700,8 @@ static bm_status assign_tc_impl(const float* X, long long m, int n, int k,
   {
     // rows of at most 128 features: the streaming kernel, one persistent CTA
     // per SM (TMA column boxes, rows held in registers)
-    int sstages = 0, sncols = 0;
-    const size_t ssmem = assign_tcs_plan(n, k, terms, limit, &sstages, &sncols);
+    TcsPlan tp{};
+    const size_t ssmem = assign_tcs_plan(n, k, terms, limit, &tp);
     const long long tiles = (m + 127) / 128;
     if (ssmem > 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 && tiles <= w.apart_cap &&
         m < (1LL << 31)) {
@@ -714,8 +714,7 @@ static bm_status assign_tc_impl(const float* X, long long m, int n, int k,
         return BM_ECUDA;
       const cudaError_t e = launch_assign_tcs(
           X, m, n, C, cstride, mask, k, labels, dmin, reinterpret_cast<float2*>(w.apart), w.asse,
-          &w.ctl->assign_ticket, w.rescored, &w.ctl->status, terms, sstages, sncols, ssmem, grid,
-          st);
+          &w.ctl->assign_ticket, w.rescored, &w.ctl->status, terms, tp, ssmem, grid, st);
       if (e == cudaSuccess) {
         double sse = 0.0;
         unsigned long long resc = 0;

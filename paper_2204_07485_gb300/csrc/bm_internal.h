@@ -251,12 +251,18 @@ inline cudaError_t launch_cooperative(Kernel fn, int grid, int threads, size_t s
 cudaError_t launch_draw(const DrawArgs& a, int chunks, cudaStream_t st);
 // Streaming tensor-core final assignment (n <= 128, n % 4 == 0, k <= 128):
 // shared memory of its plan, 0 when it does not take the shape.
-size_t assign_tcs_plan(int n, int k, int terms, size_t limit, int* stages_out, int* ncols_out);
+struct TcsPlan {
+  int w;        // compute warpgroups
+  int na;       // A-tile buffers
+  int stages;   // 16 KB column boxes in flight
+  int ncols;    // TMEM columns allocated
+};
+size_t assign_tcs_plan(int n, int k, int terms, size_t limit, TcsPlan* out);
 cudaError_t launch_assign_tcs(const float* X, long long m, int n, const float* C, int cstride,
                               const uint8_t* mask, int k, int32_t* labels, float* dmin,
                               float2* part, double* sse, uint32_t* ticket,
-                              unsigned long long* rescored, int* status, int terms, int stages,
-                              int ncols, size_t smem, int grid, cudaStream_t st);
+                              unsigned long long* rescored, int* status, int terms,
+                              const TcsPlan& plan, size_t smem, int grid, cudaStream_t st);
 size_t assign_tc_smem(int n, int k, int terms, int* stages, int* kb, int* npad16,
                       int* ncols, int* cf, bool bulk_ok, size_t limit);
 int assign_tc_max_grid(size_t smem);

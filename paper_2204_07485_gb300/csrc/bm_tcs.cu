@@ -3,11 +3,12 @@
 // rule and exact FP32 rescoring as assign_tc_kernel (bm_tc.cu), organised
 // for HBM rate.
 //
-// One persistent CTA per SM with four roles:
+// One persistent CTA per SM with these roles:
 //   - a TMA warp streams the CTA's 128-row tiles of X into a ring of
 //     shared-memory stages, one 128-byte-wide column box (32 features x 128
 //     rows, 128-byte swizzle) per stage;
-//   - two compute warpgroups take alternate tiles.  Each thread owns one row:
+//   - W compute warpgroups (two, or four for rows of at most 32 features,
+//     whose registers allow it) take tiles in turn.  Each thread owns one row:
 //     it copies the row's boxes from the stages into registers (the swizzle
 //     makes these reads conflict-free) and releases the stages at once, writes
 //     the BF16 (hi[, lo]) operand of the row into the shared A tile and the
@@ -15,8 +16,10 @@
 //     TMEM, keeps the candidates, and rescores them exactly from the row in
 //     its registers and the FP32 centroids in shared memory;
 //   - an MMA warp issues the tile's tcgen05.mma (FP32 accumulators in one of
-//     two TMEM buffers, so one warpgroup's epilogue overlaps the other's
-//     conversion and MMA).
+//     W TMEM buffers, so one warpgroup's epilogue overlaps the others'
+//     conversion and MMA).  The A tile has NA buffers: one per warpgroup
+//     where shared memory allows, so conversions do not wait for each
+//     other's MMAs, else one shared buffer.
 // The FP32 row never goes back to memory after its first read, so stages
 // turn over as fast as HBM fills them.
 #include <algorithm>
@@ -32,27 +35,29 @@
 namespace bm {
 
 constexpr int kTcsRows = 128;
-constexpr int kTcsCompute = 256;                  // two warpgroups
-constexpr int kTcsThreads = kTcsCompute + 64;     // + TMA warp + MMA warp
 constexpr int kTcsBox = 32 * 128 * 4;             // one stage: 32 features x 128 rows FP32
 constexpr int kTcsMaxStages = 8;
+constexpr int kTcsMaxW = 4;
+// W compute warpgroups + the TMA warp + the MMA warp
+__host__ __device__ constexpr int tcs_threads(int W) { return W * 128 + 64; }
 
 struct TcsLayout {
   int sA, sB, stg, cF, cc, bars, holder, pair, total;
 };
 
-__host__ __device__ inline TcsLayout tcs_layout(int nb, int N, int k, int planes, int stages) {
+__host__ __device__ inline TcsLayout tcs_layout(int nb, int N, int k, int planes, int stages,
+                                                int na) {
   const int kb = (nb * 32 + 63) / 64;
   TcsLayout L;
   int o = 0;
-  L.sA = o;    o += planes * kb * kTcsRows * 128;       // A tile, BF16 swizzled
+  L.sA = o;    o += na * planes * kb * kTcsRows * 128;  // A tiles, BF16 swizzled
   L.sB = o;    o += planes * kb * N * 128;              // centroids, BF16 swizzled
   L.stg = o;   o += stages * kTcsBox;                   // FP32 column boxes (TMA)
   L.cF = o;    o += align_up(k * (nb * 32 + 4) * 4, 16);   // FP32 centroids, padded rows
   L.cc = o;    o += align_up(N * 4, 16);                // ||c_j||^2, +inf if not live
-  L.bars = o;  o += (2 * kTcsMaxStages + 5) * 8;
+  L.bars = o;  o += (2 * kTcsMaxStages + 3 * kTcsMaxW) * 8;
   L.holder = o; o += 16;
-  L.pair = o;  o += 8 * 8;                              // per-warp SSE pairs
+  L.pair = o;  o += 4 * kTcsMaxW * 8;                   // per-warp SSE pairs
   L.total = o;
   return L;
 }
@@ -92,11 +97,13 @@ __device__ __forceinline__ void wg_sync(int wg) {
   asm volatile("bar.sync %0, 128;" :: "r"(1 + wg) : "memory");
 }
 
-template <int NB>
-// 320 threads leave 168 registers a thread: rows of up to 96 features stay
-// in registers, 128-feature rows spill a few values to local memory
-__global__ void __launch_bounds__(kTcsThreads, 1)
+// W = 2: 320 threads leave 168 registers a thread (rows of up to 96
+// features stay in registers, 128-feature rows spill a few values); W = 4:
+// 576 threads, rows of up to 32 features.
+template <int NB, int W, int NA>
+__global__ void __launch_bounds__(tcs_threads(W), 1)
 assign_tcs_kernel(const __grid_constant__ CUtensorMap xmap, TcsArgs a) {
+  constexpr int kThreads = tcs_threads(W);
   extern __shared__ __align__(1024) unsigned char tcs_raw[];
   unsigned char* sm = tcs_raw + ((1024u - (smem_u32(tcs_raw) & 1023u)) & 1023u);
   constexpr int NF = NB * 32;                // features held per row (zero padded)
@@ -104,7 +111,7 @@ assign_tcs_kernel(const __grid_constant__ CUtensorMap xmap, TcsArgs a) {
   constexpr int CS = NF + 4;                 // cF row stride (floats)
   const int n = a.n, k = a.k, N = a.N, S = a.stages;
   const int planes = a.terms == 3 ? 2 : 1;
-  const TcsLayout L = tcs_layout(NB, N, k, planes, S);
+  const TcsLayout L = tcs_layout(NB, N, k, planes, S, NA);
   unsigned char* sA = sm + L.sA;
   unsigned char* sB = sm + L.sB;
   float* stg = reinterpret_cast<float*>(sm + L.stg);
@@ -112,21 +119,22 @@ assign_tcs_kernel(const __grid_constant__ CUtensorMap xmap, TcsArgs a) {
   float* cc = reinterpret_cast<float*>(sm + L.cc);
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.bars);
   uint64_t* empty = full + kTcsMaxStages;
-  uint64_t* sa_full = empty + kTcsMaxStages;
-  uint64_t* mma_done = sa_full + 1;      // [2]
-  uint64_t* tmem_free = mma_done + 2;    // [2]
+  uint64_t* sa_full = empty + kTcsMaxStages;   // [NA]
+  uint64_t* mma_done = sa_full + kTcsMaxW;     // [W]
+  uint64_t* tmem_free = mma_done + kTcsMaxW;   // [W]
   uint32_t* holder = reinterpret_cast<uint32_t*>(sm + L.holder);
   float2* pair = reinterpret_cast<float2*>(sm + L.pair);
   __shared__ float s_bound[2];
-  __shared__ float s_cmax[kTcsThreads / 32];
+  __shared__ float s_cmax[kThreads / 32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long ntiles = (a.m + kTcsRows - 1) / kTcsRows;
   const int planeA = KB * kTcsRows * 128, planeB = KB * N * 128;
+  const int bufA = planes * planeA;   // bytes of one A buffer
 
   // ---- set-up: zero A (its K padding stays zero), build B, cF, cc
-  for (int q = tid; q < planes * planeA / 16; q += kTcsThreads)
+  for (int q = tid; q < NA * bufA / 16; q += kThreads)
     reinterpret_cast<uint4*>(sA)[q] = make_uint4(0u, 0u, 0u, 0u);
-  for (int e = tid; e < N * KB * 64; e += kTcsThreads) {
+  for (int e = tid; e < N * KB * 64; e += kThreads) {
     const int j = e / (KB * 64), f = e - j * (KB * 64);
     float v = 0.f;
     if (j < k && f < n && a.mask[j]) v = __ldg(a.C + (size_t)j * a.cstride + f);
@@ -138,10 +146,10 @@ assign_tcs_kernel(const __grid_constant__ CUtensorMap xmap, TcsArgs a) {
       *reinterpret_cast<__nv_bfloat16*>(sB + planeB + off) =
           __float2bfloat16_rn(v - __bfloat162float(h));
   }
-  for (int e = tid; e < k * 4; e += kTcsThreads)   // cF pad columns NF .. NF + 3
+  for (int e = tid; e < k * 4; e += kThreads)   // cF pad columns NF .. NF + 3
     if (KB * 64 < CS) cF[(e >> 2) * CS + KB * 64 + (e & 3)] = 0.f;
   float cmax = 0.f;
-  for (int j = tid; j < N; j += kTcsThreads) {
+  for (int j = tid; j < N; j += kThreads) {
     float s = INFINITY;
     if (j < k && a.mask[j]) {
       s = 0.f;
@@ -162,11 +170,11 @@ assign_tcs_kernel(const __grid_constant__ CUtensorMap xmap, TcsArgs a) {
       mbar_init(full + i, 1);
       mbar_init(empty + i, 128);
     }
-    mbar_init(sa_full, 128);
-    mbar_init(mma_done, 1);
-    mbar_init(mma_done + 1, 1);
-    mbar_init(tmem_free, 128);
-    mbar_init(tmem_free + 1, 128);
+    for (int i = 0; i < NA; ++i) mbar_init(sa_full + i, 128);
+    for (int i = 0; i < W; ++i) {
+      mbar_init(mma_done + i, 1);
+      mbar_init(tmem_free + i, 128);
+    }
     mbar_init_fence();
   }
   if (warp == 0) tmem_alloc(holder, (uint32_t)a.ncols);
@@ -176,7 +184,7 @@ assign_tcs_kernel(const __grid_constant__ CUtensorMap xmap, TcsArgs a) {
   tc_fence_after();
   if (tid == 0) {
     float mx = 0.f;
-    for (int w = 0; w < kTcsThreads / 32; ++w) mx = fmaxf(mx, s_cmax[w]);
+    for (int w = 0; w < kThreads / 32; ++w) mx = fmaxf(mx, s_cmax[w]);
     s_bound[0] = 2.f * eps * sqrtf(mx) * 1.0001f;
     s_bound[1] = (float)(n + 2) * 0x1.0p-22f * mx;
   }
@@ -184,7 +192,7 @@ assign_tcs_kernel(const __grid_constant__ CUtensorMap xmap, TcsArgs a) {
   const uint32_t tmem = *holder;
   bool ok = true;
 
-  if (warp == 8) {
+  if (warp == 4 * W) {
     // ---- TMA producer: boxes in (tile, box) order through the ring
     if (lane == 0) {
       long long seq = 0;
@@ -204,8 +212,8 @@ assign_tcs_kernel(const __grid_constant__ CUtensorMap xmap, TcsArgs a) {
       for (long long q = seq - 1; q >= 0 && q >= seq - S; --q)
         if (!mbar_wait(full + (int)(q % S), (uint32_t)((q / S) & 1))) ok = false;
     }
-  } else if (warp == 9) {
-    // ---- MMA issuer: one tile at a time into TMEM buffer li & 1
+  } else if (warp == 4 * W + 1) {
+    // ---- MMA issuer: tile li from A buffer li % NA into TMEM buffer li % W
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16_f32(kTcsRows, N);
       const uint64_t da = sdesc_sw128(smem_u32(sA));
@@ -214,16 +222,17 @@ assign_tcs_kernel(const __grid_constant__ CUtensorMap xmap, TcsArgs a) {
       for (long long li = 0;; ++li) {
         const long long t = (long long)blockIdx.x + li * gridDim.x;
         if (t >= ntiles) break;
-        if (!mbar_wait(sa_full, (uint32_t)(li & 1))) ok = false;
-        if (li >= 2 && !mbar_wait(tmem_free + (li & 1), (uint32_t)(((li - 2) >> 1) & 1)))
+        if (!mbar_wait(sa_full + (li % NA), (uint32_t)((li / NA) & 1))) ok = false;
+        if (li >= W && !mbar_wait(tmem_free + (li % W), (uint32_t)(((li - W) / W) & 1)))
           ok = false;
         tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)((li & 1) * N);
+        const uint32_t d = tmem + (uint32_t)((li % W) * N);
+        const uint64_t dab = da + (uint64_t)(((li % NA) * bufA) >> 4);
         uint32_t acc = 0;
         for (int b = 0; b < KB; ++b)
           for (int ks = 0; ks < 4; ++ks) {
             const uint64_t off = (uint64_t)((ks * 32) >> 4);
-            const uint64_t ab = da + (uint64_t)((b * kTcsRows * 128) >> 4) + off;
+            const uint64_t ab = dab + (uint64_t)((b * kTcsRows * 128) >> 4) + off;
             const uint64_t bb = db + (uint64_t)((b * N * 128) >> 4) + off;
             tc_mma_bf16(d, ab, bb, idesc, acc);                 // hi * hi
             acc = 1;
@@ -232,23 +241,26 @@ assign_tcs_kernel(const __grid_constant__ CUtensorMap xmap, TcsArgs a) {
               tc_mma_bf16(d, ab + alo, bb, idesc, 1);           // lo * hi
             }
           }
-        tc_commit(mma_done + (li & 1));
+        tc_commit(mma_done + (li % W));
       }
     }
   } else {
-    // ---- compute warpgroups: warpgroup wg takes local tiles wg, wg + 2, ...
+    // ---- compute warpgroups: warpgroup wg takes local tiles wg, wg + W, ...
     const int wg = warp >> 2, r = tid & 127, q = warp & 3;
     const float e_d = (float)(n + 4) * 0x1.0p-22f;
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
     unsigned rescored = 0;
-    for (long long li = wg;; li += 2) {
+    for (long long li = wg;; li += W) {
       const long long t = (long long)blockIdx.x + li * gridDim.x;
       if (t >= ntiles) break;
       const long long row = t * kTcsRows + r;
       const bool valid = row < a.m;
-      // the A tile is free once the previous tile's MMA has completed
-      if (li >= 1 && !mbar_wait(mma_done + ((li - 1) & 1), (uint32_t)(((li - 1) >> 1) & 1)))
+      // A buffer li % NA is free once the MMA of its previous tile, li - NA,
+      // has completed
+      if (li >= NA &&
+          !mbar_wait(mma_done + ((li - NA) % W), (uint32_t)(((li - NA) / W) & 1)))
         ok = false;
+      unsigned char* sAb = sA + (li % NA) * bufA;
       float x[NF];
       float xq = 0.f;
 #pragma unroll
@@ -288,18 +300,18 @@ assign_tcs_kernel(const __grid_constant__ CUtensorMap xmap, TcsArgs a) {
           const int ch = 4 * (b & 1) + c;
           const int off = (b >> 1) * (kTcsRows * 128) + (r >> 3) * 1024 + (r & 7) * 128 +
                           ((ch ^ (r & 7)) << 4);
-          *reinterpret_cast<uint4*>(sA + off) = make_uint4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<uint4*>(sAb + off) = make_uint4(h[0], h[1], h[2], h[3]);
           if (planes == 2)
-            *reinterpret_cast<uint4*>(sA + planeA + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            *reinterpret_cast<uint4*>(sAb + planeA + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
       }
       fence_proxy_async_smem();
-      mbar_arrive(sa_full);
-      if (!mbar_wait(mma_done + (li & 1), (uint32_t)((li >> 1) & 1))) ok = false;
+      mbar_arrive(sa_full + (li % NA));
+      if (!mbar_wait(mma_done + (li % W), (uint32_t)((li / W) & 1))) ok = false;
       tc_fence_after();
 
       // ---- epilogue: candidates from the approximate distances, exact rescoring
-      const uint32_t cols = lane_base + (uint32_t)((li & 1) * N);
+      const uint32_t cols = lane_base + (uint32_t)((li % W) * N);
       const float xqb = xq * 1.00002f;
       const float E1 = fmaf(sqrtf(xqb), s_bound[0], s_bound[1]);
       float m1 = INFINITY;
@@ -325,7 +337,7 @@ assign_tcs_kernel(const __grid_constant__ CUtensorMap xmap, TcsArgs a) {
         else mhi |= (uint64_t)bits << (c0 - 64);
       }
       tc_fence_before();
-      mbar_arrive(tmem_free + (li & 1));   // TMEM buffer free for tile li + 2
+      mbar_arrive(tmem_free + (li % W));   // TMEM buffer free for tile li + W
       if (!valid) mlo = mhi = 0ull;
       float best = INFINITY;
       int bj = INT_MAX, ncand = 0;
@@ -393,18 +405,18 @@ assign_tcs_kernel(const __grid_constant__ CUtensorMap xmap, TcsArgs a) {
   if (s_last) {
     __threadfence();
     float hi = 0.f, lo = 0.f;
-    for (long long i = tid; i < ntiles; i += kTcsThreads) {
+    for (long long i = tid; i < ntiles; i += kThreads) {
       const float2 p = __ldcg(a.part + i);
       two_sum_acc(hi, lo, p.x);
       lo = __fadd_rn(lo, p.y);
     }
     warp_two_sum(hi, lo);
-    __shared__ float2 s_fin[kTcsThreads / 32];
+    __shared__ float2 s_fin[kThreads / 32];
     if (lane == 0) s_fin[warp] = make_float2(hi, lo);
     __syncthreads();
     if (tid == 0) {
       double tot = 0.0;
-      for (int w = 0; w < kTcsThreads / 32; ++w) tot += (double)s_fin[w].x + (double)s_fin[w].y;
+      for (int w = 0; w < kThreads / 32; ++w) tot += (double)s_fin[w].x + (double)s_fin[w].y;
       *a.sse = tot;
       *a.ticket = 0u;
     }
@@ -434,39 +446,58 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-template <int NB>
+template <int NB, int W, int NA>
 cudaError_t launch_tcs_t(const CUtensorMap& map, const TcsArgs& a, int grid, size_t smem,
                          cudaStream_t st) {
-  cudaError_t e = allow_max_smem(assign_tcs_kernel<NB>);
+  cudaError_t e = allow_max_smem(assign_tcs_kernel<NB, W, NA>);
   if (e != cudaSuccess) return e;
-  assign_tcs_kernel<NB><<<grid, kTcsThreads, smem, st>>>(map, a);
+  assign_tcs_kernel<NB, W, NA><<<grid, tcs_threads(W), smem, st>>>(map, a);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 // Plan of the streaming kernel for (n, k, terms): shared memory (0 if the
-// kernel does not take the shape), stages and TMEM columns.
-size_t assign_tcs_plan(int n, int k, int terms, size_t limit, int* stages_out, int* ncols_out) {
+// kernel does not take the shape), warpgroups, A buffers, stages and TMEM
+// columns.  Rows of at most 32 features get four warpgroups with an A buffer
+// each, rows of at most 64 two with one each, wider rows two sharing one;
+// a configuration needs at least three stages (two for the last resort).
+size_t assign_tcs_plan(int n, int k, int terms, size_t limit, TcsPlan* out) {
   if (n < 1 || n > 128 || n % 4 != 0 || k < 1 || k > 128) return 0;
   const int nb = (n + 31) / 32, N = (k + 15) / 16 * 16;
   const int planes = terms == 3 ? 2 : 1;
-  int ncols = 32;
-  while (ncols < 2 * N) ncols <<= 1;
-  int stages = 0;
-  for (int s = kTcsMaxStages; s >= 2; --s)
-    if ((size_t)tcs_layout(nb, N, k, planes, s).total + 1024 <= limit) { stages = s; break; }
-  if (stages < 2) return 0;
-  *stages_out = stages;
-  *ncols_out = ncols;
-  return (size_t)tcs_layout(nb, N, k, planes, stages).total + 1024;
+  struct Cfg { int w, na, min_stages; };
+  Cfg cfgs[3];
+  int nc = 0;
+  if (nb == 1) cfgs[nc++] = {4, 4, 3};
+  if (nb <= 2) cfgs[nc++] = {2, 2, 3};
+  cfgs[nc++] = {2, 1, 2};
+  for (int i = 0; i < nc; ++i) {
+    const Cfg c = cfgs[i];
+    if (c.w * N > 512) continue;   // TMEM columns
+    int stages = 0;
+    for (int s = kTcsMaxStages; s >= c.min_stages; --s)
+      if ((size_t)tcs_layout(nb, N, k, planes, s, c.na).total + 1024 <= limit) {
+        stages = s;
+        break;
+      }
+    if (!stages) continue;
+    int ncols = 32;
+    while (ncols < c.w * N) ncols <<= 1;
+    out->w = c.w;
+    out->na = c.na;
+    out->stages = stages;
+    out->ncols = ncols;
+    return (size_t)tcs_layout(nb, N, k, planes, stages, c.na).total + 1024;
+  }
+  return 0;
 }
 
 cudaError_t launch_assign_tcs(const float* X, long long m, int n, const float* C, int cstride,
                               const uint8_t* mask, int k, int32_t* labels, float* dmin,
                               float2* part, double* sse, uint32_t* ticket,
-                              unsigned long long* rescored, int* status, int terms, int stages,
-                              int ncols, size_t smem, int grid, cudaStream_t st) {
+                              unsigned long long* rescored, int* status, int terms,
+                              const TcsPlan& plan, size_t smem, int grid, cudaStream_t st) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;
   // X as a 2-D tensor: dim 0 = features (contiguous), dim 1 = rows; boxes of
@@ -481,15 +512,18 @@ cudaError_t launch_assign_tcs(const float* X, long long m, int n, const float* C
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   TcsArgs a{};
-  a.m = m; a.n = n; a.k = k; a.N = (k + 15) / 16 * 16; a.terms = terms; a.stages = stages;
-  a.ncols = ncols; a.C = C; a.cstride = cstride; a.mask = mask; a.labels = labels; a.dmin = dmin;
-  a.part = part; a.sse = sse; a.ticket = ticket; a.rescored = rescored; a.status = status;
-  switch ((n + 31) / 32) {
-    case 1: return launch_tcs_t<1>(map, a, grid, smem, st);
-    case 2: return launch_tcs_t<2>(map, a, grid, smem, st);
-    case 3: return launch_tcs_t<3>(map, a, grid, smem, st);
-    default: return launch_tcs_t<4>(map, a, grid, smem, st);
-  }
+  a.m = m; a.n = n; a.k = k; a.N = (k + 15) / 16 * 16; a.terms = terms;
+  a.stages = plan.stages; a.ncols = plan.ncols; a.C = C; a.cstride = cstride; a.mask = mask;
+  a.labels = labels; a.dmin = dmin; a.part = part; a.sse = sse; a.ticket = ticket;
+  a.rescored = rescored; a.status = status;
+  const int nb = (n + 31) / 32;
+  if (nb == 1 && plan.w == 4) return launch_tcs_t<1, 4, 4>(map, a, grid, smem, st);
+  if (nb == 1 && plan.na == 2) return launch_tcs_t<1, 2, 2>(map, a, grid, smem, st);
+  if (nb == 1) return launch_tcs_t<1, 2, 1>(map, a, grid, smem, st);
+  if (nb == 2 && plan.na == 2) return launch_tcs_t<2, 2, 2>(map, a, grid, smem, st);
+  if (nb == 2) return launch_tcs_t<2, 2, 1>(map, a, grid, smem, st);
+  if (nb == 3) return launch_tcs_t<3, 2, 1>(map, a, grid, smem, st);
+  return launch_tcs_t<4, 2, 1>(map, a, grid, smem, st);
 }
 
 }  // namespace bm
