@@ -319,7 +319,8 @@ bm_status bm_selftest_wait_timeout(int32_t timeout_ms, void* stream);
  * one launch that updates all their centroids, and a recorded CUDA graph
  * replays the steps.  The rows of all problems are cut into per-CTA ranges
  * of equal cost, so one large problem spreads over many SMs and small ones
- * share an SM.  Each problem ends where bm_lloyd alone would: the same stop
+ * share an SM; between replays the unfinished problems are cut again over
+ * the whole GPU.  Each problem ends where bm_lloyd alone would: the same stop
  * rule, the same degenerate-cluster handling (live centroids that lose every
  * member become degenerate), objectives and centroids equal to rounding
  * (the sums run over a different row partition). */
@@ -359,7 +360,8 @@ bm_status bm_group_create(const bm_group_problem* problems, int32_t count,
  * outcome, *steps_out (may be NULL) the Lloyd steps launched. */
 bm_status bm_group_run(bm_group* group, bm_group_result* results_host, int32_t* steps_out);
 
-/* The plan: CTAs of the assignment launch, segments, dynamic shared memory. */
+/* The plan: CTAs of the assignment launch, segments of the partition of all
+ * problems, dynamic shared memory. */
 bm_status bm_group_info(bm_group* group, int32_t* grid_out, int32_t* segments_out,
                         int64_t* smem_out);
 

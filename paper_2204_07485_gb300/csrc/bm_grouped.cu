@@ -22,8 +22,11 @@
 //     members, the centroid update unless stopping, and the problem's state.
 //
 // A CUDA graph of a few steps is recorded once and replayed until no
-// problem is left; finished problems cost a flag test per segment.  Every
-// sum has a fixed order, so results are reproducible.
+// problem is left; finished problems cost a flag test per segment, and after
+// a replay that finished some problems the tile list of the others is cut
+// again over all CTAs (the tables live in device memory, so the recorded
+// graph stays valid).  Every sum has a fixed order and the partitions depend
+// only on the data, so results are reproducible.
 #include <algorithm>
 #include <climits>
 #include <cstdint>
@@ -40,7 +43,7 @@
 namespace bm {
 
 constexpr int kGroupThreads = 256;   // nearest_tile: 8 warps x 8 rows
-constexpr int kGroupStepsPerGraph = 4;
+constexpr int kGroupStepsPerGraph = 2;
 constexpr size_t kGroupSmemLimit = 227 * 1024;
 
 struct GroupProb {
@@ -256,13 +259,18 @@ using namespace bm;
 struct bm_group {
   int device = 0;
   cudaStream_t stream = nullptr;
-  int count = 0, grid = 0, nseg = 0;
+  int count = 0, grid = 0, nseg = 0, max_seg = 0;
+  int nseg_all = 0;             // segments of the partition of every problem
+  bool balance = true;
   size_t smem = 0;
   int max_iter = 300;
   GroupArgs args{};
   void* dev_block = nullptr;    // every device array of the group, one allocation
   int* active_host = nullptr;   // pinned
-  std::vector<int64_t> s_of;
+  std::vector<GroupProb> hp;    // problems (host copy; slots rewritten per partition)
+  std::vector<int> tiles;       // 64-row tiles per problem
+  std::vector<double> tile_cost;
+  long long sum_cap = 0, cnt_cap = 0;   // room of the partial-result arrays
   cudaGraphExec_t graph = nullptr;
 };
 
@@ -284,6 +292,85 @@ bm_status enqueue_steps(bm_group* g, int steps) {
     group_update_kernel<<<gu, kGroupThreads, 0, g->stream>>>(g->args);
   }
   return cudaGetLastError() == cudaSuccess ? BM_OK : BM_ECUDA;
+}
+
+// Cuts the tiles of the problems with active[i] set into per-CTA ranges of
+// equal cost (balance) or gives each such problem one CTA, assigns the
+// segments their slots, and uploads the tables on the group's stream.  Every
+// problem's slots are adjacent and in CTA order.
+bm_status group_partition(bm_group* g, const std::vector<char>& active) {
+  const int count = g->count, grid = g->grid;
+  std::vector<GroupSeg> segs;
+  std::vector<int> cta_seg;
+  if (g->balance) {
+    double total = 0.0;
+    for (int i = 0; i < count; ++i)
+      if (active[i]) total += g->tile_cost[i] * g->tiles[i];
+    const double per = total > 0.0 ? total / grid : 1.0;
+    double acc = 0.0;
+    int cta = 0;
+    cta_seg.push_back(0);
+    for (int i = 0; i < count; ++i) {
+      if (!active[i]) continue;
+      for (int t = 0; t < g->tiles[i]; ++t) {
+        // a tile goes to the CTA whose range holds its cost midpoint
+        const int want = std::min(grid - 1, (int)((acc + 0.5 * g->tile_cost[i]) / per));
+        while (cta < want) {
+          ++cta;
+          cta_seg.push_back((int)segs.size());
+        }
+        if (cta_seg.back() < (int)segs.size() && segs.back().prob == i && segs.back().t1 == t)
+          segs.back().t1 = t + 1;
+        else
+          segs.push_back(GroupSeg{i, t, t + 1});
+        acc += g->tile_cost[i];
+      }
+    }
+    while (cta < grid - 1) {
+      ++cta;
+      cta_seg.push_back((int)segs.size());
+    }
+    cta_seg.push_back((int)segs.size());
+  } else {
+    // grid == count: CTA i owns problem i
+    for (int i = 0; i < count; ++i) {
+      cta_seg.push_back((int)segs.size());
+      if (active[i]) segs.push_back(GroupSeg{i, 0, g->tiles[i]});
+    }
+    cta_seg.push_back((int)segs.size());
+  }
+  const int nseg = (int)segs.size();
+  if (nseg > g->max_seg) return BM_ECUDA;   // cannot happen: nseg <= grid + count
+  std::vector<GroupSlotOff> offs(nseg);
+  long long sum_total = 0, cnt_total = 0;
+  for (int i = 0; i < count; ++i) { g->hp[i].slot0 = 0; g->hp[i].slot1 = 0; }
+  std::vector<char> seen(count, 0);
+  for (int sg = 0; sg < nseg; ++sg) {
+    GroupProb& p = g->hp[segs[sg].prob];
+    offs[sg].sum = sum_total;
+    offs[sg].cnt = cnt_total;
+    sum_total += (long long)p.k * p.npad;
+    cnt_total += p.k;
+    if (!seen[segs[sg].prob]) { p.slot0 = sg; seen[segs[sg].prob] = 1; }
+    p.slot1 = sg + 1;
+  }
+  if (sum_total > g->sum_cap || cnt_total > g->cnt_cap) return BM_ECUDA;
+  g->nseg = nseg;
+  cudaStream_t st = g->stream;
+  GroupArgs& ga = g->args;
+  if (cudaMemcpyAsync((void*)ga.probs, g->hp.data(), sizeof(GroupProb) * count,
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      (nseg > 0 && cudaMemcpyAsync((void*)ga.segs, segs.data(), sizeof(GroupSeg) * nseg,
+                                   cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+      (nseg > 0 && cudaMemcpyAsync((void*)ga.offs, offs.data(), sizeof(GroupSlotOff) * nseg,
+                                   cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+      cudaMemcpyAsync((void*)ga.cta_seg, cta_seg.data(), sizeof(int) * cta_seg.size(),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {   // the host vectors die here
+    cudaGetLastError();
+    return BM_ECUDA;
+  }
+  return BM_OK;
 }
 
 }  // namespace
@@ -322,13 +409,21 @@ bm_status bm_group_create(const bm_group_problem* probs, int32_t count, int32_t 
       per_sm < 1)
     return BM_EUNSUPPORTED;
 
-  std::vector<GroupProb> hp(count);
-  std::vector<double> tile_cost(count);
-  std::vector<int> tiles(count);
-  double total = 0.0;
+  bm_group* g = new (std::nothrow) bm_group();
+  if (!g) return BM_ENOMEM;
+  g->device = dev;
+  g->stream = static_cast<cudaStream_t>(stream);
+  g->count = count;
+  g->balance = balance != 0;
+  g->grid = g->balance ? per_sm * sms : count;
+  g->smem = L.total;
+  g->max_iter = max_iter;
+  g->hp.resize(count);
+  g->tiles.resize(count);
+  g->tile_cost.resize(count);
   for (int i = 0; i < count; ++i) {
     const bm_group_problem& q = probs[i];
-    GroupProb& p = hp[i];
+    GroupProb& p = g->hp[i];
     p.P = q.P_dev;
     p.C = q.C_dev;
     p.mask = q.mask_dev;
@@ -339,95 +434,33 @@ bm_status bm_group_create(const bm_group_problem* probs, int32_t count, int32_t 
     p.k = q.k;
     p.kpad = align_up(q.k, 32);
     int ng = std::min(kGroupThreads / p.npad, acc_floats / (p.k * p.npad));
-    ng = std::max(1, std::min(ng, 8));
-    p.ng = ng;
-    tiles[i] = (int)((q.s + 63) / 64);
-    tile_cost[i] = (double)q.n * (double)(p.kpad / 32 + 1);
-    total += tile_cost[i] * tiles[i];
+    p.ng = std::max(1, std::min(ng, 8));
+    g->tiles[i] = (int)((q.s + 63) / 64);
+    g->tile_cost[i] = (double)q.n * (double)(p.kpad / 32 + 1);
   }
-  // partition: balance = 1 cuts the tile list into per-CTA ranges of equal
-  // cost; balance = 0 gives every problem one CTA of its own
-  std::vector<GroupSeg> segs;
-  std::vector<int> cta_seg;
-  int grid = 0;
-  if (balance) {
-    grid = per_sm * sms;
-    const double per = total / grid;
-    double acc = 0.0;
-    int cta = 0;
-    cta_seg.push_back(0);
-    for (int i = 0; i < count; ++i) {
-      for (int t = 0; t < tiles[i]; ++t) {
-        // a tile goes to the CTA whose range holds its cost midpoint
-        const double mid = acc + 0.5 * tile_cost[i];
-        int want = std::min(grid - 1, (int)(mid / per));
-        while (cta < want) {
-          ++cta;
-          cta_seg.push_back((int)segs.size());
-        }
-        if (!segs.empty() && (int)cta_seg.back() < (int)segs.size() &&
-            segs.back().prob == i && segs.back().t1 == t) {
-          segs.back().t1 = t + 1;
-        } else {
-          segs.push_back(GroupSeg{i, t, t + 1});
-        }
-        acc += tile_cost[i];
-      }
-    }
-    while (cta < grid - 1) {
-      ++cta;
-      cta_seg.push_back((int)segs.size());
-    }
-    cta_seg.push_back((int)segs.size());
-  } else {
-    grid = count;
-    for (int i = 0; i < count; ++i) {
-      cta_seg.push_back(i);
-      segs.push_back(GroupSeg{i, 0, tiles[i]});
-    }
-    cta_seg.push_back(count);
+  // any partition has at most grid + count segments; each slot holds one
+  // problem's [k][npad] sums and [k] counts
+  g->max_seg = g->grid + count;
+  long long kn_big = 0, k_big = 0;
+  for (int i = 0; i < count; ++i) {
+    kn_big = std::max(kn_big, (long long)g->hp[i].k * g->hp[i].npad);
+    k_big = std::max(k_big, (long long)g->hp[i].k);
   }
-  const int nseg = (int)segs.size();
-  // slots: segment order is CTA order, and a problem's segments are adjacent
-  std::vector<GroupSlotOff> offs(nseg);
-  long long sum_total = 0, cnt_total = 0;
-  for (int i = 0; i < count; ++i) { hp[i].slot0 = INT_MAX; hp[i].slot1 = 0; }
-  for (int sg = 0; sg < nseg; ++sg) {
-    GroupProb& p = hp[segs[sg].prob];
-    offs[sg].sum = sum_total;
-    offs[sg].cnt = cnt_total;
-    sum_total += (long long)p.k * p.npad;
-    cnt_total += p.k;
-    p.slot0 = std::min(p.slot0, sg);
-    p.slot1 = std::max(p.slot1, sg + 1);
-  }
-
-  bm_group* g = new (std::nothrow) bm_group();
-  if (!g) return BM_ENOMEM;
-  g->device = dev;
-  g->stream = static_cast<cudaStream_t>(stream);
-  g->count = count;
-  g->grid = grid;
-  g->nseg = nseg;
-  g->smem = L.total;
-  g->max_iter = max_iter;
+  g->sum_cap = kn_big * g->max_seg;
+  g->cnt_cap = k_big * g->max_seg;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t b_probs = al(sizeof(GroupProb) * count);
-  const size_t b_segs = al(sizeof(GroupSeg) * nseg);
-  const size_t b_offs = al(sizeof(GroupSlotOff) * nseg);
-  const size_t b_cta = al(sizeof(int) * cta_seg.size());
-  const size_t b_sum = al(sizeof(float) * (size_t)sum_total);
-  const size_t b_cnt = al(sizeof(int) * (size_t)cnt_total);
-  const size_t b_f = al(sizeof(double) * nseg);
+  const size_t b_segs = al(sizeof(GroupSeg) * g->max_seg);
+  const size_t b_offs = al(sizeof(GroupSlotOff) * g->max_seg);
+  const size_t b_cta = al(sizeof(int) * (g->grid + 1));
+  const size_t b_sum = al(sizeof(float) * (size_t)g->sum_cap);
+  const size_t b_cnt = al(sizeof(int) * (size_t)g->cnt_cap);
+  const size_t b_f = al(sizeof(double) * g->max_seg);
   const size_t b_st = al(sizeof(GroupState) * count);
   const size_t b_act = al(sizeof(int));
   const size_t bytes = b_probs + b_segs + b_offs + b_cta + b_sum + b_cnt + b_f + b_st + b_act;
-  if (cudaMalloc(&g->dev_block, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    group_free(g);
-    return BM_ENOMEM;
-  }
-  if (cudaMallocHost(&g->active_host, sizeof(int)) != cudaSuccess) {
+  if (cudaMalloc(&g->dev_block, bytes) != cudaSuccess ||
+      cudaMallocHost(&g->active_host, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     group_free(g);
     return BM_ENOMEM;
@@ -450,19 +483,12 @@ bm_status bm_group_create(const bm_group_problem* probs, int32_t count, int32_t 
   ga.npad_max = npad_max;
   ga.kpad_max = kpad_max;
   ga.acc_floats = acc_floats;
-  cudaStream_t st = g->stream;
-  cudaMemcpyAsync((void*)ga.probs, hp.data(), sizeof(GroupProb) * count, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync((void*)ga.segs, segs.data(), sizeof(GroupSeg) * nseg, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync((void*)ga.offs, offs.data(), sizeof(GroupSlotOff) * nseg, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync((void*)ga.cta_seg, cta_seg.data(), sizeof(int) * cta_seg.size(),
-                  cudaMemcpyHostToDevice, st);
-  if (cudaStreamSynchronize(st) != cudaSuccess) {
-    cudaGetLastError();
+  const bm_status rc = group_partition(g, std::vector<char>(count, 1));
+  if (rc != BM_OK) {
     group_free(g);
-    return BM_ECUDA;
+    return rc;
   }
-  g->s_of.resize(count);
-  for (int i = 0; i < count; ++i) g->s_of[i] = probs[i].s;
+  g->nseg_all = g->nseg;
   *out = g;
   return BM_OK;
 }
@@ -470,18 +496,21 @@ bm_status bm_group_create(const bm_group_problem* probs, int32_t count, int32_t 
 bm_status bm_group_run(bm_group* g, bm_group_result* results, int32_t* steps_out) {
   if (!g) return BM_EINVAL;
   cudaStream_t st = g->stream;
+  std::vector<char> active(g->count, 1);
+  bm_status rc = group_partition(g, active);
+  if (rc != BM_OK) return rc;
   group_reset_kernel<<<(g->count + 255) / 256, 256, 0, st>>>(g->args.st, g->count, g->args.active);
   if (cudaGetLastError() != cudaSuccess) return BM_ECUDA;
   if (!g->graph && st != nullptr) {
-    // record a few steps once; replays re-read every input from device memory
+    // record a few steps once; replays re-read every table from device memory
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       cudaGetLastError();
       return BM_ECUDA;
     }
-    const bm_status rc = enqueue_steps(g, kGroupStepsPerGraph);
+    const bm_status erc = enqueue_steps(g, kGroupStepsPerGraph);
     const cudaError_t ce = cudaStreamEndCapture(st, &graph);
-    if (rc != BM_OK || ce != cudaSuccess ||
+    if (erc != BM_OK || ce != cudaSuccess ||
         cudaGraphInstantiate(&g->graph, graph, 0) != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
       g->graph = nullptr;
@@ -492,7 +521,8 @@ bm_status bm_group_run(bm_group* g, bm_group_result* results, int32_t* steps_out
   }
   // every problem stops within max_iter + 1 assignments
   const int max_steps = g->max_iter + 1;
-  int steps = 0;
+  std::vector<GroupState> hs(g->count);
+  int steps = 0, last_active = g->count;
   while (true) {
     if (g->graph) {
       if (cudaGraphLaunch(g->graph, st) != cudaSuccess) { cudaGetLastError(); return BM_ECUDA; }
@@ -506,11 +536,23 @@ bm_status bm_group_run(bm_group* g, bm_group_result* results, int32_t* steps_out
       cudaGetLastError();
       return BM_ECUDA;
     }
-    if (*g->active_host <= 0) break;
+    const int now = *g->active_host;
+    if (now <= 0) break;
     if (steps >= max_steps + kGroupStepsPerGraph) return BM_ECUDA;   // cannot happen
+    if (now < last_active && g->balance) {
+      // spread the unfinished problems over the whole GPU again
+      if (cudaMemcpy(hs.data(), g->args.st, sizeof(GroupState) * g->count,
+                     cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return BM_ECUDA;
+      }
+      for (int i = 0; i < g->count; ++i) active[i] = hs[i].done == 0;
+      rc = group_partition(g, active);
+      if (rc != BM_OK) return rc;
+      last_active = now;
+    }
   }
   if (results) {
-    std::vector<GroupState> hs(g->count);
     if (cudaMemcpyAsync(hs.data(), g->args.st, sizeof(GroupState) * g->count,
                         cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
@@ -532,7 +574,7 @@ bm_status bm_group_info(bm_group* g, int32_t* grid_out, int32_t* segments_out,
                         int64_t* smem_out) {
   if (!g) return BM_EINVAL;
   if (grid_out) *grid_out = g->grid;
-  if (segments_out) *segments_out = g->nseg;
+  if (segments_out) *segments_out = g->nseg_all;
   if (smem_out) *smem_out = (int64_t)g->smem;
   return BM_OK;
 }

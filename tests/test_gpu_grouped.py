@@ -145,7 +145,7 @@ def test_iteration_cap(bm):
     refs = [o.lloyd(P, C0.astype(np.float64), np.ones(C0.shape[0], bool), max_iter=2)
             for P, C0 in probs]
     out, steps, _ = _group(bm, probs, max_iter=2)
-    assert steps <= 4 + 3
+    assert steps <= 2 + 3
     for ro, (r, C, mask, _) in zip(refs, out):
         assert r["iters"] == ro.iters <= 2
         assert rel(r["f"], ro.f) <= OBJ_REL
