@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-grouped", action="store_true")
-    ap.add_argument("--profile", choices=["chunk_np", "chunk_tc", "assign_tc"], default=None,
+    ap.add_argument("--profile", choices=["chunk_np", "chunk_tc", "assign_tc", "grouped"],
+                    default=None,
                     help="run one short job of a kernel family (for ncu captures) and exit")
     ap.add_argument("--chunks", type=int, default=WORKLOAD["chunks"])
     return ap.parse_args()
@@ -657,11 +658,39 @@ PROFILE_CASES = {
 }
 
 
+def profile_grouped(count=64):
+    """The first `count` chunks of the grouped workload run once (for ncu)."""
+    import torch
+    import bminputs
+    import paper_2204_07485_gb300 as bm
+    dev = torch.device("cuda", 0)
+    spec = bminputs.mixtures.grouped_chunks_spec(0, count)
+    probs = []
+    for q in spec:
+        P = bminputs.mixtures.isotropic_blobs_device(q["s"], q["n"], q["k"], q["seed"],
+                                                     device=dev)
+        rows = torch.from_numpy(bminputs.mixtures.forgy_rows(q["s"], q["k"], q["seed"])).to(dev)
+        probs.append(dict(P=P, s=q["s"], n=q["n"], k=q["k"], C=P[rows].contiguous(),
+                          mask=torch.ones(q["k"], dtype=torch.uint8, device=dev)))
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize(dev)
+    g = bm.bm_group_create(probs, stream=stream)
+    try:
+        res, steps = bm.bm_group_run(g, count)
+    finally:
+        bm.bm_group_destroy(g)
+    print(json.dumps({"profile": "grouped", "problems": count, "steps": steps,
+                      "max_iters": max(r["iters"] for r in res)}))
+    return 0
+
+
 def profile_case(name):
     """One short job of the named kernel family (for ncu; prints one line)."""
     import torch
     import bminputs
     import paper_2204_07485_gb300 as bm
+    if name == "grouped":
+        return profile_grouped()
     m, n, k, s, prec, T = PROFILE_CASES[name]
     dev = torch.device("cuda", 0)
     if n == 28:

@@ -95,7 +95,7 @@ struct GroupSmem {
 __host__ __device__ inline GroupSmem group_smem(int npad_max, int kpad_max, int acc_floats) {
   GroupSmem L;
   int o = 0;
-  L.cenT = o;  o += align_up(npad_max * kpad_max * 4, 16);   // centroids [f][kpad]
+  L.cenT = o;  o += align_up(npad_max * (kpad_max + 1) * 4, 16);   // centroids [f][kpad + 1]
   L.stage = o; o += align_up(64 * npad_max * 4, 16);         // staged tile
   L.acc = o;   o += align_up(acc_floats * 4, 16);            // [ng][k][npad] sums
   L.cnt = o;   o += align_up(8 * kpad_max * 4, 16);          // [ng][k] counts
@@ -123,10 +123,13 @@ group_assign_kernel(GroupArgs a) {
     if (__ldcg(&a.st[seg.prob].done)) continue;   // uniform over the CTA
     const GroupProb p = a.probs[seg.prob];
     const int n = p.n, npad = p.npad, k = p.k, kpad = p.kpad, ng = p.ng;
+    // centroid rows are kpad + 1 floats apart, so that the update's reads of
+    // one centroid's features fall in different banks (the scan reads rows)
+    const int cs = kpad + 1;
     __syncthreads();   // the previous segment is done with shared memory
     for (int e = threadIdx.x; e < npad * kpad; e += blockDim.x) {
       const int f = e / kpad, j = e - f * kpad;
-      cenT[e] = (j < k && f < n) ? __ldcg(p.C + (size_t)j * n + f) : 0.f;
+      cenT[f * cs + j] = (j < k && f < n) ? __ldcg(p.C + (size_t)j * n + f) : 0.f;
     }
     for (int j = threadIdx.x; j < kpad; j += blockDim.x)
       live[j] = j < k && __ldcg(reinterpret_cast<const unsigned char*>(p.mask) + j) != 0;
@@ -141,7 +144,8 @@ group_assign_kernel(GroupArgs a) {
       stage_tile(stage, p.P + (size_t)r0 * n, n, rows, n, npad, vec4, false);
       int j;
       float d;
-      if (nearest_tile(stage, cenT, live, k, kpad, n, rows, j, d)) {
+      // (nearest_tile takes the row stride as its kpad: cs >> 5 == kpad >> 5)
+      if (nearest_tile(stage, cenT, live, k, cs, n, rows, j, d)) {
         const int r = w * 8 + l;
         lab[r] = j;
         fa += (double)d;
@@ -157,7 +161,7 @@ group_assign_kernel(GroupArgs a) {
         for (int r = g; r < rows; r += ng) {
           const int jr = lab[r];
           if (jr >= k) continue;
-          ag[jr * npad + f] += stage[f * 64 + (r ^ sz)] - cenT[f * kpad + jr];
+          ag[jr * npad + f] += stage[f * 64 + (r ^ sz)] - cenT[f * cs + jr];
           if (f == 0) cnt[g * k + jr] += 1;
         }
       }

@@ -554,7 +554,6 @@ template <int NP, bool GENERIC>
 __device__ bool phase_kpp(const ChunkArgs& a, const Smem& S, GridBarrier& gb,
                           int r0, int nrows, long long* nd_out) {
   const int k = a.k, G = gridDim.x, b = blockIdx.x;
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int nlive = S.lidx[k];
   if (nlive == k) return true;
   if (a.init == kInitForgy) {
