@@ -207,9 +207,10 @@ bm_status bm_set_state(bm_ctx* ctx, const float* C_host,
  * CTA 0's rows, [4] wait at the first Lloyd grid barrier, [5] cross-CTA
  * reduction + centroid update, [6] wait at the second barrier + reload,
  * [7] keep-the-best; [8], [9], [10] split [3] -- row-in-register kernels:
- * the assignment, the per-warp update slices and their combination into the
- * partial sums; tensor-core kernel: the tensor-core candidate pass, the
- * multi-candidate rows plus the label sort, and the staged exact sweep.
+ * the assignment, the stable sort of the rows by label, and the per-centroid
+ * sums into the partial sums; tensor-core kernel: the tensor-core candidate
+ * pass, the multi-candidate rows plus the label sort, and the staged exact
+ * sweep.
  * ns_out receives min(count, 11) values.  The times are collected only by
  * contexts created with cfg.trace = 1 (each timer read sits on CTA 0's path
  * to the next grid barrier, so tracing slows the run slightly); otherwise
@@ -218,8 +219,10 @@ bm_status bm_trace(bm_ctx* ctx, double* ns_out, int32_t count);
 
 /* One-call job on HOST memory: copies X_host (m x n) to the device, runs
  * `chunks` chunks and the final assignment, and copies back C (k x n),
- * mask (k), labels (m) and f(C, X).  Outputs may be NULL.  Uses and frees
- * its own device memory and stream. */
+ * mask (k), labels (m) and f(C, X).  Outputs may be NULL.  Uses its own
+ * stream; its device memory comes from a stream-ordered pool per device that
+ * the library keeps (with the freed blocks, for the next call) until the
+ * process exits. */
 bm_status bm_fit_host(const bm_config* cfg, const float* X_host,
                       int32_t chunks, float* C_out_host,
                       uint8_t* mask_out_host, int32_t* labels_out_host,

@@ -274,8 +274,8 @@ def bm_set_state(ctx, C_host, mask_host, f_opt, chunk_counter):
 
 
 PHASES = ("setup", "gather", "kmeanspp", "lloyd_own_rows", "lloyd_barrier1",
-          "lloyd_reduce", "lloyd_barrier2", "keep", "own_assign", "own_slices",
-          "own_combine")
+          "lloyd_reduce", "lloyd_barrier2", "keep", "own_assign", "own_sort",
+          "own_sums")
 
 
 def bm_trace(ctx):

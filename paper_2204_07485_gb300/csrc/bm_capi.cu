@@ -1126,12 +1126,40 @@ bm_status bm_set_state(bm_ctx* c, const float* C_host, const uint8_t* mask_host,
   return BM_OK;
 }
 
+// Device memory of bm_fit_host: a stream-ordered pool per device that keeps
+// freed blocks for the next call (held until the process exits), so repeated
+// calls neither pay for cudaMalloc nor synchronise the device in cudaFree.
+static cudaMemPool_t fit_host_pool(int dev) {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  uint64_t keep = UINT64_MAX;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  pools[dev] = pool;
+  return pool;
+}
+
 bm_status bm_fit_host(const bm_config* cfg, const float* X_host, int32_t chunks,
                       float* C_out_host, uint8_t* mask_out_host,
                       int32_t* labels_out_host, double* sse_out,
                       bm_fit_report* report) {
   if (!cfg || !X_host || chunks < 0) return BM_EINVAL;
   if (!shape_ok(cfg->m, cfg->n, cfg->k, cfg->s)) return BM_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return BM_ECUDA; }
+  cudaMemPool_t pool = fit_host_pool(dev);
+  if (!pool) return BM_ECUDA;
   cudaStream_t st = nullptr;
   if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return BM_ECUDA;
   float* X = nullptr;
@@ -1139,14 +1167,25 @@ bm_status bm_fit_host(const bm_config* cfg, const float* X_host, int32_t chunks,
   const size_t xbytes = (size_t)cfg->m * cfg->n * 4;
   bm_status rc = BM_OK;
   bm_ctx* c = nullptr;
-  if (cudaMalloc(&X, xbytes) != cudaSuccess) { rc = BM_ENOMEM; goto done; }
-  if (labels_out_host && cudaMalloc(&labels, (size_t)cfg->m * 4) != cudaSuccess) { rc = BM_ENOMEM; goto done; }
+  if (cudaMallocFromPoolAsync(reinterpret_cast<void**>(&X), xbytes, pool, st) != cudaSuccess) {
+    cudaGetLastError();
+    rc = BM_ENOMEM;
+    goto done;
+  }
+  if (labels_out_host &&
+      cudaMallocFromPoolAsync(reinterpret_cast<void**>(&labels), (size_t)cfg->m * 4, pool, st) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    rc = BM_ENOMEM;
+    goto done;
+  }
   if (cudaMemcpyAsync(X, X_host, xbytes, cudaMemcpyHostToDevice, st) != cudaSuccess) { rc = BM_ECUDA; goto done; }
   {
-    // a one-shot context: recording a graph would not pay for itself
+    // a one-shot context: recording a graph would not pay for itself; its
+    // workspace comes from the same pool
     bm_config once = *cfg;
     once.graphs = 0;
-    rc = bm_create(&once, X, st, &c);
+    rc = bm::ctx_create(&once, X, st, pool, &c, 0);
   }
   if (rc != BM_OK) goto done;
   rc = bm_fit_chunk(c, chunks, report);
@@ -1159,8 +1198,9 @@ bm_status bm_fit_host(const bm_config* cfg, const float* X_host, int32_t chunks,
   rc = bm_objective(c, nullptr, C_out_host, mask_out_host);
 done:
   if (c) bm_destroy(c);
-  if (labels) cudaFree(labels);
-  if (X) cudaFree(X);
+  if (labels) cudaFreeAsync(labels, st);
+  if (X) cudaFreeAsync(X, st);
+  cudaStreamSynchronize(st);
   cudaStreamDestroy(st);
   return rc;
 }

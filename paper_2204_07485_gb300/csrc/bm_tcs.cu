@@ -429,20 +429,19 @@ assign_tcs_kernel(const __grid_constant__ CUtensorMap xmap, TcsArgs a) {
 // ------------------------------------------------------------------ host
 namespace {
 
+// The driver's tensor-map encoder, looked up once (thread-safe static
+// initialisation: server workers call this concurrently).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     cudaDriverEntryPointQueryResult q{};
     void* p = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    else
-      cudaGetLastError();
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+    return static_cast<PFN_cuTensorMapEncodeTiled_v12000>(nullptr);
+  }();
   return fn;
 }
 
@@ -460,8 +459,16 @@ cudaError_t launch_tcs_t(const CUtensorMap& map, const TcsArgs& a, int grid, siz
 // Plan of the streaming kernel for (n, k, terms): shared memory (0 if the
 // kernel does not take the shape), warpgroups, A buffers, stages and TMEM
 // columns.  Rows of at most 32 features get four warpgroups with an A buffer
-// each, rows of at most 64 two with one each, wider rows two sharing one;
-// a configuration needs at least three stages (two for the last resort).
+// each, rows of at most 64 two with one each, wider rows two sharing one.
+//
+// Stage-ring depth.  A warpgroup converting tile li knows only that tile
+// li - NA is converted (its A buffer's previous MMA has completed); the
+// tiles in between belong to other warpgroups and may not have landed.  Its
+// parity wait on a stage is only sound if the stage's previous use has
+// completed, so that use must lie in tile li - NA or earlier, or in its own
+// tile: the ring needs at least NA * NB stages when NA > 1 (a shallower ring
+// let a wait succeed one phase early).  Every configuration also wants a few
+// stages in flight: at least three, two for the last resort.
 size_t assign_tcs_plan(int n, int k, int terms, size_t limit, TcsPlan* out) {
   if (n < 1 || n > 128 || n % 4 != 0 || k < 1 || k > 128) return 0;
   const int nb = (n + 31) / 32, N = (k + 15) / 16 * 16;
@@ -475,8 +482,10 @@ size_t assign_tcs_plan(int n, int k, int terms, size_t limit, TcsPlan* out) {
   for (int i = 0; i < nc; ++i) {
     const Cfg c = cfgs[i];
     if (c.w * N > 512) continue;   // TMEM columns
+    const int need = std::max(c.min_stages, c.na > 1 ? c.na * nb : 0);
+    if (need > kTcsMaxStages) continue;
     int stages = 0;
-    for (int s = kTcsMaxStages; s >= c.min_stages; --s)
+    for (int s = kTcsMaxStages; s >= need; --s)
       if ((size_t)tcs_layout(nb, N, k, planes, s, c.na).total + 1024 <= limit) {
         stages = s;
         break;

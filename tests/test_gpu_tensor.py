@@ -39,7 +39,8 @@ def _case(m, n, k, seed, dead=True, scale=5.0):
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("m,n,k,seed", [(10_000, 28, 25, 0), (4097, 2, 10, 1),
                                         (3000, 1, 3, 2), (5000, 16, 128, 3),
-                                        (1000, 32, 1, 4), (20_011, 8, 50, 5)])
+                                        (1000, 32, 1, 4), (20_011, 8, 50, 5),
+                                        (251_573, 8, 82, 6), (60_000, 28, 96, 7)])
 def test_bf16_rescore_equals_fp32_path_bitwise(bm, m, n, k, seed, prec):
     X, C, live = _case(m, n, k, seed)
     Xd, Cd, md = dev(X), dev(C), dev(live)
