@@ -198,10 +198,12 @@ __device__ __forceinline__ void nearest2_np(const float (&pa)[NP], const float (
 // half to `spare` ([R] distances, then [R] labels), and the halves merge in
 // index order -- the upper half's winner replaces the lower's only when
 // strictly nearer (or when the lower half found none), so the lowest index
-// still wins ties.
+// still wins ties.  With SUM, the merge also starts the fixed-order sum of
+// the rows' distances (dmin_sum's arithmetic): each warp's exact FP32 pair
+// goes to S.red[warp] as a double, for lloyd_own_rows to add up.
 static_assert(kMaxTrials >= 2, "nearest_own_rows keeps 2 x R words in S.dc");
 
-template <int NP>
+template <int NP, bool SUM>
 __device__ void nearest_own_rows(const Smem& S, float* spare, int R, int k, int nrows) {
   const int H = blockDim.x >> 1;
   const bool upper = threadIdx.x >= H;
@@ -229,12 +231,20 @@ __device__ void nearest_own_rows(const Smem& S, float* spare, int R, int k, int 
     }
   }
   __syncthreads();
+  float hi = 0.f, lo = 0.f;
   for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
     const float dh = spare[i];
-    if (S.lab[i] == INT_MAX || dh < S.dmin[i]) {
+    float d = S.dmin[i];
+    if (S.lab[i] == INT_MAX || dh < d) {
+      d = dh;
       S.dmin[i] = dh;
       S.lab[i] = spare_lab[i];
     }
+    if (SUM) two_sum_acc(hi, lo, d);
+  }
+  if (SUM) {
+    warp_two_sum(hi, lo);
+    if ((threadIdx.x & 31) == 0) S.red[threadIdx.x >> 5] = (double)hi + (double)lo;
   }
   __syncthreads();
 }
@@ -259,7 +269,7 @@ template <int NP, bool GENERIC>
 __device__ void assign_own_rows(const ChunkArgs& a, const Smem& S, int r0,
                                 int nrows) {
   if constexpr (!GENERIC) {
-    nearest_own_rows<NP>(S, S.dc, a.rows_per_cta, a.k, nrows);
+    nearest_own_rows<NP, false>(S, S.dc, a.rows_per_cta, a.k, nrows);
   } else {
     for (int t0 = 0; t0 < nrows; t0 += 64) {
       const int rows = min(64, nrows - t0);
@@ -333,21 +343,22 @@ __device__ void own_rows_to_cands(const ChunkArgs& a, const Smem& S, int r0,
 
 // One Lloyd assignment over own rows plus the partial sums of the update:
 // S.lab / S.dmin, part_sum[j][f][b] = sum over own rows labelled j of
-// (p_f - c_jf) and part_cnt[j][b].  Every sum has a fixed order.
-//   np path: per-warp slices [k][32], lane = feature, warp w takes rows
-//            w, w + wu, ...; rows and centroids read from shared memory;
+// (p_f - c_jf) and part_cnt[j][b], and (thread 0's *fp) the fixed-order sum
+// of the rows' distances, dmin_sum's value.  Every sum has a fixed order.
+//   np path: a stable counting sort of the rows by label, then thread
+//            (j, f) adds centroid j's rows in row order;
 //   generic: per row-group accumulators [k][npad], thread = (group, feature),
 //            rows of each staged tile split among the groups.
 template <int NP, bool GENERIC>
 __device__ void lloyd_own_rows(const ChunkArgs& a, const Smem& S,
-                               const ChunkSmem& L, int r0, int nrows, int G) {
+                               const ChunkSmem& L, int r0, int nrows, int G, double* fp) {
   const int k = a.k, n = a.n, npad = a.npad, b = blockIdx.x;
   if constexpr (!GENERIC) {
     uint64_t tsub = trace_now(a);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
     (void)L;
     // assignment (S.dc, the K-means++ candidate distances, is free here)
-    nearest_own_rows<NP>(S, S.dc, a.rows_per_cta, k, nrows);
+    nearest_own_rows<NP, true>(S, S.dc, a.rows_per_cta, k, nrows);
     phase_tick(a, 8, &tsub);
     // stable counting sort of own rows by label: order[start[j] ..) lists
     // centroid j's rows in ascending row order
@@ -421,6 +432,11 @@ __device__ void lloyd_own_rows(const ChunkArgs& a, const Smem& S,
     for (int j = threadIdx.x; j < k; j += blockDim.x)
       a.part_cnt[(size_t)j * G + b] = start[j + 1] - start[j];
     __syncthreads();
+    if (threadIdx.x == 0) {   // the merge left one exact pair per warp in S.red
+      double t = 0.0;
+      for (int i = 0; i < nw; ++i) t += S.red[i];
+      *fp = t;
+    }
     phase_tick(a, 10, &tsub);
   } else {
     const int ng = L.wu;
@@ -657,8 +673,9 @@ __device__ bool phase_lloyd(const ChunkArgs& a, const Smem& S,
   long long nd = 0;
   while (true) {
     const int nlive = S.lidx[k];
-    lloyd_own_rows<NP, GENERIC>(a, S, L, r0, nrows, G);
-    const double fp = own_dmin_sum(S, nrows);
+    double fp = 0.0;
+    lloyd_own_rows<NP, GENERIC>(a, S, L, r0, nrows, G, &fp);
+    if constexpr (GENERIC) fp = own_dmin_sum(S, nrows);
     if (threadIdx.x == 0) FPART[b] = fp;
     nd += (long long)a.s * nlive;
     phase_tick(a, 3, tclk);
