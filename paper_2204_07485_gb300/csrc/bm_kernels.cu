@@ -418,16 +418,30 @@ __device__ void lloyd_own_rows(const ChunkArgs& a, const Smem& S,
       __syncthreads();
     }
     phase_tick(a, 9, &tsub);
-    // partial sums of (p - c_j) over each centroid's rows, in row order
-    for (int q = threadIdx.x; q < k * NP; q += blockDim.x) {
-      const int j = q / NP, f = q - j * NP;
-      if (f >= n) continue;
-      const float c = S.cen[q];
+    // partial sums of (p - c_j) over each centroid's rows, in row order;
+    // thread (j, q) keeps the four chains of features 4q .. 4q + 3 (one
+    // float4 load per row), so k * NP / 4 threads cover the table in one
+    // round.  Padding features sum exact zeros.
+    constexpr int NQ = NP / 4;
+    for (int t = threadIdx.x; t < k * NQ; t += blockDim.x) {
+      const int j = t / NQ, qd = t - j * NQ;
+      if (4 * qd >= n) continue;
+      const float4 c = reinterpret_cast<const float4*>(S.cen + j * NP)[qd];
       const int e0 = start[j], e1 = start[j + 1];
-      float sum = 0.f;
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll 4
-      for (int e = e0; e < e1; ++e) sum += S.prow[order[e] * NP + f] - c;
-      a.part_sum[((size_t)j * npad + f) * G + b] = sum;
+      for (int e = e0; e < e1; ++e) {
+        const float4 v = reinterpret_cast<const float4*>(S.prow + order[e] * NP)[qd];
+        s0 += v.x - c.x;
+        s1 += v.y - c.y;
+        s2 += v.z - c.z;
+        s3 += v.w - c.w;
+      }
+      float* ps = a.part_sum + ((size_t)j * npad + 4 * qd) * G + b;
+      ps[0] = s0;
+      ps[(size_t)G] = s1;
+      ps[2 * (size_t)G] = s2;
+      ps[3 * (size_t)G] = s3;
     }
     for (int j = threadIdx.x; j < k; j += blockDim.x)
       a.part_cnt[(size_t)j * G + b] = start[j + 1] - start[j];
