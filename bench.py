@@ -36,6 +36,9 @@ CPU_SAMPLE_CHUNKS = 20
 # precision comparison on the m = 1e7, n = 128 mixture (generated on the device)
 C3_WORKLOAD = dict(name="gas_sensor_like_m1e7_n128_k50_s50000_T100", m=10_000_000, n=128,
                    k=50, s=50_000, chunks=100, seed=0)
+# the E4M3 variant: per-feature scales log-uniform in [0.1, 10]
+C3_FP8_WORKLOAD = dict(name="scaled_384_m2e6_n384_k100_s50000_T100", m=2_000_000, n=384,
+                       k=100, s=50_000, chunks=100, seed=0)
 
 
 def parse():
@@ -216,7 +219,8 @@ def time_jobs(bm, torch, ctx, stream, T, steps, warmup, flush, labels):
 def precision_forms(bm, torch, dev, X, m, n, k, s, T, seed, steps, warmup, flush,
                     forms=("fp32", "bf16x3")):
     """Time to SSE of the same job in the FP32 and tensor-core forms."""
-    codes = {"fp32": bm.BM_FP32, "bf16": bm.BM_BF16_RESCORE, "bf16x3": bm.BM_BF16X3_RESCORE}
+    codes = {"fp32": bm.BM_FP32, "bf16": bm.BM_BF16_RESCORE, "bf16x3": bm.BM_BF16X3_RESCORE,
+             "fp8": bm.BM_FP8_RESCORE}
     stream = torch.cuda.Stream(device=dev)
     labels = torch.empty(m, dtype=torch.int32, device=dev)
     out = {}
@@ -637,6 +641,13 @@ def run_ours(args, wl):
             bm, torch, dev, Xg, big["m"], big["n"], big["k"], big["s"], big["chunks"],
             big["seed"], pw, 1, flush)
         del Xg
+        torch.cuda.empty_cache()
+        v8 = C3_FP8_WORKLOAD
+        Xs = bminputs.mixtures.scaled_384_device(v8["seed"], m=v8["m"], device=dev)
+        out["precision_forms"][v8["name"]] = precision_forms(
+            bm, torch, dev, Xs, v8["m"], v8["n"], v8["k"], v8["s"], v8["chunks"], v8["seed"],
+            pw, 1, flush, forms=("fp32", "bf16x3", "fp8"))
+        del Xs
     if rank == 0 and not args.no_precision:
         out["launch_latency"] = launch_latency(bm, torch, dev)
     if rank == 0 and not args.no_grouped:

@@ -106,7 +106,7 @@ def scaled_384(seed=0, m=2_000_000):
 
 
 def isotropic_blobs_device(m, n, comps, seed, sigma=1.0, box=10.0, alpha=None,
-                           device="cuda"):
+                           device="cuda", feature_scale=None):
     """isotropic_blobs generated on a CUDA device (for workloads of several GB).
 
     Means and weights come from numpy PCG64(seed) as in isotropic_blobs; the
@@ -129,7 +129,17 @@ def isotropic_blobs_device(m, n, comps, seed, sigma=1.0, box=10.0, alpha=None,
         b = min(m, a + block)
         comp = torch.multinomial(probs, b - a, replacement=True, generator=g)
         X[a:b] = mu[comp] + sigma * torch.randn((b - a, n), generator=g, device=device)
+    if feature_scale is not None:
+        X *= torch.tensor(np.asarray(feature_scale), dtype=torch.float32, device=device)
     return X
+
+
+def scaled_384_device(seed=0, m=2_000_000, device="cuda"):
+    """scaled_384 generated on a CUDA device (same scales and mixture law)."""
+    rng = np.random.default_rng(seed + 7919)
+    scale = np.exp(rng.uniform(np.log(0.1), np.log(10.0), size=384))
+    return isotropic_blobs_device(m, 384, 100, seed, alpha=0.5, device=device,
+                                  feature_scale=scale)
 
 
 def gas_sensor_like_device(seed=0, m=10_000_000, n=128, device="cuda"):

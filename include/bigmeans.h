@@ -54,7 +54,8 @@ typedef enum bm_status {
 typedef enum bm_precision {
   BM_FP32 = 0,          /* FP32 distances throughout                          */
   BM_BF16_RESCORE = 1,  /* BF16 tensor-core distances, FP32 rescore of ties   */
-  BM_FP8_RESCORE = 2,   /* FP8 E4M3 tensor-core distances, FP32 rescore       */
+  BM_FP8_RESCORE = 2,   /* FP8 E4M3 tensor-core distances (rows and centroids
+                           scaled by powers of two), FP32 rescore             */
   BM_BF16X3_RESCORE = 3 /* split BF16 (hi*hi + hi*lo + lo*hi) tensor-core
                            distances, FP32 rescore of the few remaining ties  */
 } bm_precision;
@@ -140,9 +141,11 @@ bm_status bm_fit_chunk(bm_ctx* ctx, int32_t chunks, bm_fit_report* out);
 /* Final step of Alg. 1: labels_dev[i] (int32, m entries, caller-owned device
  * memory; may be NULL to skip labels) = nearest live incumbent centroid of
  * x_i (lowest index on ties); *sse_out (host, may be NULL) = f(C, X)
- * accumulated in float64.  With cfg.precision = BM_BF16_RESCORE the
- * distances run on the tensor cores with exact FP32 rescoring (see
- * bm_assign_rows_prec).  Blocks until done. */
+ * accumulated in float64.  With a tensor-core precision form (BM_BF16_RESCORE,
+ * BM_BF16X3_RESCORE, BM_FP8_RESCORE) the distances run on the tensor cores in
+ * that arithmetic with exact FP32 rescoring (see bm_assign_rows_prec); the
+ * chunks of such a context screen with split BF16 whatever the form.  Blocks
+ * until done. */
 bm_status bm_assign(bm_ctx* ctx, int32_t* labels_dev, double* sse_out);
 
 /* Streaming (stream processing of newly arriving data portions, Sec. 1 and
@@ -278,8 +281,12 @@ bm_status bm_assign_rows(const float* X_dev, int64_t m, int32_t n,
  * tensor cores in BF16 with FP32 accumulation, bounds the error of every
  * resulting distance, and rescores in exact FP32 every row for which more
  * than one centroid lies within the bounds; labels and distances equal those
- * of the FP32 arithmetic.  *rescored_out (host, may be NULL) receives the
- * number of rescored rows.  k <= 128.  Blocks until done. */
+ * of the FP32 arithmetic.  BM_BF16X3_RESCORE does the same with split BF16
+ * products (tighter bounds, fewer rescored rows); BM_FP8_RESCORE with E4M3
+ * products of rows and centroids each scaled by a power of two into
+ * [128, 256) (looser bounds, more rescored rows).  *rescored_out (host, may
+ * be NULL) receives the number of rescored rows.  k <= 128.  Blocks until
+ * done. */
 bm_status bm_assign_rows_prec(const float* X_dev, int64_t m, int32_t n,
                               const float* C_dev, const uint8_t* mask_dev,
                               int32_t k, int32_t precision, int32_t* labels_dev,

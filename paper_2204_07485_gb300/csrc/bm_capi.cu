@@ -368,14 +368,21 @@ static bm_status check_config(const bm_config* cfg) {
       !(cfg->tol >= 0.0))
     return BM_EINVAL;
   if (cfg->precision != BM_FP32 && cfg->precision != BM_BF16_RESCORE &&
-      cfg->precision != BM_BF16X3_RESCORE)
+      cfg->precision != BM_BF16X3_RESCORE && cfg->precision != BM_FP8_RESCORE)
     return BM_EUNSUPPORTED;
   if (cfg->init != BM_INIT_KMEANSPP && cfg->init != BM_INIT_FORGY) return BM_EINVAL;
   return BM_OK;
 }
 
 static bool wants_tc(const bm_config* cfg) {
-  return cfg->precision == BM_BF16_RESCORE || cfg->precision == BM_BF16X3_RESCORE;
+  return cfg->precision == BM_BF16_RESCORE || cfg->precision == BM_BF16X3_RESCORE ||
+         cfg->precision == BM_FP8_RESCORE;
+}
+
+// Screening arithmetic of the tensor-core final assignment for a precision
+// form (the chunk kernels' tensor-core path always screens with split BF16).
+static int assign_terms(int precision) {
+  return precision == BM_BF16_RESCORE ? 1 : precision == BM_FP8_RESCORE ? kTermsFp8 : 3;
 }
 
 bm_status ctx_create(const bm_config* cfg, const float* X_dev, cudaStream_t stream,
@@ -703,8 +710,8 @@ static bm_status assign_tc_impl(const float* X, long long m, int n, int k,
     TcsPlan tp{};
     const size_t ssmem = assign_tcs_plan(n, k, terms, limit, &tp);
     const long long tiles = (m + 127) / 128;
-    if (ssmem > 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 && tiles <= w.apart_cap &&
-        m < (1LL << 31)) {
+    if (terms != kTermsFp8 && ssmem > 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+        tiles <= w.apart_cap && m < (1LL << 31)) {
       int sms = 0, dev = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -743,7 +750,7 @@ static bm_status assign_tc_impl(const float* X, long long m, int n, int k,
     smem = assign_tc_smem(n, k, terms, &stages, &kb, &npad16, &ncols, &cf, bulk_ok, limit);
   }
   if (smem > limit) return BM_EUNSUPPORTED;
-  int maxg = assign_tc_max_grid(smem);
+  int maxg = assign_tc_max_grid(smem, terms);
   if (maxg <= 0) return BM_EUNSUPPORTED;
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
@@ -803,11 +810,11 @@ bm_status bm_assign(bm_ctx* c, int32_t* labels_dev, double* sse_out) {
   bm_status st;
   // FP32 results from the tensor cores too when the FP32 kernel's tables do
   // not fit (the rescoring makes the labels and distances those of FP32)
-  if (c->cfg.precision == BM_BF16_RESCORE || c->cfg.precision == BM_BF16X3_RESCORE ||
+  if (wants_tc(&c->cfg) ||
       c->plan.agrid == 0)
     st = assign_tc_impl(c->X, c->cfg.m, c->cfg.n, c->cfg.k, c->ws.Cinc, c->plan.npad,
                         c->ws.mask_inc, labels_dev, nullptr, c->ws, c->stream, sse_out,
-                        &c->rescored, c->cfg.precision == BM_BF16_RESCORE ? 1 : 3,
+                        &c->rescored, assign_terms(c->cfg.precision),
                         c->plan.cap);
   else
     st = assign_impl(c->X, c->cfg.m, c->cfg.n, c->cfg.k, c->plan, c->ws.Cinc,
@@ -1346,7 +1353,9 @@ bm_status bm_assign_rows_prec(const float* X_dev, int64_t m, int32_t n,
     return bm_assign_rows(X_dev, m, n, C_dev, mask_dev, k, labels_dev, dmin_dev, sse_out,
                           stream);
   }
-  if (precision != BM_BF16_RESCORE && precision != BM_BF16X3_RESCORE) return BM_EUNSUPPORTED;
+  if (precision != BM_BF16_RESCORE && precision != BM_BF16X3_RESCORE &&
+      precision != BM_FP8_RESCORE)
+    return BM_EUNSUPPORTED;
   if (!X_dev || !C_dev || !mask_dev || m < 1 || n < 1 || k < 1 || m > 2147483647LL)
     return BM_EINVAL;
   std::lock_guard<std::mutex> g(g_ops_mu);
@@ -1360,7 +1369,7 @@ bm_status bm_assign_rows_prec(const float* X_dev, int64_t m, int32_t n,
   if (rc != BM_OK) return rc;
   unsigned long long resc = 0;
   rc = assign_tc_impl(X_dev, m, n, k, C_dev, n, mask_dev, labels_dev, dmin_dev, w, st,
-                      sse_out, &resc, precision == BM_BF16X3_RESCORE ? 3 : 1);
+                      sse_out, &resc, assign_terms(precision));
   if (rescored_out) *rescored_out = resc;
   cudaStreamSynchronize(st);
   w.release();

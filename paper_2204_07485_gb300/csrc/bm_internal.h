@@ -11,6 +11,7 @@ namespace bm {
 
 constexpr int kMaxTrials = 4;      // K-means++ candidates per centre (paper: 3)
 constexpr int kMaxK = 128;         // centroids per job handled by the kernels
+constexpr int kTermsFp8 = 8;       // AssignTcArgs::terms of the E4M3 form
 constexpr int kRoundSlots = 64;    // per-round draw counters (== kMaxRounds)
 constexpr int kNpMax = 32;         // widest row kept in registers
 constexpr int kNumPhaseTimers = 11;  // see Stats::phase_ns
@@ -138,7 +139,8 @@ struct AssignTcArgs {
   int ncols;           // TMEM columns allocated
   int stages;          // FP32 row tiles filled ahead by bulk copies (0: thread loads)
   int use_bulk;        // X is 16-byte aligned: bulk copies for full tiles
-  int terms;           // 1: BF16 products; 3: split BF16 (hi*hi + hi*lo + lo*hi)
+  int terms;           // 1: BF16 products; 3: split BF16 (hi*hi + hi*lo + lo*hi);
+                       // kTermsFp8: E4M3 products of power-of-two scaled operands
   int cf;              // FP32 centroid copy kept in shared memory
 };
 
@@ -265,7 +267,7 @@ cudaError_t launch_assign_tcs(const float* X, long long m, int n, const float* C
                               const TcsPlan& plan, size_t smem, int grid, cudaStream_t st);
 size_t assign_tc_smem(int n, int k, int terms, int* stages, int* kb, int* npad16,
                       int* ncols, int* cf, bool bulk_ok, size_t limit);
-int assign_tc_max_grid(size_t smem);
+int assign_tc_max_grid(size_t smem, int terms);
 cudaError_t launch_assign_tc(const AssignTcArgs& a, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_chunk(const ChunkArgs& a, int grid, bool generic, int np,
                          size_t smem, cudaStream_t st);

@@ -18,6 +18,16 @@
 // rows with more than one candidate ("rescored") pay for extra exact
 // distances.
 //
+// The E4M3 form (FP8, single term) scales each row and each centroid by a
+// power of two that brings its largest magnitude into [128, 256), so no
+// operand saturates; the accumulator is scaled back exactly in the
+// epilogue.  Each operand then carries a relative rounding error of at most
+// 2^-4 plus an absolute error of 2^-10 / scale (the subnormal spacing), so
+// eps = 2^-3 + 2^-8 + 2^-16 sqrt(n) + (n + 16) 2^-22 bounds the dot
+// product's error relative to ||x|| ||c_j||; the candidate rule and the exact
+// rescoring are those below.  Rows are converted a warp per row (every lane
+// holds part of the row, so the row's maximum is a warp reduction).
+//
 // Data movement: each lane turns 8 consecutive FP32 features of a row into
 // one 16-byte chunk of the 128-byte-swizzled BF16 K-major tile the MMA
 // reads (and, in the split form, a second chunk with the low parts); row
@@ -26,6 +36,7 @@
 // memory each), so one CTA's loads overlap another's MMA and epilogue.
 #include <algorithm>
 #include <climits>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include "bm_device.cuh"
@@ -45,7 +56,7 @@ constexpr int kTcRows = 128;       // MMA M: rows per tile, one thread per row
 constexpr int kTcThreads = 128;
 
 struct TcLayout {
-  int sB, sA, stg, xF, cF, cc, xx, red, bars, holder, total;
+  int sB, sA, stg, xF, cF, cc, xx, sc, red, bars, holder, total;
 };
 
 // planes = 1 (BF16) or 2 (hi and lo BF16 parts of the split form); stages:
@@ -63,6 +74,7 @@ __host__ __device__ inline TcLayout tc_layout(int n, int kb, int npad16, int k, 
   L.cF = o;    o += cf ? align_up(k * n * 4, 16) : 0;   // FP32 centroids
   L.cc = o;    o += align_up(npad16 * 4, 16);           // ||c_j||^2, +inf if not live
   L.xx = o;    o += kTcRows * 4;                        // ||x||^2 of the tile's rows
+  L.sc = o;    o += (kTcRows + 128) * 4;                // E4M3 form: 1/scale of rows, centroids
   L.red = o;   o += 40 * 8;
   L.bars = o;  o += 8 * 3;                              // MMA completion, stage arrivals
   L.holder = o; o += 16;
@@ -104,6 +116,7 @@ __device__ __forceinline__ float dist_exact(const float* x, const float* c, int 
   return (s0 + s1) + (s2 + s3);
 }
 
+template <bool FP8>
 __global__ void __launch_bounds__(kTcThreads, 4)
 assign_tc_kernel(AssignTcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw_tc[];
@@ -111,7 +124,7 @@ assign_tc_kernel(AssignTcArgs a) {
   unsigned char* smem_tc =
       smem_raw_tc + ((1024u - (smem_u32(smem_raw_tc) & 1023u)) & 1023u);
   const int n = a.n, k = a.k, kb = a.kb, N = a.npad16;
-  const int planes = a.terms == 3 ? 2 : 1;
+  const int planes = (!FP8 && a.terms == 3) ? 2 : 1;
   const bool cf = a.cf != 0;
   const int S = a.stages;   // FP32 row tiles in flight (0: thread loads)
   const TcLayout L = tc_layout(n, kb, N, k, planes, cf, S);
@@ -126,6 +139,8 @@ assign_tc_kernel(AssignTcArgs a) {
   float* xF = reinterpret_cast<float*>(smem_tc + L.xF);
   float* cc = reinterpret_cast<float*>(smem_tc + L.cc);
   float* xx = reinterpret_cast<float*>(smem_tc + L.xx);
+  float* rsc = reinterpret_cast<float*>(smem_tc + L.sc);   // E4M3: 1 / row scale
+  float* csc = rsc + kTcRows;                               // E4M3: 1 / centroid scale
   double* red = reinterpret_cast<double*>(smem_tc + L.red);
   uint64_t* mma_bar = reinterpret_cast<uint64_t*>(smem_tc + L.bars);
   uint32_t* holder = reinterpret_cast<uint32_t*>(smem_tc + L.holder);
@@ -138,17 +153,41 @@ assign_tc_kernel(AssignTcArgs a) {
   // ---- set-up: zero A (its K padding must stay finite), build B, cF, cc
   for (int q = tid; q < planes * planeA / 16; q += kTcThreads)
     reinterpret_cast<uint4*>(sA)[q] = make_uint4(0u, 0u, 0u, 0u);
-  for (int e = tid; e < N * kb * 64; e += kTcThreads) {
-    const int j = e / (kb * 64), f = e - j * (kb * 64);
-    float v = 0.f;
-    if (j < k && f < n && a.mask[j]) v = __ldg(a.C + (size_t)j * a.cstride + f);
-    if (cf && j < k && f < n) cF[j * n + f] = v;
-    const int off = (f >> 6) * N * 128 + sw128_offset(j, f & 63);
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    *reinterpret_cast<__nv_bfloat16*>(sB + off) = h;
-    if (planes == 2)
-      *reinterpret_cast<__nv_bfloat16*>(sB + planeB + off) =
-          __float2bfloat16_rn(v - __bfloat162float(h));
+  if constexpr (FP8) {
+    // centroid j's scale 2^(7 - floor(log2 max|c_j|)) (1 for a zero or dead row)
+    for (int j = tid; j < N; j += kTcThreads) {
+      float mx = 0.f;
+      if (j < k && a.mask[j])
+        for (int f = 0; f < n; ++f) mx = fmaxf(mx, fabsf(__ldg(a.C + (size_t)j * a.cstride + f)));
+      const int e2 = (mx > 0.f && mx <= 3.0e38f) ? max(ilogbf(mx), -119) : 7;
+      csc[j] = ldexpf(1.f, e2 - 7);
+    }
+    __syncthreads();
+    // K-major rows of 128 E4M3 features: byte f & 15 of 16-byte chunk
+    // (f & 127) >> 4, 128-byte swizzled, K block f >> 7
+    for (int e = tid; e < N * kb * 128; e += kTcThreads) {
+      const int j = e / (kb * 128), f = e - j * (kb * 128);
+      float v = 0.f;
+      if (j < k && f < n && a.mask[j]) v = __ldg(a.C + (size_t)j * a.cstride + f);
+      if (cf && j < k && f < n) cF[j * n + f] = v;
+      const int w = f & 127, ch = w >> 4;
+      const int off = (f >> 7) * N * 128 + (j >> 3) * 1024 + (j & 7) * 128 +
+                      ((ch ^ (j & 7)) << 4) + (w & 15);
+      sB[off] = (unsigned char)__nv_cvt_float_to_fp8(v / csc[j], __NV_SATFINITE, __NV_E4M3);
+    }
+  } else {
+    for (int e = tid; e < N * kb * 64; e += kTcThreads) {
+      const int j = e / (kb * 64), f = e - j * (kb * 64);
+      float v = 0.f;
+      if (j < k && f < n && a.mask[j]) v = __ldg(a.C + (size_t)j * a.cstride + f);
+      if (cf && j < k && f < n) cF[j * n + f] = v;
+      const int off = (f >> 6) * N * 128 + sw128_offset(j, f & 63);
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      *reinterpret_cast<__nv_bfloat16*>(sB + off) = h;
+      if (planes == 2)
+        *reinterpret_cast<__nv_bfloat16*>(sB + planeB + off) =
+            __float2bfloat16_rn(v - __bfloat162float(h));
+    }
   }
   float cmax = 0.f;
   for (int j = tid; j < N; j += kTcThreads) {
@@ -166,8 +205,10 @@ assign_tc_kernel(AssignTcArgs a) {
   // error of the tensor-core dot product relative to ||x|| ||c_j||: one BF16
   // rounding per operand, or (split form, hi*hi + hi*lo + lo*hi) the dropped
   // lo*lo term and the second roundings; plus FP32 accumulation
-  const float eps = planes == 1 ? 1.01f * 0x1.0p-7f + (float)(n + 16) * 0x1.0p-22f
-                                : 3.1f * 0x1.0p-16f + (float)(3 * n + 16) * 0x1.0p-22f;
+  const float eps = FP8 ? 1.01f * (0x1.0p-3f + 0x1.0p-8f + 0x1.0p-16f * sqrtf((float)n)) +
+                               (float)(n + 16) * 0x1.0p-22f
+                   : planes == 1 ? 1.01f * 0x1.0p-7f + (float)(n + 16) * 0x1.0p-22f
+                                 : 3.1f * 0x1.0p-16f + (float)(3 * n + 16) * 0x1.0p-22f;
   cmax = warp_max_f32(cmax);
   if (lane == 0) red[warp] = cmax;
   for (int r = tid; r < kTcRows; r += kTcThreads) xx[r] = 0.f;
@@ -188,7 +229,7 @@ assign_tc_kernel(AssignTcArgs a) {
     s_bound[1] = (float)(n + 2) * 0x1.0p-22f * mx;
   }
   const uint32_t tmem = *holder;
-  const uint32_t idesc = idesc_bf16_f32(kTcRows, N);
+  const uint32_t idesc = FP8 ? idesc_e4m3_f32(kTcRows, N) : idesc_bf16_f32(kTcRows, N);
   const float e_d = (float)(n + 4) * 0x1.0p-22f;    // exact FP32 distance vs true
   const bool xvec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.X) & 15) == 0);
   const bool cvec = (n % 4 == 0) && (cf || ((a.cstride % 4 == 0) &&
@@ -229,6 +270,69 @@ assign_tc_kernel(AssignTcArgs a) {
         prefetch_l2(a.X + (size_t)tn * kTcRows * n, (uint32_t)(kTcRows * n * 4));
     }
 
+    if constexpr (FP8) {
+      // ---- rows -> scaled E4M3, a warp per row: lane l holds the 8-feature
+      // units l, l + 32, ... (n <= 512: at most two), so the row's maximum
+      // and norm are warp reductions
+      const int nunits = (n + 7) >> 3;
+      for (int r = warp; r < kTcRows; r += kTcThreads / 32) {
+        float v[2][8];
+        float mx = 0.f, q = 0.f;
+#pragma unroll
+        for (int uu = 0; uu < 2; ++uu) {
+          const int un = lane + 32 * uu, f0 = un * 8;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[uu][u] = 0.f;
+          if (r < rows && un < nunits) {
+            const float* p = src + (size_t)r * n + f0;
+            if (xvec && f0 + 8 <= n) {
+              const float4 x0 = __ldg(reinterpret_cast<const float4*>(p));
+              const float4 x1 = __ldg(reinterpret_cast<const float4*>(p) + 1);
+              v[uu][0] = x0.x; v[uu][1] = x0.y; v[uu][2] = x0.z; v[uu][3] = x0.w;
+              v[uu][4] = x1.x; v[uu][5] = x1.y; v[uu][6] = x1.z; v[uu][7] = x1.w;
+            } else {
+#pragma unroll
+              for (int u = 0; u < 8; ++u) if (f0 + u < n) v[uu][u] = __ldg(p + u);
+            }
+            if (xf) {   // FP32 copy for the exact distances
+              float* d = xF + r * xs + f0;
+              reinterpret_cast<float4*>(d)[0] = make_float4(v[uu][0], v[uu][1], v[uu][2], v[uu][3]);
+              if (f0 + 8 <= xs)
+                reinterpret_cast<float4*>(d)[1] = make_float4(v[uu][4], v[uu][5], v[uu][6], v[uu][7]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            mx = fmaxf(mx, fabsf(v[uu][u]));
+            q = fmaf(v[uu][u], v[uu][u], q);
+          }
+        }
+        mx = warp_max_f32(mx);
+        q = warp_sum_f32(q);
+        const int e2 = (mx > 0.f && mx <= 3.0e38f) ? max(ilogbf(mx), -119) : 7;
+        const float inv = ldexpf(1.f, e2 - 7);   // 1 / scale, a power of two
+        if (lane == 0) {
+          xx[r] = q;
+          rsc[r] = inv;
+        }
+#pragma unroll
+        for (int uu = 0; uu < 2; ++uu) {
+          const int un = lane + 32 * uu, f0 = un * 8;
+          if (f0 >= kb * 128) continue;
+          uint32_t w[2] = {0u, 0u};
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const uint32_t byte =
+                (uint32_t)__nv_cvt_float_to_fp8(v[uu][u] / inv, __NV_SATFINITE, __NV_E4M3);
+            w[u >> 2] |= byte << (8 * (u & 3));
+          }
+          const int wi = f0 & 127, ch = wi >> 4;
+          const int off = (f0 >> 7) * (kTcRows * 128) + (r >> 3) * 1024 + (r & 7) * 128 +
+                          ((ch ^ (r & 7)) << 4) + (wi & 8);
+          *reinterpret_cast<uint2*>(sA + off) = make_uint2(w[0], w[1]);
+        }
+      }
+    } else
     // ---- rows -> BF16 (hi[, lo]) 16-byte chunks; norms over the chunks of a row
     for (int c = tid; c < kTcRows * cslots; c += kTcThreads) {
       const int r = c >> cshift, ch = c & (cslots - 1);
@@ -312,11 +416,16 @@ assign_tc_kernel(AssignTcArgs a) {
           const uint64_t off = (uint64_t)((ks * 32) >> 4);
           const uint64_t ab = da + (uint64_t)((b * kTcRows * 128) >> 4) + off;
           const uint64_t bb = db + (uint64_t)((b * N * 128) >> 4) + off;
-          tc_mma_bf16(tmem, ab, bb, idesc, acc);              // hi * hi
-          acc = 1;
-          if (planes == 2) {
-            tc_mma_bf16(tmem, ab, bb + blo, idesc, 1);        // hi * lo
-            tc_mma_bf16(tmem, ab + alo, bb, idesc, 1);        // lo * hi
+          if constexpr (FP8) {
+            tc_mma_e4m3(tmem, ab, bb, idesc, acc);            // K = 32 per step
+            acc = 1;
+          } else {
+            tc_mma_bf16(tmem, ab, bb, idesc, acc);            // hi * hi
+            acc = 1;
+            if (planes == 2) {
+              tc_mma_bf16(tmem, ab, bb + blo, idesc, 1);      // hi * lo
+              tc_mma_bf16(tmem, ab + alo, bb, idesc, 1);      // lo * hi
+            }
           }
         }
       tc_commit(mma_bar);
@@ -332,13 +441,21 @@ assign_tc_kernel(AssignTcArgs a) {
     const float xq = xx[r] * 1.00002f;
     const float E1 = fmaf(sqrtf(xq), s_bound[0], s_bound[1]);
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    // approximate distance minus ||x||^2 from accumulator column j (the E4M3
+    // form scales the accumulator back by 1 / (row scale x centroid scale),
+    // exact powers of two)
+    const float s2 = FP8 ? -2.f * rsc[r] : -2.f;
+    auto dapx = [&](float v, int j) {
+      if constexpr (FP8) return fmaf(s2 * csc[j], v, cc[j]);
+      else return fmaf(-2.f, v, cc[j]);
+    };
     float m1 = INFINITY;
     for (int c0 = 0; c0 < N; c0 += 32) {
       float v[32];
       tmem_ld32(lane_base + (uint32_t)c0, v);
 #pragma unroll
       for (int u = 0; u < 32; ++u)
-        if (c0 + u < N) m1 = fminf(m1, fmaf(-2.f, v[u], cc[c0 + u]));
+        if (c0 + u < N) m1 = fminf(m1, dapx(v[u], c0 + u));
     }
     // every centroid that can hold the exact FP32 minimum lies within thr
     const float thr = m1 + 2.f * E1 + 3.f * e_d * fmaxf(0.f, xq + m1 + E1);
@@ -351,7 +468,7 @@ assign_tc_kernel(AssignTcArgs a) {
       uint32_t cand = 0u;
 #pragma unroll
       for (int u = 0; u < 32; ++u)
-        if (c0 + u < N && fmaf(-2.f, v[u], cc[c0 + u]) <= thr) cand |= 1u << u;
+        if (c0 + u < k && dapx(v[u], c0 + u) <= thr) cand |= 1u << u;
       if (!valid) cand = 0u;
       // exact distances of the candidates, ascending index
       while (cand) {
@@ -430,7 +547,8 @@ assign_tc_kernel(AssignTcArgs a) {
 size_t assign_tc_smem(int n, int k, int terms, int* stages_out, int* kb_out,
                       int* npad16_out, int* ncols_out, int* cf_out, bool bulk_ok,
                       size_t limit) {
-  const int kb = (n + 63) / 64;
+  const bool fp8 = terms == kTermsFp8;
+  const int kb = fp8 ? (n + 127) / 128 : (n + 63) / 64;   // K blocks of 128-byte rows
   const int npad16 = (k + 15) / 16 * 16;
   const int planes = terms == 3 ? 2 : 1;
   int ncols = 32;
@@ -441,9 +559,9 @@ size_t assign_tc_smem(int n, int k, int terms, int* stages_out, int* kb_out,
   // the larger footprint leaves fewer CTAs per SM to hide that latency
   // (measured slower than thread loads at n = 128)
   int stages = 0;
-  if (bulk_ok && n % 4 == 0 &&
+  if (!fp8 && bulk_ok && n % 4 == 0 &&
       (size_t)tc_layout(n, kb, npad16, k, planes, cf, 2).total + 1024 <= limit)
-    stages = 2;
+    stages = 2;   // (the E4M3 form converts from its own thread loads)
   const TcLayout L = tc_layout(n, kb, npad16, k, planes, cf, stages);
   *stages_out = stages;
   *kb_out = kb;
@@ -453,15 +571,14 @@ size_t assign_tc_smem(int n, int k, int terms, int* stages_out, int* kb_out,
   return (size_t)L.total + 1024;   // + alignment slack of the dynamic base
 }
 
-// CTAs per SM from shared memory and registers (the occupancy API reports a
-// single CTA per SM for this TMEM-allocating kernel, but more co-reside; the
-// host additionally caps the count by TMEM columns).
-int assign_tc_max_grid(size_t smem) {
-  if (allow_max_smem(assign_tc_kernel) != cudaSuccess) return 0;
-  cudaFuncSetAttribute(assign_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+template <bool FP8>
+static int assign_tc_max_grid_t(size_t smem) {
+  auto fn = assign_tc_kernel<FP8>;
+  if (allow_max_smem(fn) != cudaSuccess) return 0;
+  cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                        cudaSharedmemCarveoutMaxShared);
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, assign_tc_kernel) != cudaSuccess) return 0;
+  if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return 0;
   int dev = 0, sms = 0, smem_sm = 0, regs_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -475,10 +592,24 @@ int assign_tc_max_grid(size_t smem) {
   return per_sm * sms;
 }
 
+// CTAs per SM from shared memory and registers (the occupancy API reports a
+// single CTA per SM for this TMEM-allocating kernel, but more co-reside; the
+// host additionally caps the count by TMEM columns).
+int assign_tc_max_grid(size_t smem, int terms) {
+  return terms == kTermsFp8 ? assign_tc_max_grid_t<true>(smem)
+                            : assign_tc_max_grid_t<false>(smem);
+}
+
 cudaError_t launch_assign_tc(const AssignTcArgs& a, int grid, size_t smem, cudaStream_t st) {
-  cudaError_t e = allow_max_smem(assign_tc_kernel);
-  if (e != cudaSuccess) return e;
-  assign_tc_kernel<<<grid, kTcThreads, smem, st>>>(a);
+  if (a.terms == kTermsFp8) {
+    cudaError_t e = allow_max_smem(assign_tc_kernel<true>);
+    if (e != cudaSuccess) return e;
+    assign_tc_kernel<true><<<grid, kTcThreads, smem, st>>>(a);
+  } else {
+    cudaError_t e = allow_max_smem(assign_tc_kernel<false>);
+    if (e != cudaSuccess) return e;
+    assign_tc_kernel<false><<<grid, kTcThreads, smem, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

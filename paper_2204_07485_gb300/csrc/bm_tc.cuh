@@ -60,6 +60,21 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 }
 
 // D[tmem] (+)= A[desc] * B[desc]^T, one K=16 step, issued by one thread.
+// Instruction descriptor, kind::f8f6f4: FP32 accumulator, E4M3 A and B (type
+// code 0), both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D[tmem] (+)= A[desc] * B[desc]^T for E4M3 operands, one K=32 step (32 bytes
+// of each 128-byte K-major row), issued by one thread.
+__device__ __forceinline__ void tc_mma_e4m3(uint32_t d_tmem, uint64_t a, uint64_t b,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n"
+               :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
 __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b,
                                             uint32_t idesc, uint32_t accumulate) {
   asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"

@@ -1,6 +1,7 @@
-"""Tensor-core assignment (BF16 distances, exact FP32 rescoring) through the C ABI.
+"""Tensor-core assignment (BF16, split-BF16 or scaled E4M3 distances, exact FP32
+rescoring) through the C ABI.
 
-The BF16 path must reproduce the FP32 arithmetic: for n <= 32 its labels and
+Every form must reproduce the FP32 arithmetic: for n <= 32 its labels and
 per-row distances equal bm_assign_rows' bit for bit (both finish with the
 same exact FP32 distance), and for every n they match the FP64 oracle under
 the parity rules of gpu_helpers.
@@ -14,8 +15,9 @@ from gpu_helpers import OBJ_REL, dev, host, labels_match, rel, require_gpu, torc
 
 pytestmark = pytest.mark.gpu
 BF16 = 1
+FP8 = 2
 BF16X3 = 3
-PRECS = [BF16, BF16X3]
+PRECS = [BF16, BF16X3, FP8]
 
 
 @pytest.fixture(scope="module")
@@ -128,3 +130,43 @@ def test_results_do_not_depend_on_the_tuned_grid(bm):
     for lab, dmin, sse in outs[1:]:
         assert torch.equal(lab, outs[0][0]) and torch.equal(dmin, outs[0][1])
         assert sse == outs[0][2]
+
+
+def test_fp8_on_per_feature_scaled_rows(bm):
+    """n = 384, k = 100 with per-feature scales log-uniform in [0.1, 10] (the
+    mixture the E4M3 form is meant for): oracle labels and distances."""
+    m, n, k = 20_000, 384, 100
+    rng = np.random.default_rng(7919)
+    scale = np.exp(rng.uniform(np.log(0.1), np.log(10.0), size=n))
+    X, _ = bi.mixtures.isotropic_blobs(m, n, 100, 3, alpha=0.5, feature_scale=scale)
+    C = X[np.random.default_rng(3).choice(m, k, replace=False)].astype(np.float32)
+    live = np.ones(k, np.uint8)
+    lab = torch.empty(m, dtype=torch.int32, device="cuda:0")
+    dmin = torch.empty(m, dtype=torch.float32, device="cuda:0")
+    sse, resc = bm.bm_assign_rows_prec(dev(X), m, n, dev(C), dev(live), k, FP8, lab, dmin)
+    ref_lab, d1, d2 = o.nearest(X, C, live.astype(bool))
+    bad, _ = labels_match(host(lab), ref_lab, d1, d2)
+    assert bad == 0
+    np.testing.assert_allclose(host(dmin), d1, rtol=(n + 2) * 2.0 ** -24, atol=1e-30)
+    assert rel(sse, float(d1.sum())) <= OBJ_REL
+    assert 0 <= resc <= m
+
+
+def test_fp8_context_end_to_end(bm):
+    """A context in the E4M3 form: split-BF16 chunks, E4M3 final assignment;
+    same labels and SSE as the split-BF16 form on the same job."""
+    m, n, k, s, T = 20_000, 64, 20, 5_000, 3
+    X, _ = bi.mixtures.isotropic_blobs(m, n, 30, 4, box=8.0)
+    out = []
+    for prec in (BF16X3, FP8):
+        cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=4, precision=prec)
+        ctx = bm.bm_create(cfg, dev(X))
+        try:
+            bm.bm_fit_chunk(ctx, T)
+            lab = torch.empty(m, dtype=torch.int32, device="cuda:0")
+            out.append((bm.bm_assign(ctx, lab), host(lab)))
+        finally:
+            bm.bm_destroy(ctx)
+    (s3, l3), (s8, l8) = out
+    assert np.array_equal(l3, l8)
+    assert rel(s3, s8) <= 1e-12
