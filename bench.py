@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-grouped", action="store_true")
-    ap.add_argument("--profile", choices=["chunk_np", "chunk_tc", "assign_tc", "grouped"],
+    ap.add_argument("--profile", choices=["chunk_np", "chunk_tc", "assign_tc", "assign_fp8",
+                                          "grouped"],
                     default=None,
                     help="run one short job of a kernel family (for ncu captures) and exit")
     ap.add_argument("--chunks", type=int, default=WORKLOAD["chunks"])
@@ -76,7 +77,7 @@ def peaks():
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one chunk_kernel<28, 0>
 # launch on the default workload (a typical chunk: gather + Lloyd)
-CHUNK_NP28_DRAM_BYTES = 11_239_936
+CHUNK_NP28_DRAM_BYTES = 11_241_472
 
 # FP32 ALU peak of GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz.
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -665,7 +666,8 @@ PROFILE_CASES = {
     # kernel family: (m, n, k, s, precision, chunks); small jobs for ncu captures
     "chunk_np": (1_000_000, 28, 25, 50_000, 0, 4),     # chunk_kernel<28, 0>
     "chunk_tc": (1_000_000, 128, 50, 50_000, 3, 3),    # chunk_tc_kernel
-    "assign_tc": (2_000_000, 128, 50, 50_000, 3, 1),   # assign_tc_kernel (final assignment)
+    "assign_tc": (2_000_000, 128, 50, 50_000, 3, 1),   # assign_tcs_kernel (final assignment)
+    "assign_fp8": (2_000_000, 384, 100, 50_000, 2, 1),  # assign_tc_kernel<true> (E4M3)
 }
 
 
@@ -706,6 +708,8 @@ def profile_case(name):
     dev = torch.device("cuda", 0)
     if n == 28:
         X = torch.from_numpy(bminputs.mixtures.hepmass_like(0, m=m)).to(dev)
+    elif n == 384:
+        X = bminputs.mixtures.scaled_384_device(0, m=m, device=dev)
     else:
         X = bminputs.mixtures.isotropic_blobs_device(m, n, 100, 0, alpha=0.5, device=dev)
     stream = torch.cuda.Stream(device=dev)
