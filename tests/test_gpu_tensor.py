@@ -170,3 +170,23 @@ def test_fp8_context_end_to_end(bm):
     (s3, l3), (s8, l8) = out
     assert np.array_equal(l3, l8)
     assert rel(s3, s8) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("m,n,k", [(1, 8, 1), (127, 28, 3), (129, 64, 5), (300, 384, 2)])
+def test_small_and_ragged_inputs(bm, m, n, k, prec):
+    """One row, fewer rows than a tile, one row past a tile, and all-zero
+    rows and centroids mixed in: labels and distances of the FP32 oracle."""
+    X, C, live = _case(max(m, 2 * k), n, k, m, dead=False)
+    X = X[:m].copy()
+    X[m // 2] = 0.0          # an all-zero row
+    if k > 1:
+        C[k - 1] = 0.0       # an all-zero centroid
+    lab = torch.empty(m, dtype=torch.int32, device="cuda:0")
+    dmin = torch.empty(m, dtype=torch.float32, device="cuda:0")
+    sse, resc = bm.bm_assign_rows_prec(dev(X), m, n, dev(C), dev(live), k, prec, lab, dmin)
+    ref_lab, d1, d2 = o.nearest(X, C, live.astype(bool))
+    bad, _ = labels_match(host(lab), ref_lab, d1, d2)
+    assert bad == 0
+    np.testing.assert_allclose(host(dmin), d1, rtol=(n + 2) * 2.0 ** -24, atol=1e-30)
+    assert rel(sse, float(d1.sum())) <= OBJ_REL or float(d1.sum()) == 0.0
