@@ -91,7 +91,7 @@ __device__ __forceinline__ float dist_exact(const float* x, const float* c, int 
   if (vec) {
     const float4* x4 = reinterpret_cast<const float4*>(x);
     const float4* c4 = reinterpret_cast<const float4*>(c);
-#pragma unroll 4
+#pragma unroll 8
     for (int q = 0; q < n / 4; ++q) {
       const float4 a = x4[q], b = c4[q];
       const float e0 = a.x - b.x, e1 = a.y - b.y, e2 = a.z - b.z, e3 = a.w - b.w;
@@ -334,6 +334,9 @@ assign_tc_kernel(AssignTcArgs a) {
       }
     } else
     // ---- rows -> BF16 (hi[, lo]) 16-byte chunks; norms over the chunks of a row
+    // (every thread runs cslots iterations; unrolled so that the loads of
+    // several chunks are in flight together)
+#pragma unroll 4
     for (int c = tid; c < kTcRows * cslots; c += kTcThreads) {
       const int r = c >> cshift, ch = c & (cslots - 1);
       float v[8];
