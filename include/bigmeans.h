@@ -113,8 +113,8 @@ void bm_config_default(bm_config* cfg);
 /* Human-readable name of a status code (static string). */
 const char* bm_status_string(int32_t status);
 
-/* Creates a Big-means context for the dataset X_dev (m x n, borrowed) on the
- * current CUDA device.  Allocates all device state (sample, centroids,
+/* Creates a Big-means context for the dataset X_dev (m x n, borrowed: it
+ * must stay valid and unchanged until bm_destroy) on the current CUDA device.  Allocates all device state (sample, centroids,
  * partial sums) once.  The incumbent starts with every centroid degenerate
  * and f_opt = +inf (Alg. 1).  stream: the stream all work is queued on. */
 bm_status bm_create(const bm_config* cfg, const float* X_dev, void* stream,

@@ -9,6 +9,7 @@ shared library has not been built, importing this package raises.
 """
 import ctypes
 import os
+import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbigmeans.so")
@@ -190,15 +191,43 @@ def bm_config_default(**overrides):
     return cfg
 
 
+# The native side borrows the memory behind the pointers it is given (a
+# context's dataset, a group's problems, a queued job's buffers).  The objects
+# that own that memory are kept referenced here, by handle, until the handle
+# is destroyed or the job ends, so a temporary tensor passed in is not freed
+# (and its memory reused by the caching allocator) while kernels still read it.
+_held = {}
+_held_ended = set()   # jobs whose end came before their submit returned
+_held_lock = threading.Lock()
+
+
+def _hold(key, *objs):
+    with _held_lock:
+        if key in _held_ended:
+            _held_ended.discard(key)
+        else:
+            _held[key] = objs
+
+
+def _release(key, ended=False):
+    with _held_lock:
+        if _held.pop(key, None) is None and ended:
+            _held_ended.add(key)
+
+
 def bm_create(cfg, X_dev, stream=None):
     ctx = _vp()
     _check(_lib.bm_create(ctypes.byref(cfg), _ptr(X_dev), _stream(stream),
                           ctypes.byref(ctx)), "bm_create")
+    _hold(("ctx", ctx.value), X_dev)
     return ctx.value
 
 
 def bm_destroy(ctx):
-    _check(_lib.bm_destroy(ctx), "bm_destroy")
+    try:
+        _check(_lib.bm_destroy(ctx), "bm_destroy")
+    finally:
+        _release(("ctx", ctx))
 
 
 def bm_reset(ctx):
@@ -333,6 +362,8 @@ def bm_group_create(problems, max_iter=300, tol=1e-4, balance=True, stream=None)
     _check(_lib.bm_group_create(arr, len(problems), int(max_iter), float(tol),
                                 1 if balance else 0, _stream(stream), ctypes.byref(out)),
            "bm_group_create")
+    _hold(("group", out.value), *[(q["P"], q["C"], q["mask"], q.get("labels"))
+                                  for q in problems])
     return out.value
 
 
@@ -352,7 +383,10 @@ def bm_group_info(group):
 
 
 def bm_group_destroy(group):
-    _check(_lib.bm_group_destroy(group), "bm_group_destroy")
+    try:
+        _check(_lib.bm_group_destroy(group), "bm_group_destroy")
+    finally:
+        _release(("group", group))
 
 
 def bm_assign_rows(X_dev, m, n, C_dev, mask_dev, k, labels_dev=None, dmin_dev=None,
@@ -396,9 +430,6 @@ def bm_selftest_wait_timeout(timeout_ms=100, stream=None):
 
 
 # ------------------------------------------------------------------ serving
-_callbacks = {}   # ticket -> ctypes callback object, alive until the job ends
-
-
 def bm_server_create(workers=2, memory_budget=0, max_queue=256):
     cfg = bm_server_config(int(workers), int(memory_budget), int(max_queue))
     sv = _vp()
@@ -407,13 +438,22 @@ def bm_server_create(workers=2, memory_budget=0, max_queue=256):
 
 
 def bm_server_destroy(server):
-    _check(_lib.bm_server_destroy(server), "bm_server_destroy")
+    try:
+        _check(_lib.bm_server_destroy(server), "bm_server_destroy")
+    finally:
+        with _held_lock:
+            for key in [q for q in _held if q[0] == "job" and q[1] == server]:
+                del _held[key]
+            _held_ended.difference_update(
+                [q for q in _held_ended if q[0] == "job" and q[1] == server])
 
 
 def bm_submit(server, cfg, X_dev, chunks, labels_dev=None, C_out_host=None,
               mask_out_host=None, callback=None):
     """Admits a job; returns its ticket.  callback(ticket, result_dict) runs on
-    a worker thread when the job ends."""
+    a worker thread when the job ends.  The job's buffers (and the callback)
+    stay referenced until the job's result is taken by bm_wait or handed to
+    the callback."""
     job = bm_job()
     job.cfg = cfg
     job.X_dev = _ptr(X_dev)
@@ -427,13 +467,12 @@ def bm_submit(server, cfg, X_dev, chunks, labels_dev=None, C_out_host=None,
             try:
                 _f(int(ticket), res.contents.as_dict())
             finally:
-                _callbacks.pop(int(ticket), None)
+                _release(("job", server, int(ticket)), ended=True)
         holder = bm_job_callback(_cb)
         job.callback = holder
     ticket = ctypes.c_uint64()
     _check(_lib.bm_submit(server, ctypes.byref(job), ctypes.byref(ticket)), "bm_submit")
-    if holder is not None:
-        _callbacks.setdefault(ticket.value, holder)
+    _hold(("job", server, ticket.value), holder, X_dev, labels_dev, C_out_host, mask_out_host)
     return ticket.value
 
 
@@ -445,6 +484,7 @@ def bm_wait(server, ticket, timeout=-1.0):
     if st == BM_ETIMEOUT:
         return None
     _check(st, "bm_wait")
+    _release(("job", server, int(ticket)))
     return res.as_dict()
 
 

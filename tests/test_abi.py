@@ -113,3 +113,43 @@ def test_group_entry_points_validate_without_a_device():
     assert bm._lib.bm_group_create(None, 1, 300, 1e-4, 1, None, bm.ctypes.byref(out)) == bm.BM_EINVAL
     assert bm._lib.bm_group_run(None, None, None) == bm.BM_EINVAL
     assert bm._lib.bm_group_destroy(None) == bm.BM_OK
+
+
+def test_binding_keeps_borrowed_objects_until_the_handle_ends():
+    # the library borrows the memory behind the pointers it is given; the
+    # binding keeps the owning objects referenced until destroy / job end
+    _ensure_built()
+    import gc
+    import weakref
+    import paper_2204_07485_gb300 as bm
+
+    class Owner:
+        pass
+
+    x = Owner()
+    ref = weakref.ref(x)
+    bm._hold(("ctx", 0xABC), x)
+    del x
+    gc.collect()
+    assert ref() is not None
+    bm._release(("ctx", 0xABC))
+    gc.collect()
+    assert ref() is None
+    # a job that ends (its callback ran) before its submit registered it is
+    # not held afterwards, and leaves nothing behind
+    y = Owner()
+    ref = weakref.ref(y)
+    bm._release(("job", 7, 1), ended=True)
+    bm._hold(("job", 7, 1), y)
+    del y
+    gc.collect()
+    assert ref() is None
+    assert ("job", 7, 1) not in bm._held and ("job", 7, 1) not in bm._held_ended
+    # a job released normally after being held
+    z = Owner()
+    ref = weakref.ref(z)
+    bm._hold(("job", 7, 2), z)
+    del z
+    bm._release(("job", 7, 2), ended=True)
+    gc.collect()
+    assert ref() is None and ("job", 7, 2) not in bm._held_ended

@@ -391,3 +391,75 @@ def test_identical_points(bm):
     st, recs = o.big_means(X, k, draws)
     assert f_opt == 0.0 == st.f_opt
     assert np.array_equal(mask, st.live)
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_context_keeps_a_temporary_dataset_alive(bm, prec):
+    # the context borrows X; a temporary tensor handed to bm_create stays
+    # referenced by the binding, so later allocations of the same size (the
+    # labels, scratch filled with garbage) cannot take its memory
+    m, n, k, s, T, seed = 5432, 2 if prec == 0 else 100, 3, 2401, 2, 310199
+    X, _ = bi.mixtures.isotropic_blobs(m, n, 40, seed, box=3.0)
+    cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=seed, precision=prec)
+    ctx = bm.bm_create(cfg, dev(X))
+    try:
+        junk = [torch.full((m, n), 1e3, dtype=torch.float32, device="cuda:0") for _ in range(4)]
+        bm.bm_fit_chunk(ctx, T)
+        C = np.zeros((k, n), np.float32)
+        mask = np.zeros(k, np.uint8)
+        bm.bm_get_state(ctx, C, mask)
+        lab = torch.empty(m, dtype=torch.int32, device="cuda:0")
+        sse = bm.bm_assign(ctx, lab)
+        del junk
+    finally:
+        bm.bm_destroy(ctx)
+    A, sse_ref, d1, d2 = o.final_assignment(X, C, mask.astype(bool))
+    assert labels_match(host(lab), A, d1, d2)[0] == 0
+    assert rel(sse, sse_ref) <= OBJ_REL
+
+
+def test_random_whole_jobs_match_oracle(bm):
+    # seeded sweep of whole jobs (chunks + final assignment) over n, k, m, s,
+    # chunk count, precision form and reinitialisation; non-decisive draws are
+    # skipped, every decisive one must match the oracle on every output
+    rng = np.random.default_rng(2204)
+    ran = 0
+    while ran < 40:
+        n = int(rng.choice([1, 2, 3, 4, 7, 8, 15, 16, 27, 28, 32, 33, 40, 64, 100, 128]))
+        k = int(rng.integers(1, 40))
+        m = int(rng.integers(max(k, 10), 6000))
+        s = int(rng.integers(k, m + 1))
+        T = int(rng.integers(1, 4))
+        prec = int(rng.choice([0, 1, 2, 3]))
+        init = int(rng.choice([0, 0, 0, 1]))
+        seed = int(rng.integers(1 << 20))
+        comps = int(rng.integers(1, 50))
+        box = float(rng.choice([3.0, 8.0, 20.0]))
+        X, _ = bi.mixtures.isotropic_blobs(m, n, comps, seed, box=box)
+        draws = [bi.chunk_draws(seed, t, m, s, k) for t in range(T)]
+        st, recs = o.big_means(X, k, draws, init="forgy" if init == 1 else "kmeans++")
+        mgs = [_margins(r) for r in recs]
+        if not all(g["gap"] >= 1e-5 and g["stop"] >= 1e-6 and g["keep"] >= 1e-6
+                   and g["kpp"] >= KPP_BAND and g["pot"] >= 1e-6 for g in mgs):
+            continue
+        case = dict(m=m, n=n, k=k, s=s, T=T, prec=prec, init=init, seed=seed)
+        cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=seed, precision=prec, init=init)
+        ctx = bm.bm_create(cfg, dev(X))
+        try:
+            rep = bm.bm_fit_chunk(ctx, T)
+            C = np.zeros((k, n), np.float32)
+            mask = np.zeros(k, np.uint8)
+            f_opt, _ = bm.bm_get_state(ctx, C, mask)
+            lab = torch.empty(m, dtype=torch.int32, device="cuda:0")
+            sse = bm.bm_assign(ctx, lab)
+        finally:
+            bm.bm_destroy(ctx)
+        ran += 1
+        assert rep["accepted"] == sum(r.accepted for r in recs), case
+        assert rep["lloyd_iters"] == sum(r.iters for r in recs), case
+        assert np.array_equal(mask.astype(bool), st.live), case
+        assert rel(f_opt, st.f_opt) <= OBJ_REL, case
+        assert centroids_close(C, st.C, st.live) <= CEN_REL, case
+        A, sse_ref, d1, d2 = o.final_assignment(X, st.C.astype(np.float32), st.live)
+        assert labels_match(host(lab), A, d1, d2)[0] == 0, case
+        assert rel(sse, sse_ref) <= OBJ_REL, case
