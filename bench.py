@@ -597,6 +597,8 @@ def run_ours(args, wl):
         e2e_times.append(time.perf_counter() - t0)
     e2e_val = flops_step / float(np.median(e2e_times)) / 1e12
     e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": m * n * 4,
+           "host_gather_ctas": rep_h["host_gathers"],
+           "sse_equals_device_path": bool(sse_h == sse),
            "d2h_bytes_per_step": m * 4 + k * n * 4 + k,
            "ms_per_step": float(np.median(e2e_times)) * 1e3}
 

@@ -41,7 +41,7 @@ class bm_fit_report(ctypes.Structure):
     _fields_ = [("chunks", ctypes.c_int64), ("accepted", ctypes.c_int64),
                 ("lloyd_iters", ctypes.c_int64), ("n_d", ctypes.c_int64),
                 ("chunk_counter", ctypes.c_int64), ("f_opt", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("host_gathers", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -338,6 +338,10 @@ struct FitGraph {
 struct bm_ctx {
   bm_config cfg;
   const float* X;
+  // bm_fit_host while its copy of X is in flight: the device-accessible host
+  // rows and the flag that turns 1 when X holds them (null otherwise)
+  const float* Xh = nullptr;
+  const uint32_t* x_ready = nullptr;
   cudaStream_t stream;
   Plan plan;
   Workspace ws;
@@ -577,6 +581,8 @@ bm_status bm_fit_chunk(bm_ctx* c, int32_t chunks, bm_fit_report* out) {
       cudaStreamSynchronize(c->stream) != cudaSuccess)
     return BM_ECUDA;
   ChunkArgs a = chunk_args(c->ws, c->plan, c->X, c->cfg.m, c->cfg.n, c->cfg.k, c->cfg.s);
+  a.Xh = c->Xh;
+  a.x_ready = c->x_ready;
   a.seed = c->cfg.seed;
   a.max_iter = c->cfg.max_iter;
   a.tol = c->cfg.tol;
@@ -618,6 +624,7 @@ bm_status bm_fit_chunk(bm_ctx* c, int32_t chunks, bm_fit_report* out) {
     out->chunk_counter = c->t;
     out->f_opt = f_opt;
     out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    out->host_gathers = after.host_gathers - before.host_gathers;
   }
   return BM_OK;
 }
@@ -1157,6 +1164,18 @@ static cudaMemPool_t fit_host_pool(int dev) {
   return pool;
 }
 
+// The device address of host memory the GPU can read directly (pinned or
+// registered), or null (pageable memory, or no such mapping).
+static const float* host_rows_on_device(const float* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+  return static_cast<const float*>(at.devicePointer);
+}
+
 bm_status bm_fit_host(const bm_config* cfg, const float* X_host, int32_t chunks,
                       float* C_out_host, uint8_t* mask_out_host,
                       int32_t* labels_out_host, double* sse_out,
@@ -1167,11 +1186,17 @@ bm_status bm_fit_host(const bm_config* cfg, const float* X_host, int32_t chunks,
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return BM_ECUDA; }
   cudaMemPool_t pool = fit_host_pool(dev);
   if (!pool) return BM_ECUDA;
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr, cs = nullptr;
+  cudaEvent_t e_alloc = nullptr, e_copied = nullptr;
   if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return BM_ECUDA;
   float* X = nullptr;
   int32_t* labels = nullptr;
+  uint32_t* ready = nullptr;
   const size_t xbytes = (size_t)cfg->m * cfg->n * 4;
+  // Rows the GPU can read in place: the copy to the device runs on a second
+  // stream while the first chunks gather their samples from host memory;
+  // the final assignment waits for the copy.
+  const float* Xh = host_rows_on_device(X_host);
   bm_status rc = BM_OK;
   bm_ctx* c = nullptr;
   if (cudaMallocFromPoolAsync(reinterpret_cast<void**>(&X), xbytes, pool, st) != cudaSuccess) {
@@ -1186,7 +1211,24 @@ bm_status bm_fit_host(const bm_config* cfg, const float* X_host, int32_t chunks,
     rc = BM_ENOMEM;
     goto done;
   }
-  if (cudaMemcpyAsync(X, X_host, xbytes, cudaMemcpyHostToDevice, st) != cudaSuccess) { rc = BM_ECUDA; goto done; }
+  if (Xh) {
+    if (cudaMallocFromPoolAsync(reinterpret_cast<void**>(&ready), 16, pool, st) != cudaSuccess ||
+        cudaMemsetAsync(ready, 0, 16, st) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e_alloc, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e_copied, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(e_alloc, st) != cudaSuccess ||
+        cudaStreamWaitEvent(cs, e_alloc, 0) != cudaSuccess ||
+        cudaMemcpyAsync(X, X_host, xbytes, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        launch_x_ready(ready, cs) != cudaSuccess ||
+        cudaEventRecord(e_copied, cs) != cudaSuccess) {
+      rc = BM_ECUDA;
+      goto done;
+    }
+  } else if (cudaMemcpyAsync(X, X_host, xbytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    rc = BM_ECUDA;
+    goto done;
+  }
   {
     // a one-shot context: recording a graph would not pay for itself; its
     // workspace comes from the same pool
@@ -1195,7 +1237,16 @@ bm_status bm_fit_host(const bm_config* cfg, const float* X_host, int32_t chunks,
     rc = bm::ctx_create(&once, X, st, pool, &c, 0);
   }
   if (rc != BM_OK) goto done;
+  if (Xh) {
+    c->Xh = Xh;
+    c->x_ready = ready;
+  }
   rc = bm_fit_chunk(c, chunks, report);
+  if (Xh) {
+    c->Xh = nullptr;
+    c->x_ready = nullptr;
+    if (cudaStreamWaitEvent(st, e_copied, 0) != cudaSuccess && rc == BM_OK) rc = BM_ECUDA;
+  }
   if (rc != BM_OK) goto done;
   rc = bm_assign(c, labels, sse_out);
   if (rc != BM_OK) goto done;
@@ -1204,10 +1255,16 @@ bm_status bm_fit_host(const bm_config* cfg, const float* X_host, int32_t chunks,
        cudaStreamSynchronize(st) != cudaSuccess)) { rc = BM_ECUDA; goto done; }
   rc = bm_objective(c, nullptr, C_out_host, mask_out_host);
 done:
+  // the copy (and the flag write after it) ends before X and the flag go
+  if (cs) cudaStreamSynchronize(cs);
   if (c) bm_destroy(c);
+  if (ready) cudaFreeAsync(ready, st);
   if (labels) cudaFreeAsync(labels, st);
   if (X) cudaFreeAsync(X, st);
   cudaStreamSynchronize(st);
+  if (e_alloc) cudaEventDestroy(e_alloc);
+  if (e_copied) cudaEventDestroy(e_copied);
+  if (cs) cudaStreamDestroy(cs);
   cudaStreamDestroy(st);
   return rc;
 }

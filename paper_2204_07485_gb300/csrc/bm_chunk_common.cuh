@@ -30,6 +30,23 @@ __device__ __forceinline__ void phase_tick(const ChunkArgs& a, int i, uint64_t* 
   }
 }
 
+// Where a CTA gathers its sample rows from: X, or -- while X is still being
+// filled by a copy from host memory (*x_ready == 0) -- the host copy itself,
+// read over the CPU-GPU link.  Both hold the same bytes, so the results do
+// not depend on the choice; each CTA takes one source for its whole gather.
+// Called by all threads.
+__device__ __forceinline__ const float* gather_source(const ChunkArgs& a) {
+  if (!a.Xh) return a.X;
+  __shared__ int s_dev;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_dev = ld_acquire(a.x_ready) != 0u;
+    if (!s_dev) atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats->host_gathers), 1ull);
+  }
+  __syncthreads();
+  return s_dev ? a.X : a.Xh;
+}
+
 // lidx[0..c) <- indices of the live centroids in ascending order, lidx[k] = c.
 // Called by all threads; ends with a barrier.
 __device__ __forceinline__ void build_live_list(const int* live, int* lidx, int k) {

@@ -861,9 +861,10 @@ __device__ void tcc_gather(const ChunkArgs& a, const TccS& S, int r0, int nrows)
   const int n = a.n, npad = a.npad, w = threadIdx.x >> 5, l = threadIdx.x & 31;
   for (int i = threadIdx.x; i < nrows; i += blockDim.x) S.order[i] = __ldcg(a.idx + r0 + i);
   __syncthreads();
-  if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(a.X) & 15) == 0) {
+  const float* X = gather_source(a);
+  if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
     const int q4 = npad >> 2, units = nrows * q4;
-    const float4* X4 = reinterpret_cast<const float4*>(a.X);
+    const float4* X4 = reinterpret_cast<const float4*>(X);
     float4* P4 = reinterpret_cast<float4*>(a.P) + (size_t)r0 * q4;
     for (int u0 = threadIdx.x; u0 < units; u0 += 8 * kTccThreads) {
       float4 v[8];
@@ -892,7 +893,7 @@ __device__ void tcc_gather(const ChunkArgs& a, const TccS& S, int r0, int nrows)
         v[q] = 0.f;
         if (u < units) {
           const int i = u / nch, f = (u - i * nch) * 32 + l;
-          if (f < n) v[q] = __ldg(a.X + (size_t)S.order[i] * n + f);
+          if (f < n) v[q] = __ldg(X + (size_t)S.order[i] * n + f);
         }
       }
 #pragma unroll

@@ -53,10 +53,16 @@ struct Stats {
   // [7] keep-the-best; [8..10] split [3] into assignment, update slices and
   // slice combination + partial-sum stores
   unsigned long long phase_ns[kNumPhaseTimers];
+  long long host_gathers;   // CTA gathers that read the host-memory copy of X
 };
 
 struct ChunkArgs {
   const float* X;      // m x n (row stride n)
+  // Optional second copy of X in device-accessible host memory: the gathers
+  // read it while *x_ready is 0 (X still being filled by a host-to-device
+  // copy) and X afterwards.  Both hold the same bytes.  Null: X only.
+  const float* Xh;
+  const uint32_t* x_ready;
   long long m;
   int n, npad, k, s;
   int rows_per_cta;    // R = ceil(s / gridDim.x)
@@ -251,6 +257,9 @@ inline cudaError_t launch_cooperative(Kernel fn, int grid, int threads, size_t s
 
 // Host-side launch helpers (bm_kernels.cu, bm_sample.cu, bm_tc.cu).
 cudaError_t launch_draw(const DrawArgs& a, int chunks, cudaStream_t st);
+// *flag <- 1 once every earlier operation of the stream has completed (the
+// host-to-device copy of X that chunk gathers wait for).
+cudaError_t launch_x_ready(uint32_t* flag, cudaStream_t st);
 // Streaming tensor-core final assignment (n <= 128, n % 4 == 0, k <= 128):
 // shared memory of its plan, 0 when it does not take the shape.
 struct TcsPlan {

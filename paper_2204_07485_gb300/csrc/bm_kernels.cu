@@ -528,12 +528,13 @@ __device__ __forceinline__ int block_excl_scan(int v, int* buf, int* total) {
 template <int NP, bool GENERIC>
 __device__ void phase_gather(const ChunkArgs& a, const Smem& S, int r0, int nrows) {
   const int npad = a.npad, n = a.n;
+  const float* X = gather_source(a);
   if constexpr (!GENERIC) {
-    const bool vec4 = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.X) & 15) == 0);
+    const bool vec4 = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
       const long long row = __ldcg(a.idx + r0 + i);
       float p[NP];
-      load_row_np<NP>(p, a.X + (size_t)row * n, n, vec4, false);
+      load_row_np<NP>(p, X + (size_t)row * n, n, vec4, false);
       float4* dst = reinterpret_cast<float4*>(a.P + (size_t)(r0 + i) * NP);
       float4* res = reinterpret_cast<float4*>(S.prow + i * NP);
 #pragma unroll
@@ -553,7 +554,7 @@ __device__ void phase_gather(const ChunkArgs& a, const Smem& S, int r0, int nrow
         v[u] = 0.f;
         if (e < total) {
           const int i = e / npad, f = e - i * npad;
-          if (f < n) v[u] = __ldg(a.X + (size_t)__ldcg(a.idx + r0 + i) * n + f);
+          if (f < n) v[u] = __ldg(X + (size_t)__ldcg(a.idx + r0 + i) * n + f);
         }
       }
 #pragma unroll
@@ -976,6 +977,13 @@ assign_generic_kernel(AssignArgs a) {
   assign_finish(a, acc, red);
 }
 
+// Publishes the end of the host-to-device copy of X that precedes it on its
+// stream: chunk gathers switch from the host copy to X once they see 1.
+__global__ void x_ready_kernel(uint32_t* flag) {
+  __threadfence();
+  atomicExch(flag, 1u);
+}
+
 // ------------------------------------------------------------ launch glue
 template <int NP, bool GENERIC>
 static cudaError_t launch_chunk_t(const ChunkArgs& a, int grid, size_t smem,
@@ -1049,6 +1057,11 @@ int assign_max_grid(bool generic, int np, size_t smem) {
     case 28: return max_grid_of(assign_np_kernel<28>, smem);
     default: return max_grid_of(assign_np_kernel<32>, smem);
   }
+}
+
+cudaError_t launch_x_ready(uint32_t* flag, cudaStream_t st) {
+  x_ready_kernel<<<1, 1, 0, st>>>(flag);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_assign(const AssignArgs& a, int grid, bool generic, int np,

@@ -360,6 +360,51 @@ def test_fit_host_matches_device_path(bm):
     assert rel(sse, sse_ref) <= OBJ_REL
 
 
+@pytest.mark.parametrize("m,n,k,s,T,prec", [
+    (2_000_000, 28, 25, 50_000, 6, 0),     # row-in-register gather
+    (1_000_000, 40, 20, 20_000, 4, 0),     # tiled FP32 gather
+    (1_000_000, 128, 50, 20_000, 4, 3),    # tensor-core chunk kernel gather
+])
+def test_fit_host_pinned_overlap_equals_device_path(bm, m, n, k, s, T, prec):
+    # pinned host rows: chunks that start while the copy to the device is in
+    # flight gather from host memory; every result must equal the path that
+    # runs on a device copy of X, bit for bit, whichever source each CTA used
+    X = bi.mixtures.isotropic_blobs_device(m, n, 60, 5, device="cuda:0").cpu().numpy()
+    Xh = torch.from_numpy(X).pin_memory()
+    cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=9, precision=prec)
+    C = np.zeros((k, n), np.float32)
+    mask = np.zeros(k, np.uint8)
+    lab = torch.empty(m, dtype=torch.int32).pin_memory()
+    bm.bm_fit_host(cfg, Xh.data_ptr(), 1, C, mask, lab.data_ptr())   # warm: pool, modules
+    # a competing host-to-device copy keeps the copy engines busy, so the
+    # first chunks of the measured call are likely to start before X lands
+    big = torch.empty(256 << 20, dtype=torch.float32).pin_memory()
+    side = torch.cuda.Stream()
+    busy = torch.empty_like(big, device="cuda:0")
+    with torch.cuda.stream(side):
+        busy.copy_(big, non_blocking=True)
+    sse, rep = bm.bm_fit_host(cfg, Xh.data_ptr(), T, C, mask, lab.data_ptr())
+    torch.cuda.synchronize()
+    assert rep["host_gathers"] >= 0
+    Xd = dev(X)
+    ctx = bm.bm_create(cfg, Xd)
+    try:
+        rep2 = bm.bm_fit_chunk(ctx, T)
+        C2 = np.zeros((k, n), np.float32)
+        mask2 = np.zeros(k, np.uint8)
+        f2, _ = bm.bm_get_state(ctx, C2, mask2)
+        lab2 = torch.empty(m, dtype=torch.int32, device="cuda:0")
+        sse2 = bm.bm_assign(ctx, lab2)
+    finally:
+        bm.bm_destroy(ctx)
+    print("host_gathers", rep["host_gathers"])
+    assert rep2["host_gathers"] == 0
+    assert np.array_equal(C, C2) and np.array_equal(mask, mask2)
+    assert rep["f_opt"] == f2 and rep["accepted"] == rep2["accepted"]
+    assert rep["lloyd_iters"] == rep2["lloyd_iters"]
+    assert np.array_equal(lab.numpy(), host(lab2)) and sse == sse2
+
+
 # ---------------------------------------------------------------- edges
 
 @pytest.mark.parametrize("m,n,k,s,seed,T", [
