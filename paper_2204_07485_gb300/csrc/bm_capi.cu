@@ -637,28 +637,14 @@ static bm_status assign_impl(const float* X, long long m, int n, int k,
   a.X = X; a.m = m; a.n = n; a.npad = p.npad; a.k = k; a.kpad = p.kpad;
   a.C = C; a.cstride = cstride; a.mask = mask; a.labels = labels; a.dmin = dmin;
   a.part = w.apart; a.sse = w.asse; a.ticket = &w.ctl->assign_ticket;
-  a.status = &w.ctl->status;
-  // rows up to 32 features, X 16-byte aligned, at least one 512-row tile:
-  // tiles staged in shared memory by bulk copies
-  const size_t ssmem = p.generic ? 0 : assign_staged_smem(n, k, p.np);
-  const int sgrid = (!p.generic && m >= kAsgRows && ssmem + 2048 <= kSmemLimit &&
-                     (reinterpret_cast<uintptr_t>(X) & 15) == 0)
-                        ? assign_staged_max_grid(p.np, ssmem) : 0;
-  if (sgrid > 0) {
-    int grid = (int)std::min<long long>(sgrid, m / kAsgRows);
-    if (p.cap > 0) grid = std::min(grid, p.cap * std::max(1, sgrid / std::max(1, sm_count())));
-    if (launch_assign_staged(a, grid, p.np, ssmem, st) != cudaSuccess) return BM_ECUDA;
-  } else {
-    const long long rows_per = p.generic ? 64 : 256;  // rows per CTA pass
-    int grid = (int)std::max<long long>(1, std::min<long long>(p.agrid, (m + rows_per - 1) / rows_per));
-    if (p.cap > 0) grid = std::min(grid, p.cap * std::max(1, p.agrid / std::max(1, sm_count())));
-    if (launch_assign(a, grid, p.generic, p.np, p.asmem, st) != cudaSuccess) return BM_ECUDA;
-  }
+  const long long rows_per = p.generic ? 64 : 256;  // rows per CTA pass
+  int grid = (int)std::max<long long>(1, std::min<long long>(p.agrid, (m + rows_per - 1) / rows_per));
+  if (p.cap > 0) grid = std::min(grid, p.cap * std::max(1, p.agrid / std::max(1, sm_count())));
+  if (launch_assign(a, grid, p.generic, p.np, p.asmem, st) != cudaSuccess) return BM_ECUDA;
   double sse = 0.0;
   if (cudaMemcpyAsync(&sse, w.asse, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return BM_ECUDA;
-  const bm_status rc = check_status(w, st, 0);
-  if (rc != BM_OK) return rc;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return BM_ECUDA;
   if (sse_out) *sse_out = sse;
   return BM_OK;
 }

@@ -113,7 +113,6 @@ struct AssignArgs {
   double* part;        // [G]
   double* sse;         // device scalar
   uint32_t* ticket;    // zero between launches
-  int* status;         // sticky error word (a staged copy that never landed)
 };
 
 struct DrawArgs {
@@ -294,13 +293,6 @@ cudaError_t launch_assign(const AssignArgs& a, int grid, bool generic, int np,
                           size_t smem, cudaStream_t st);
 int assign_max_grid(bool generic, int np, size_t smem);
 size_t assign_smem(int npad, int k, int kpad, bool generic);
-// Final assignment of rows up to 32 features from 512-row tiles staged in
-// shared memory by bulk copies (X 16-byte aligned, at least one full tile).
-constexpr int kAsgRows = 512;
-size_t assign_staged_smem(int n, int k, int np);
-int assign_staged_max_grid(int np, size_t smem);
-cudaError_t launch_assign_staged(const AssignArgs& a, int grid, int np, size_t smem,
-                                 cudaStream_t st);
 
 }  // namespace bm
 

@@ -28,7 +28,6 @@
 #include "bm_internal.h"
 #include "bm_chunk_common.cuh"
 #include "bm_kpp.cuh"
-#include "bm_tc.cuh"
 #include "bm_tile.cuh"
 
 namespace bm {
@@ -946,129 +945,6 @@ assign_np_kernel(AssignArgs a) {
   assign_finish(a, acc, red);
 }
 
-// Rows of at most 32 features, X 16-byte aligned: the CTA's 512-row tiles
-// of X move into shared memory as single bulk copies, two stages deep (the
-// next tile lands while this one is scanned), and each thread takes rows
-// tid and tid + 256 of the tile with the same arithmetic as
-// assign_np_kernel, so labels and distances are the same bits.  The rows
-// after the last full tile go to one CTA through plain loads.
-constexpr int kAsgStages = 2;
-
-template <int NP>
-__device__ __forceinline__ void load_row_stage(float (&p)[NP], const float* row, int n,
-                                               bool vec4) {
-  if (vec4) {
-#pragma unroll
-    for (int q = 0; q < NP / 4; ++q) {
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (4 * q < n) v = reinterpret_cast<const float4*>(row)[q];
-      p[4 * q] = v.x; p[4 * q + 1] = v.y; p[4 * q + 2] = v.z; p[4 * q + 3] = v.w;
-    }
-  } else {
-#pragma unroll
-    for (int f = 0; f < NP; ++f) p[f] = f < n ? row[f] : 0.f;
-  }
-}
-
-template <int NP>
-__global__ void __launch_bounds__(kThreads)
-assign_np_staged_kernel(AssignArgs a, long long ntiles) {
-  extern __shared__ __align__(16) char smem_raw[];
-  const int n = a.n, k = a.k, tid = threadIdx.x;
-  const size_t tf = (size_t)kAsgRows * n;   // floats per tile
-  float* stg = reinterpret_cast<float*>(smem_raw);
-  int o = align_up(kAsgStages * kAsgRows * n * 4, 16);
-  float* cen = reinterpret_cast<float*>(smem_raw + o);
-  o += align_up(k * NP * 4, 16);
-  int* live = reinterpret_cast<int*>(smem_raw + o);
-  o += align_up(k * 4, 16);
-  int* lidx = reinterpret_cast<int*>(smem_raw + o);
-  o += align_up((k + 1) * 4, 16);
-  double* red = reinterpret_cast<double*>(smem_raw + o);
-  o += 64 * 8;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + o);
-  if (tid == 0) {
-    for (int s = 0; s < kAsgStages; ++s) mbar_init(bar + s, 1);
-    mbar_init_fence();
-  }
-  load_centroids<false>(cen, nullptr, live, a.C, a.cstride, a.mask, k, n, NP, 0, false);
-  build_live_list(live, lidx, k);   // block barriers: the mbarriers are ready
-  const uint32_t bytes = (uint32_t)(tf * 4);
-  // the CTA's i-th tile into stage i % kAsgStages (thread 0)
-  auto issue = [&](long long i) {
-    const long long tt = (long long)blockIdx.x + i * gridDim.x;
-    if (tt >= ntiles) return;
-    const int s = (int)(i % kAsgStages);
-    mbar_expect_tx(bar + s, bytes);
-    bulk_g2s(stg + (size_t)s * tf, a.X + (size_t)tt * tf, bytes, bar + s);
-  };
-  if (tid == 0)
-    for (int i = 0; i < kAsgStages; ++i) issue(i);
-  const bool vec4 = (n & 3) == 0;
-  double acc = 0.0;
-  bool ok = true;
-  long long it = 0;
-  for (;; ++it) {
-    const long long t = (long long)blockIdx.x + it * gridDim.x;
-    if (t >= ntiles) break;
-    const int s = (int)(it % kAsgStages);
-    const bool landed = mbar_wait(bar + s, (uint32_t)((it / kAsgStages) & 1));
-    if (!__syncthreads_and(landed)) {   // a copy that never landed: stop here
-      ok = false;
-      break;
-    }
-    const float* tile = stg + (size_t)s * tf;
-    float pa[NP], pb[NP];
-    load_row_stage<NP>(pa, tile + (size_t)tid * n, n, vec4);
-    load_row_stage<NP>(pb, tile + (size_t)(tid + kThreads) * n, n, vec4);
-    int ja, jb;
-    float da, db;
-    nearest2_np<NP>(pa, pb, cen, lidx, 0, lidx[k], ja, da, jb, db);
-    const long long i0 = t * kAsgRows + tid, i1 = i0 + kThreads;
-    if (a.labels) { a.labels[i0] = ja; a.labels[i1] = jb; }
-    if (a.dmin) { a.dmin[i0] = da; a.dmin[i1] = db; }
-    acc += (double)da;
-    acc += (double)db;
-    __syncthreads();   // stage s has been read for the last time
-    if (tid == 0) {
-      fence_proxy_async_smem();
-      issue(it + kAsgStages);
-    }
-  }
-  if (!ok) {
-    // no copy may still be landing when the CTA exits: wait (bounded) for
-    // the stages issued after the one that failed
-    if (tid == 0) {
-      for (long long i = it + 1; i < it + kAsgStages; ++i)
-        if ((long long)blockIdx.x + i * gridDim.x < ntiles)
-          mbar_wait(bar + (int)(i % kAsgStages), (uint32_t)((i / kAsgStages) & 1));
-      atomicCAS(a.status, kStatusOk, kStatusTimeout);
-    }
-  } else if (blockIdx.x == (int)(ntiles % gridDim.x)) {
-    // rows after the last full tile
-    const bool xvec = vec4 && ((reinterpret_cast<uintptr_t>(a.X) & 15) == 0);
-    for (long long i = ntiles * kAsgRows + tid; i < a.m; i += 2 * kThreads) {
-      const long long i2 = i + kThreads;
-      const bool two = i2 < a.m;
-      float pa[NP], pb[NP];
-      load_row_np<NP>(pa, a.X + (size_t)i * n, n, xvec, false);
-      load_row_np<NP>(pb, a.X + (size_t)(two ? i2 : i) * n, n, xvec, false);
-      int ja, jb;
-      float da, db;
-      nearest2_np<NP>(pa, pb, cen, lidx, 0, lidx[k], ja, da, jb, db);
-      if (a.labels) a.labels[i] = ja;
-      if (a.dmin) a.dmin[i] = da;
-      acc += (double)da;
-      if (two) {
-        if (a.labels) a.labels[i2] = jb;
-        if (a.dmin) a.dmin[i2] = db;
-        acc += (double)db;
-      }
-    }
-  }
-  assign_finish(a, acc, red);
-}
-
 __global__ void __launch_bounds__(kThreads)
 assign_generic_kernel(AssignArgs a) {
   extern __shared__ __align__(16) char smem_raw[];
@@ -1180,40 +1056,6 @@ int assign_max_grid(bool generic, int np, size_t smem) {
     case 16: return max_grid_of(assign_np_kernel<16>, smem);
     case 28: return max_grid_of(assign_np_kernel<28>, smem);
     default: return max_grid_of(assign_np_kernel<32>, smem);
-  }
-}
-
-size_t assign_staged_smem(int n, int k, int np) {
-  return (size_t)align_up(kAsgStages * kAsgRows * n * 4, 16) + align_up(k * np * 4, 16) +
-         align_up(k * 4, 16) + align_up((k + 1) * 4, 16) + 64 * 8 + 8 * kAsgStages;
-}
-
-int assign_staged_max_grid(int np, size_t smem) {
-  switch (np) {
-    case 4: return max_grid_of(assign_np_staged_kernel<4>, smem);
-    case 8: return max_grid_of(assign_np_staged_kernel<8>, smem);
-    case 16: return max_grid_of(assign_np_staged_kernel<16>, smem);
-    case 28: return max_grid_of(assign_np_staged_kernel<28>, smem);
-    default: return max_grid_of(assign_np_staged_kernel<32>, smem);
-  }
-}
-
-template <int NP>
-static cudaError_t launch_staged_t(const AssignArgs& a, int grid, size_t smem, cudaStream_t st) {
-  const cudaError_t e = allow_max_smem(assign_np_staged_kernel<NP>);
-  if (e != cudaSuccess) return e;
-  assign_np_staged_kernel<NP><<<grid, kThreads, smem, st>>>(a, a.m / kAsgRows);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_assign_staged(const AssignArgs& a, int grid, int np, size_t smem,
-                                 cudaStream_t st) {
-  switch (np) {
-    case 4: return launch_staged_t<4>(a, grid, smem, st);
-    case 8: return launch_staged_t<8>(a, grid, smem, st);
-    case 16: return launch_staged_t<16>(a, grid, smem, st);
-    case 28: return launch_staged_t<28>(a, grid, smem, st);
-    default: return launch_staged_t<32>(a, grid, smem, st);
   }
 }
 
