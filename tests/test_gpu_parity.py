@@ -91,7 +91,9 @@ def test_gather_bit_exact(bm, m, n, s):
 
 ASSIGN_CASES = [(5000, 2, 10, 0), (4097, 28, 25, 1), (3001, 128, 50, 2),
                 (2000, 1, 3, 3), (1000, 33, 100, 4), (777, 127, 7, 5),
-                (64, 5, 1, 6), (10_000, 16, 128, 7), (513, 384, 20, 8)]
+                (64, 5, 1, 6), (10_000, 16, 128, 7), (513, 384, 20, 8),
+                (512, 12, 6, 9), (204_800, 7, 9, 10), (300_001, 28, 25, 11),
+                (100_003, 32, 40, 12)]
 
 
 @pytest.mark.parametrize("m,n,k,seed", ASSIGN_CASES)
