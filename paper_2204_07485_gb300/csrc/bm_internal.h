@@ -168,7 +168,7 @@ struct PolishArgs {
 
 // Shared-memory layout of the chunk kernel (bytes), identical on host/device.
 struct ChunkSmem {
-  int cen, crow, live, lidx, sw, cw, lab, dmin, dc, cand, stage, prow, cn, red, total;
+  int cen, crow, live, lidx, sw, cw, lab, dmin, dc, cand, stage, prow, red, total;
   int wu;              // tiled path: row groups that own a private update accumulator
 };
 
@@ -215,7 +215,6 @@ __host__ __device__ inline ChunkSmem chunk_smem(int npad, int k, int kpad, int R
   L.stage = o; o += generic ? align_up(64 * npad * 4, 16) : 0;
   // row-in-register path: the CTA's R sample rows stay resident for the chunk
   L.prow = o;  o += generic ? 0 : align_up(R * npad * 4, 16);
-  L.cn = o;    o += generic ? 0 : align_up(k * 4, 16);   // row-in-register path: ||c_j||^2
   L.red = o;   o += 80 * 8;
   L.total = o;
   return L;

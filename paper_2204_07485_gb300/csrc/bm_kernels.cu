@@ -46,7 +46,6 @@ struct Smem {
   float* cand;  // [kMaxTrials][npad] candidate rows
   float* stage; // generic: swizzled transposed 64-row tile
   float* prow;  // np: [R][npad] own sample rows, resident for the chunk
-  float* cn;    // np: [k] squared norms of the centroid rows (set by each scan)
   double* red;  // scratch for block reductions (64 doubles)
 };
 
@@ -64,7 +63,6 @@ __device__ __forceinline__ Smem carve(char* base, const ChunkSmem& L) {
   S.cand = reinterpret_cast<float*>(base + L.cand);
   S.stage = reinterpret_cast<float*>(base + L.stage);
   S.prow = reinterpret_cast<float*>(base + L.prow);
-  S.cn = reinterpret_cast<float*>(base + L.cn);
   S.red = reinterpret_cast<double*>(base + L.red);
   return S;
 }
@@ -192,121 +190,6 @@ __device__ __forceinline__ void nearest2_np(const float (&pa)[NP], const float (
   }
 }
 
-// Squared norm of a centroid row of NP floats (16-byte aligned), four chains.
-template <int NP>
-__device__ __forceinline__ float row_norm2(const float* c) {
-  const float4* c4 = reinterpret_cast<const float4*>(c);
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll
-  for (int u = 0; u < NP / 4; ++u) {
-    const float4 v = c4[u];
-    s0 = fmaf(v.x, v.x, s0);
-    s1 = fmaf(v.y, v.y, s1);
-    s2 = fmaf(v.z, v.z, s2);
-    s3 = fmaf(v.w, v.w, s3);
-  }
-  return (s0 + s1) + (s2 + s3);
-}
-
-// dist2_np's arithmetic for one row and one centroid row: the same bits.
-template <int NP>
-__device__ __forceinline__ float dist1_np(const float (&p)[NP], const float* c) {
-  const float4* c4 = reinterpret_cast<const float4*>(c);
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll
-  for (int u = 0; u < NP / 4; ++u) {
-    const float4 v = c4[u];
-    a0 = sq(p[4 * u] - v.x, a0);
-    a1 = sq(p[4 * u + 1] - v.y, a1);
-    a2 = sq(p[4 * u + 2] - v.z, a2);
-    a3 = sq(p[4 * u + 3] - v.w, a3);
-  }
-  return (a0 + a1) + (a2 + a3);
-}
-
-// nearest2_np's result with about half the arithmetic.  One pass scores
-// every centroid j of [q0, q1) by the expanded form s_j = ||c_j||^2 - 2 x.c_j
-// (one FMA per feature; cn[j] = ||c_j||^2) and keeps each row's two smallest
-// scores m1 (first index on equal scores) and m2.  In FP32, s_j differs from
-// ||x - c_j||^2 - ||x||^2 by at most
-//   E = (NP + 2) 2^-24 1.01 (||c||^2_max + 2 ||x|| ||c||_max),
-// and the direct form dist2_np computes differs from ||x - c_j||^2 by at most
-// e_d = (NP + 4) 2^-22 of it.  So when m2 > m1 + 2E + 3 e_d max(0, ||x||^2 +
-// m1 + E), the best-scoring centroid has the strictly smallest direct-form
-// distance, and only that distance is computed (dist1_np: the same bits).
-// A row whose runner-up is closer -- ties, near-ties, non-finite values --
-// takes nearest2_np's full direct scan.
-template <int NP>
-__device__ __forceinline__ void nearest2_np_screened(const float (&pa)[NP], const float (&pb)[NP],
-                                                     const float* cen, const float* cn,
-                                                     const int* lidx, int q0, int q1, int& ja,
-                                                     float& da, int& jb, float& db) {
-  if (q0 >= q1) {
-    da = db = INFINITY;
-    ja = jb = INT_MAX;
-    return;
-  }
-  float a1 = INFINITY, a2 = INFINITY, b1 = INFINITY, b2 = INFINITY, cm = 0.f;
-  int ia = 0, ib = 0;
-  float4 cv[NP / 4];
-  int j = lidx[q0];
-#pragma unroll
-  for (int u = 0; u < NP / 4; ++u) cv[u] = reinterpret_cast<const float4*>(cen + j * NP)[u];
-#pragma unroll 1
-  for (int q = q0; q < q1; ++q) {
-    const int jn = lidx[min(q + 1, q1 - 1)];   // the last step reloads its own row
-    float4 nv[NP / 4];
-#pragma unroll
-    for (int u = 0; u < NP / 4; ++u) nv[u] = reinterpret_cast<const float4*>(cen + jn * NP)[u];
-    float x0 = 0.f, x1 = 0.f, x2 = 0.f, x3 = 0.f, y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
-#pragma unroll
-    for (int u = 0; u < NP / 4; ++u) {
-      const float4 v = cv[u];
-      x0 = fmaf(pa[4 * u], v.x, x0);
-      x1 = fmaf(pa[4 * u + 1], v.y, x1);
-      x2 = fmaf(pa[4 * u + 2], v.z, x2);
-      x3 = fmaf(pa[4 * u + 3], v.w, x3);
-      y0 = fmaf(pb[4 * u], v.x, y0);
-      y1 = fmaf(pb[4 * u + 1], v.y, y1);
-      y2 = fmaf(pb[4 * u + 2], v.z, y2);
-      y3 = fmaf(pb[4 * u + 3], v.w, y3);
-    }
-    const float c2 = cn[j];
-    cm = fmaxf(cm, c2);
-    const float sa = fmaf(-2.f, (x0 + x1) + (x2 + x3), c2);
-    const float sb = fmaf(-2.f, (y0 + y1) + (y2 + y3), c2);
-    if (sa < a1) { a2 = a1; a1 = sa; ia = j; } else if (sa < a2) { a2 = sa; }
-    if (sb < b1) { b2 = b1; b1 = sb; ib = j; } else if (sb < b2) { b2 = sb; }
-#pragma unroll
-    for (int u = 0; u < NP / 4; ++u) cv[u] = nv[u];
-    j = jn;
-  }
-  float xa0 = 0.f, xa1 = 0.f, xb0 = 0.f, xb1 = 0.f;
-#pragma unroll
-  for (int f = 0; f < NP; f += 2) {
-    xa0 = fmaf(pa[f], pa[f], xa0);
-    xa1 = fmaf(pa[f + 1], pa[f + 1], xa1);
-    xb0 = fmaf(pb[f], pb[f], xb0);
-    xb1 = fmaf(pb[f + 1], pb[f + 1], xb1);
-  }
-  constexpr float e = (float)(NP + 2) * 0x1.0p-24f * 1.01f;
-  constexpr float ed = (float)(NP + 4) * 0x1.0p-22f;
-  const float cmx = cm * 1.0001f, scm = sqrtf(cmx);
-  const float xqa = (xa0 + xa1) * 1.00002f, xqb = (xb0 + xb1) * 1.00002f;
-  const float Ea = e * fmaf(2.f * sqrtf(xqa), scm, cmx);
-  const float Eb = e * fmaf(2.f * sqrtf(xqb), scm, cmx);
-  const float ta = a1 + 2.f * Ea + 3.f * ed * fmaxf(0.f, xqa + a1 + Ea);
-  const float tb = b1 + 2.f * Eb + 3.f * ed * fmaxf(0.f, xqb + b1 + Eb);
-  if (a2 > ta && b2 > tb) {
-    ja = ia;
-    jb = ib;
-    da = dist1_np<NP>(pa, cen + ia * NP);
-    db = dist1_np<NP>(pb, cen + ib * NP);
-  } else {
-    nearest2_np<NP>(pa, pb, cen, lidx, q0, q1, ja, da, jb, db);
-  }
-}
-
 // Nearest live centroid of every own row (resident in S.prow) -> S.lab /
 // S.dmin.  The shared-memory reads of the
 // centroid table, not the arithmetic, limit a one-row-per-thread scan, so
@@ -328,9 +211,6 @@ __device__ void nearest_own_rows(const Smem& S, float* spare, int R, int k, int 
   const int nl = S.lidx[k], h = (nl + 1) >> 1;
   const int q0 = upper ? h : 0, q1 = upper ? nl : h;
   int* spare_lab = reinterpret_cast<int*>(spare + R);
-  // squared norms of the centroid rows for the screened scan
-  for (int j = threadIdx.x; j < k; j += blockDim.x) S.cn[j] = row_norm2<NP>(S.cen + j * NP);
-  __syncthreads();
   for (int base = 0; base < nrows; base += 2 * H) {
     const int ia = base + u, ib = base + H + u;
     if (ia >= nrows) break;
@@ -339,7 +219,7 @@ __device__ void nearest_own_rows(const Smem& S, float* spare, int R, int k, int 
     load_row_smem<NP>(pb, S.prow + (ib < nrows ? ib : ia) * NP);
     int ja, jb;
     float da, db;
-    nearest2_np_screened<NP>(pa, pb, S.cen, S.cn, S.lidx, q0, q1, ja, da, jb, db);
+    nearest2_np<NP>(pa, pb, S.cen, S.lidx, q0, q1, ja, da, jb, db);
     if (upper) {
       spare[ia] = da;
       spare_lab[ia] = ja;
@@ -1035,13 +915,9 @@ assign_np_kernel(AssignArgs a) {
   o += align_up(a.k * 4, 16);
   int* lidx = reinterpret_cast<int*>(smem_raw + o);
   o += align_up((a.k + 1) * 4, 16);
-  float* cn = reinterpret_cast<float*>(smem_raw + o);
-  o += align_up(a.k * 4, 16);
   double* red = reinterpret_cast<double*>(smem_raw + o);
   load_centroids<false>(cen, nullptr, live, a.C, a.cstride, a.mask, a.k, a.n, NP, 0, false);
   build_live_list(live, lidx, a.k);
-  for (int j = threadIdx.x; j < a.k; j += blockDim.x) cn[j] = row_norm2<NP>(cen + j * NP);
-  __syncthreads();
   const bool vec4 = (a.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.X) & 15) == 0);
   // two rows per thread, a grid stride apart: each centroid load from
   // shared memory serves both
@@ -1056,7 +932,7 @@ assign_np_kernel(AssignArgs a) {
     load_row_np<NP>(pb, a.X + (size_t)(two ? i2 : i) * a.n, a.n, vec4, false);
     int ja, jb;
     float da, db;
-    nearest2_np_screened<NP>(pa, pb, cen, cn, lidx, 0, lidx[a.k], ja, da, jb, db);
+    nearest2_np<NP>(pa, pb, cen, lidx, 0, lidx[a.k], ja, da, jb, db);
     if (a.labels) a.labels[i] = ja;
     if (a.dmin) a.dmin[i] = da;
     acc += (double)da;
@@ -1156,8 +1032,7 @@ int chunk_max_grid(bool generic, int np, size_t smem) {
 
 size_t assign_smem(int npad, int k, int kpad, bool generic) {
   if (!generic)
-    return align_up(k * npad * 4, 16) + align_up(k * 4, 16) + align_up((k + 1) * 4, 16) +
-           align_up(k * 4, 16) + 64 * 8;
+    return align_up(k * npad * 4, 16) + align_up(k * 4, 16) + align_up((k + 1) * 4, 16) + 64 * 8;
   return align_up(npad * kpad * 4, 16) + align_up(k * 4, 16) +
          align_up(64 * npad * 4, 16) + 64 * 8;
 }
