@@ -659,7 +659,7 @@ static bm_status assign_impl(const float* X, long long m, int n, int k,
 }  // extern "C"
 
 template <typename Launch>
-static int tc_tuned_grid(int n, int k, int terms, int stages, size_t smem, int maxg, long long tiles,
+static int tc_tuned_grid(int n, int k, int terms, int stages, int maxg, long long tiles,
                          Launch launch, cudaStream_t st) {
   static std::mutex mu;
   // (dev, n, MMA width, terms): k enters the kernel's cost through the MMA
@@ -765,7 +765,7 @@ static bm_status assign_tc_impl(const float* X, long long m, int n, int k,
   maxg = std::min(maxg, sms * std::max(1, 512 / ncols));   // TMEM columns per SM
   const long long tiles = (m + 127) / 128;
   if (tiles > w.apart_cap) return BM_EUNSUPPORTED;
-  const int grid = tc_tuned_grid(n, k, terms, stages, smem, maxg, tiles, [&](int g) {
+  const int grid = tc_tuned_grid(n, k, terms, stages, maxg, tiles, [&](int g) {
     AssignTcArgs t{};
     t.X = X; t.m = m; t.n = n; t.C = C; t.cstride = cstride; t.mask = mask; t.k = k;
     t.labels = labels; t.dmin = dmin; t.part = reinterpret_cast<float2*>(w.apart);
