@@ -69,6 +69,15 @@ typedef enum bm_init {
                            no distance evaluations                           */
 } bm_init;
 
+/* What Lloyd does with a live centroid that loses all its members (the paper
+ * leaves the empty-cluster rule open as an interchangeable ingredient). */
+typedef enum bm_empty {
+  BM_EMPTY_DEGENERATE = 0, /* it becomes degenerate: out of the rest of the
+                              chunk, reseeded at the next chunk (Sec. 3.3)    */
+  BM_EMPTY_KEEP = 1        /* it keeps its position and stays live, so it can
+                              win rows again at a later step                 */
+} bm_empty;
+
 /* Parameters of one Big-means job (Alg. 1 inputs X, k, s and the stop rule). */
 typedef struct bm_config {
   int64_t m;            /* number of points                                    */
@@ -90,6 +99,8 @@ typedef struct bm_config {
                            SMs' worth of final-assignment CTAs), leaving the
                            other SMs to concurrent jobs; 0: no cap             */
   int32_t init;         /* bm_init: how degenerate centroids are reinitialised */
+  int32_t empty;        /* bm_empty: Lloyd's rule for a centroid without members
+                           (grouped problems and bm_lloyd use the default)     */
 } bm_config;
 
 /* What one bm_fit_chunk call did. */

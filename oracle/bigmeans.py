@@ -37,6 +37,11 @@ design notes):
       sum_i min(D^2_i, ||p_i - cand||^2) (lowest trial index on ties).
   R8  The sample is drawn without replacement (indices are an input here).
   R9  Argmin ties go to the lowest centroid index.
+  R16 The alternative empty-cluster rule ("keep"; the paper names the
+      handling of empty clusters as an interchangeable ingredient without
+      fixing one): a centroid that loses all members keeps its position and
+      stays live, so it can regain members at a later step; R5 is the
+      default ("degenerate").
   R13 Forgy (Sec. 2: a uniform sample of the data as initial centres) as the
       alternative reinitialisation: each degenerate slot independently takes
       the sample row floor(u * s), u the slot's first K-means++ uniform.
@@ -184,8 +189,12 @@ class LloydResult:
         self.stop_margin = stop_margin  # min relative distance to the stop threshold
 
 
-def lloyd(P, C, live, tol=1e-4, max_iter=300):
-    """K-means local search on sample P from centroids C (Sec. 2; R3, R4, R5)."""
+def lloyd(P, C, live, tol=1e-4, max_iter=300, empty="degenerate"):
+    """K-means local search on sample P from centroids C (Sec. 2; R3, R4, R5).
+    ``empty`` is what happens to a live centroid without members: it becomes
+    degenerate (R5) or, with "keep", stays where it is and live (R16)."""
+    if empty not in ("degenerate", "keep"):
+        raise ValueError("empty must be 'degenerate' or 'keep'")
     P = np.asarray(P, dtype=np.float64)
     C = np.array(C, dtype=np.float64, copy=True)
     live = np.array(live, dtype=bool, copy=True)
@@ -215,13 +224,15 @@ def lloyd(P, C, live, tol=1e-4, max_iter=300):
                 continue
             members = P[labels == j]
             if members.shape[0] == 0:
-                live[j] = False
+                if empty == "degenerate":
+                    live[j] = False
             else:
                 C[j] = members.mean(axis=0)
         f_prev = f
         it += 1
-    counts = np.bincount(labels, minlength=k)
-    live &= counts > 0
+    if empty == "degenerate":
+        counts = np.bincount(labels, minlength=k)
+        live &= counts > 0
     return LloydResult(C, live, f, it, f_trace, min_gap, stop_margin, n_d)
 
 
@@ -257,10 +268,11 @@ class BigMeansState:
 
 
 def big_means_chunk(X, state, idx, u_first, u, tol=1e-4, max_iter=300,
-                    trials=3, t=0, init="kmeans++"):
+                    trials=3, t=0, init="kmeans++", empty="degenerate"):
     """One pass of Alg. 1's loop body on the sample X[idx]; updates ``state``.
     ``init`` chooses the reinitialisation of degenerate centroids: K-means++
-    (the paper's choice, R7) or Forgy (R13)."""
+    (the paper's choice, R7) or Forgy (R13); ``empty`` the empty-cluster rule
+    of Lloyd (R5 or R16)."""
     P = np.asarray(X, dtype=np.float32)[np.asarray(idx)].astype(np.float64)
     picks = []
     s = P.shape[0]
@@ -278,7 +290,7 @@ def big_means_chunk(X, state, idx, u_first, u, tol=1e-4, max_iter=300,
         C1, live1 = forgy_reseed(P, state.C, state.live, u)
     else:
         C1, live1 = kmeanspp_reseed(P, state.C, state.live, u_first, u, trials, picks)
-    res = lloyd(P, C1, live1, tol, max_iter)
+    res = lloyd(P, C1, live1, tol, max_iter, empty)
     accepted = res.f < state.f_opt
     keep_margin = (abs(res.f - state.f_opt) / state.f_opt
                    if math.isfinite(state.f_opt) and state.f_opt > 0 else math.inf)
@@ -291,7 +303,7 @@ def big_means_chunk(X, state, idx, u_first, u, tol=1e-4, max_iter=300,
 
 
 def big_means(X, k, draws, tol=1e-4, max_iter=300, trials=3, state=None,
-              t0=0, init="kmeans++"):
+              t0=0, init="kmeans++", empty="degenerate"):
     """Alg. 1 over the given chunk draws [(idx, u_first, u), ...].
 
     Returns (state, records).  The final assignment is ``final_assignment``.
@@ -302,7 +314,8 @@ def big_means(X, k, draws, tol=1e-4, max_iter=300, trials=3, state=None,
     records = []
     for q, (idx, u_first, u) in enumerate(draws):
         records.append(big_means_chunk(X, state, idx, u_first, u, tol,
-                                       max_iter, trials, t=t0 + q, init=init))
+                                       max_iter, trials, t=t0 + q, init=init,
+                                       empty=empty))
     return state, records
 
 

@@ -25,6 +25,7 @@ BM_OK, BM_EINVAL, BM_ENOMEM, BM_ECUDA, BM_ETIMEOUT, BM_EBUSY, BM_ECANCELLED, \
     BM_EUNSUPPORTED = range(8)
 BM_FP32, BM_BF16_RESCORE, BM_FP8_RESCORE, BM_BF16X3_RESCORE = range(4)
 BM_INIT_KMEANSPP, BM_INIT_FORGY = 0, 1
+BM_EMPTY_DEGENERATE, BM_EMPTY_KEEP = 0, 1
 
 
 class bm_config(ctypes.Structure):
@@ -34,7 +35,7 @@ class bm_config(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
                 ("time_budget_s", ctypes.c_double), ("graphs", ctypes.c_int32),
                 ("trace", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
-                ("init", ctypes.c_int32)]
+                ("init", ctypes.c_int32), ("empty", ctypes.c_int32)]
 
 
 class bm_fit_report(ctypes.Structure):

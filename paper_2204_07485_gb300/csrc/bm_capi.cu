@@ -375,6 +375,7 @@ static bm_status check_config(const bm_config* cfg) {
       cfg->precision != BM_BF16X3_RESCORE && cfg->precision != BM_FP8_RESCORE)
     return BM_EUNSUPPORTED;
   if (cfg->init != BM_INIT_KMEANSPP && cfg->init != BM_INIT_FORGY) return BM_EINVAL;
+  if (cfg->empty != BM_EMPTY_DEGENERATE && cfg->empty != BM_EMPTY_KEEP) return BM_EINVAL;
   return BM_OK;
 }
 
@@ -444,6 +445,7 @@ void bm_config_default(bm_config* cfg) {
   cfg->trace = 0;
   cfg->max_ctas = 0;
   cfg->init = BM_INIT_KMEANSPP;
+  cfg->empty = BM_EMPTY_DEGENERATE;
 }
 
 const char* bm_status_string(int32_t s) {
@@ -590,6 +592,7 @@ bm_status bm_fit_chunk(bm_ctx* c, int32_t chunks, bm_fit_report* out) {
   a.phases = kPhaseGather | kPhaseKpp | kPhaseLloyd | kPhaseKeep;
   a.trace = c->cfg.trace != 0;
   a.init = c->cfg.init;
+  a.empty_keep = c->cfg.empty == BM_EMPTY_KEEP;
   bm_status st = BM_OK;
   if (chunks > 0) {
     // graph replay needs a capturable stream (not the legacy default stream)
@@ -884,6 +887,7 @@ bm_status bm_fit_workers(bm_ctx* c, int32_t workers, int32_t rounds, int32_t mod
       a.seed = x->cfg.seed; a.max_iter = x->cfg.max_iter; a.tol = x->cfg.tol;
       a.trials = x->cfg.kpp_trials;
       a.init = x->cfg.init;
+      a.empty_keep = x->cfg.empty == BM_EMPTY_KEEP;
       a.phases = kPhaseGather | kPhaseKpp | kPhaseLloyd | kPhaseKeep;
       x->t = t0 + (long long)r * workers + i;
       if (rc == BM_OK) rc = queue_chunks(x, a, 1, 1);
@@ -982,6 +986,7 @@ bm_status bm_stream_push(bm_ctx* c, const float* P_dev, int64_t rows, bm_fit_rep
   a.rows_per_cta = c->plan.R;   // the plan's shape, fewer rows
   a.seed = c->cfg.seed; a.max_iter = c->cfg.max_iter; a.tol = c->cfg.tol;
   a.trials = c->cfg.kpp_trials; a.init = c->cfg.init; a.trace = c->cfg.trace != 0;
+  a.empty_keep = c->cfg.empty == BM_EMPTY_KEEP;
   a.phases = kPhaseKpp | kPhaseLloyd | kPhaseKeep;
   a.t = c->t;
   a.bar_sel = (int)(c->launches & 1);
@@ -1053,6 +1058,7 @@ bm_status bm_polish(bm_ctx* c, int32_t max_iter, double tol, double* f_out,
   pa.rows_per_cta = (m + c->pol_grid - 1) / c->pol_grid;
   pa.wu = wu;
   pa.fw = fw;
+  pa.empty_keep = c->cfg.empty == BM_EMPTY_KEEP;
   double f = 0.0, f_prev = 0.0;
   int it = 0;
   while (true) {

@@ -655,7 +655,8 @@ __device__ bool tcc_assign(const ChunkArgs& a, const TccS& S, int r0, int nrows,
 // the member count over CTAs and the slice's sums over CTAs (lane l sums the
 // CTAs u = l, l + 32, ... -- all loads in flight at once -- then a fixed
 // xor butterfly), c <- c + sum / count, the slice's planes and squared norm.
-// Centroids without members become degenerate (Sec. 3.3).
+// Centroids without members become degenerate (Sec. 3.3) unless the launch
+// keeps them in place.
 __device__ void tcc_reduce(const ChunkArgs& a, const TccS& S, bool stop) {
   const int k = a.k, npad = a.npad, n = a.n, G = gridDim.x;
   const int nsl = (npad + 7) >> 3;
@@ -680,8 +681,8 @@ __device__ void tcc_reduce(const ChunkArgs& a, const TccS& S, bool stop) {
       v[4] += x1.x; v[5] += x1.y; v[6] += x1.z; v[7] += x1.w;
     }
     cnt = warp_sum_i32(cnt);
-    if (cnt == 0) {
-      if (sl == 0 && l == 0) a.mask[j] = 0;
+    if (cnt == 0) {   // degenerate, or kept in place (planes and norm unchanged)
+      if (!a.empty_keep && sl == 0 && l == 0) a.mask[j] = 0;
       continue;
     }
     if (stop) continue;

@@ -75,6 +75,7 @@ struct ChunkArgs {
   int bar_sel;         // which Ctl::bar counter this launch uses
   int trace;           // 1: CTA 0 times its phases into Stats::phase_ns
   int init;            // reinitialisation of degenerate centroids: kInitKmeanspp / kInitForgy
+  int empty_keep;      // 1: a centroid without members keeps its position, live
   int kpad;            // k rounded up to 32 (generic path)
   int32_t* idx;        // s
   float* P;            // s x npad
@@ -157,7 +158,9 @@ struct PolishArgs {
   int n, npad, k;
   float* C;                // k x cstride working centroids (updated in place)
   int cstride;
-  uint8_t* mask;           // k live flags (cleared for centroids without members)
+  uint8_t* mask;           // k live flags (cleared for centroids without members,
+                           // unless empty_keep)
+  int empty_keep;          // 1: a centroid without members keeps its position, live
   const int32_t* labels;   // m labels of the last assignment
   float* part_sum;         // [G][k][npad]
   int32_t* part_cnt;       // [G][k]

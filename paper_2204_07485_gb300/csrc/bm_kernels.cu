@@ -762,8 +762,8 @@ __device__ bool phase_lloyd(const ChunkArgs& a, const Smem& S,
         cnt = warp_sum_i32(lane_sum_ldcg(a.part_cnt + (size_t)j * G, G));
         sum = warp_sum_f32(lane_sum_ldcg(a.part_sum + ((size_t)j * npad + ff) * G, G));
       }
-      if (cnt == 0) {
-        if (ff == 0 && l == 0) a.mask[j] = 0;
+      if (cnt == 0) {   // degenerate (Sec. 3.3), or kept in place and live
+        if (!a.empty_keep && ff == 0 && l == 0) a.mask[j] = 0;
         continue;
       }
       if (stop) continue;

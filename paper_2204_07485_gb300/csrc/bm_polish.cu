@@ -91,8 +91,8 @@ __global__ void __launch_bounds__(kPolishThreads) polish_accum_kernel(PolishArgs
 
 // New centroids: thread per (j, f); CTA partials added in CTA order, sixteen
 // loads in flight.  A live centroid without members becomes degenerate
-// (Sec. 3.3) whether or not the iteration stops; the others move to
-// c + sum / count unless it stops.
+// (Sec. 3.3) whether or not the iteration stops, or with empty_keep stays
+// where it is; the others move to c + sum / count unless it stops.
 __global__ void __launch_bounds__(kPolishThreads) polish_reduce_kernel(PolishArgs a, int G,
                                                                       int stop) {
   const int k = a.k, npad = a.npad, n = a.n;
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kPolishThreads) polish_reduce_kernel(PolishArg
     }
   }
   if (cnt == 0) {   // every thread of centroid j sees the same count
-    if (f == 0) a.mask[j] = 0;
+    if (!a.empty_keep && f == 0) a.mask[j] = 0;
     return;
   }
   if (!stop && f < n) {

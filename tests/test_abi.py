@@ -46,7 +46,7 @@ def test_invalid_shapes_rejected_before_any_device_work():
     bad = [dict(m=10, n=2, k=3, s=20), dict(m=10, n=2, k=11, s=10),
            dict(m=10, n=0, k=1, s=5), dict(m=10, n=2, k=0, s=5),
            dict(m=2**31, n=2, k=2, s=5), dict(m=10, n=2, k=2, s=5, kpp_trials=0),
-           dict(m=10, n=2, k=2, s=5, init=7)]
+           dict(m=10, n=2, k=2, s=5, init=7), dict(m=10, n=2, k=2, s=5, empty=5)]
     for kw in bad:
         cfg = bm.bm_config_default(**kw)
         with pytest.raises(bm.BigMeansError) as e:
@@ -71,6 +71,7 @@ def test_config_defaults_follow_the_paper():
     cfg = bm.bm_config_default()
     assert cfg.max_iter == 300 and cfg.tol == 1e-4 and cfg.kpp_trials == 3
     assert cfg.graphs == 1
+    assert cfg.init == bm.BM_INIT_KMEANSPP and cfg.empty == bm.BM_EMPTY_DEGENERATE
 
 
 def test_server_entry_points_validate_without_a_device():

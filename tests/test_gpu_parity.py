@@ -407,6 +407,47 @@ def test_fit_host_pinned_overlap_equals_device_path(bm, m, n, k, s, T, prec):
     assert np.array_equal(lab.numpy(), host(lab2)) and sse == sse2
 
 
+@pytest.mark.parametrize("m,n,k,s,prec,seed", [
+    (20_000, 6, 5, 3000, 0, 40),    # row-in-register kernel
+    (8000, 40, 6, 2500, 0, 41),     # tiled FP32 kernel
+    (6000, 64, 7, 3000, 3, 42),     # tensor-core chunk kernel
+])
+def test_keep_rule_leaves_an_empty_centroid_live_in_place(bm, m, n, k, s, prec, seed):
+    # an incumbent with one centroid far from every row: under BM_EMPTY_KEEP it
+    # loses all members, stays live and does not move (R16); every chunk must
+    # match the oracle run with the same rule
+    X, _ = bi.mixtures.isotropic_blobs(m, n, k + 2, seed, box=8.0)
+    rng = np.random.default_rng(seed)
+    C = X[rng.choice(m, k, replace=False)].astype(np.float32)
+    C[k // 2] = 1e3
+    T = 2
+    draws = [bi.chunk_draws(seed, t, m, s, k) for t in range(T)]
+    st = o.BigMeansState(k, n)
+    st.C = C.astype(np.float64)
+    st.live = np.ones(k, bool)
+    st.f_opt = 1e30
+    st, recs = o.big_means(X, k, draws, state=st, empty="keep")
+    _assert_decisive(recs)
+    assert st.live.all() and np.array_equal(st.C[k // 2], C[k // 2].astype(np.float64))
+    cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=seed, precision=prec,
+                               empty=bm.BM_EMPTY_KEEP)
+    ctx = bm.bm_create(cfg, dev(X))
+    try:
+        bm.bm_set_state(ctx, C, np.ones(k, np.uint8), 1e30, 0)
+        rep = bm.bm_fit_chunk(ctx, T)
+        C2 = np.zeros((k, n), np.float32)
+        mask2 = np.zeros(k, np.uint8)
+        f2, _ = bm.bm_get_state(ctx, C2, mask2)
+    finally:
+        bm.bm_destroy(ctx)
+    assert rep["accepted"] == sum(r.accepted for r in recs)
+    assert rep["lloyd_iters"] == sum(r.iters for r in recs)
+    assert np.array_equal(mask2.astype(bool), st.live)
+    assert np.array_equal(C2[k // 2], C[k // 2])
+    assert rel(f2, st.f_opt) <= OBJ_REL
+    assert centroids_close(C2, st.C, st.live) <= CEN_REL
+
+
 # ---------------------------------------------------------------- edges
 
 @pytest.mark.parametrize("m,n,k,s,seed,T", [

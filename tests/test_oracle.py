@@ -192,6 +192,37 @@ def test_lloyd_empty_cluster_becomes_degenerate():
     assert res.f == pytest.approx(0.01, rel=1e-12)
 
 
+def test_lloyd_keep_rule_leaves_an_empty_centroid_in_place():
+    # R16: a centroid too far to win any row keeps its position and stays
+    # live; the others follow exactly the Lloyd run without it
+    X = _mixture(m=600, n=3, comps=4, seed=21)
+    C0 = X[np.random.default_rng(21).choice(len(X), 4, replace=False)].copy()
+    far = np.full((1, 3), 1e3)
+    res = o.lloyd(X, np.vstack([C0[:2], far, C0[2:]]), np.ones(5, bool), empty="keep")
+    ref = o.lloyd(X, C0, np.ones(4, bool))
+    assert res.live.all()
+    assert np.array_equal(res.C[2], far[0])
+    assert np.allclose(np.delete(res.C, 2, axis=0), ref.C, rtol=0, atol=0)
+    assert res.f == ref.f and res.iters == ref.iters
+    # the default rule drops it instead
+    deg = o.lloyd(X, np.vstack([C0[:2], far, C0[2:]]), np.ones(5, bool))
+    assert list(deg.live) == [True, True, False, True, True]
+
+
+def test_lloyd_keep_rule_never_creates_degenerate_slots():
+    emptied = 0
+    for seed in range(5):
+        X = _mixture(m=400, n=2, comps=3, seed=30 + seed)
+        # more centroids than clusters, some started on duplicated rows, so
+        # that some of them lose every member along the way
+        C0 = np.vstack([X[:6], X[:6]])
+        res = o.lloyd(X, C0, np.ones(12, bool), empty="keep")
+        assert res.live.all()
+        deg = o.lloyd(X, C0, np.ones(12, bool))
+        emptied += int(not deg.live.all())
+    assert emptied > 0   # the cases do exercise empty clusters
+
+
 def test_lloyd_matches_textbook_lloyd_at_fixed_point():
     sk = pytest.importorskip("sklearn.cluster")
     X = _mixture(m=800, n=4, comps=5, seed=7)
