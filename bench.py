@@ -77,7 +77,7 @@ def peaks():
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one chunk_kernel<28, 0>
 # launch on the default workload (a typical chunk: gather + Lloyd)
-CHUNK_NP28_DRAM_BYTES = 11_244_032
+CHUNK_NP28_DRAM_BYTES = 11_244_288
 
 # FP32 ALU peak of GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz.
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
