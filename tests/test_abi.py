@@ -154,3 +154,22 @@ def test_binding_keeps_borrowed_objects_until_the_handle_ends():
     bm._release(("job", 7, 2), ended=True)
     gc.collect()
     assert ref() is None and ("job", 7, 2) not in bm._held_ended
+
+
+def test_fit_host_validates_without_a_device():
+    _ensure_built()
+    import numpy as np
+    import paper_2204_07485_gb300 as bm
+    X = np.zeros((10, 2), np.float32)
+    cfg = bm.bm_config_default(m=10, n=2, k=2, s=5)
+    with pytest.raises(bm.BigMeansError) as e:
+        bm.bm_fit_host(cfg, None, 1)
+    assert e.value.status == bm.BM_EINVAL
+    with pytest.raises(bm.BigMeansError) as e:
+        bm.bm_fit_host(cfg, X, -1)
+    assert e.value.status == bm.BM_EINVAL
+    for kw in (dict(k=6), dict(s=11), dict(n=0)):
+        bad = bm.bm_config_default(**dict(dict(m=10, n=2, k=2, s=5), **kw))
+        with pytest.raises(bm.BigMeansError) as e:
+            bm.bm_fit_host(bad, X, 1)
+        assert e.value.status == bm.BM_EINVAL
