@@ -37,11 +37,6 @@ design notes):
       sum_i min(D^2_i, ||p_i - cand||^2) (lowest trial index on ties).
   R8  The sample is drawn without replacement (indices are an input here).
   R9  Argmin ties go to the lowest centroid index.
-  R16 The alternative empty-cluster rule ("keep"; the paper names the
-      handling of empty clusters as an interchangeable ingredient without
-      fixing one): a centroid that loses all members keeps its position and
-      stays live, so it can regain members at a later step; R5 is the
-      default ("degenerate").
   R13 Forgy (Sec. 2: a uniform sample of the data as initial centres) as the
       alternative reinitialisation: each degenerate slot independently takes
       the sample row floor(u * s), u the slot's first K-means++ uniform.
@@ -50,6 +45,11 @@ design notes):
       ties, and a shared incumbent changes only when strictly improved (as
       R2).  The paper gives no round structure for mode 3; rounds are
       synchronous here.
+  R16 The alternative empty-cluster rule ("keep"; the paper names the
+      handling of empty clusters as an interchangeable ingredient without
+      fixing one): a centroid that loses all members keeps its position and
+      stays live, so it can regain members at a later step; R5 is the
+      default ("degenerate").
 """
 import math
 
