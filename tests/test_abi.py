@@ -173,3 +173,63 @@ def test_fit_host_validates_without_a_device():
         with pytest.raises(bm.BigMeansError) as e:
             bm.bm_fit_host(bad, X, 1)
         assert e.value.status == bm.BM_EINVAL
+
+
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    # every ctypes structure of the binding has the size and field offsets of
+    # the C struct it mirrors, as a C compiler lays the header out
+    import shutil
+    import subprocess
+    _ensure_built()
+    import paper_2204_07485_gb300 as bm
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = [(bm.bm_config, "bm_config"), (bm.bm_fit_report, "bm_fit_report"),
+             (bm.bm_server_config, "bm_server_config"), (bm.bm_job_result, "bm_job_result"),
+             (bm.bm_job, "bm_job"), (bm.bm_server_stats_t, "bm_server_stats"),
+             (bm.bm_group_problem, "bm_group_problem"), (bm.bm_group_result, "bm_group_result")]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bigmeans.h"',
+             'int main(void) {']
+    expect = []
+    for cls, cname in pairs:
+        lines.append('  printf("%%zu\\n", sizeof(%s));' % cname)
+        expect.append(ctypes.sizeof(cls))
+        for fname, _ in cls._fields_:
+            lines.append('  printf("%%zu\\n", offsetof(%s, %s));' % (cname, fname))
+            expect.append(getattr(cls, fname).offset)
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    exe = tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                           text=True).stdout.split()]
+    assert got == expect
+
+
+def test_binding_constants_match_the_header(tmp_path):
+    # every BM_* integer the binding defines has the header's value
+    import shutil
+    import subprocess
+    _ensure_built()
+    import paper_2204_07485_gb300 as bm
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    header = open(os.path.join(ROOT, "include", "bigmeans.h")).read()
+    names = sorted(n for n in dir(bm) if n.startswith("BM_") and isinstance(getattr(bm, n), int)
+                   and re.search(r"\b%s\b" % n, header))
+    assert len(names) >= 10
+    lines = ['#include <stdio.h>', '#include "bigmeans.h"', 'int main(void) {']
+    lines += ['  printf("%%lld\\n", (long long)(%s));' % n for n in names]
+    lines += ['  return 0;', '}']
+    src = tmp_path / "consts.c"
+    exe = tmp_path / "consts"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                           text=True).stdout.split()]
+    assert dict(zip(names, got)) == {n: getattr(bm, n) for n in names}
