@@ -233,3 +233,18 @@ def test_binding_constants_match_the_header(tmp_path):
     got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
                                            text=True).stdout.split()]
     assert dict(zip(names, got)) == {n: getattr(bm, n) for n in names}
+
+
+def test_binding_argument_counts_match_the_header():
+    _ensure_built()
+    import paper_2204_07485_gb300 as bm
+    src = open(os.path.join(ROOT, "include", "bigmeans.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    decls = re.findall(r"\b(?:bm_status|void|const char\s*\*|int32_t|int64_t|size_t)\s+"
+                       r"(bm_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S)
+    assert sorted(d[0] for d in decls) == _declared()
+    for name, params in decls:
+        p = params.strip()
+        n = 0 if p in ("", "void") else p.count(",") + 1
+        argtypes = getattr(bm._lib, name).argtypes
+        assert argtypes is not None and len(argtypes) == n, name
