@@ -6,6 +6,7 @@ example, or an independent textbook implementation.  CPU only.
 """
 import itertools
 import math
+import os
 
 import numpy as np
 import pytest
@@ -236,21 +237,32 @@ def test_lloyd_matches_textbook_lloyd_at_fixed_point():
 
 # ------------------------------------------------------------- K-means++
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _fixture(name):
+    out = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.split("#", 1)[0].split()
+        if line:
+            out[line[0]] = [float(v) for v in line[1:]]
+    return out
+
+
 def test_kpp_hand_worked_example():
-    # 1-D points 0, 1, 3, 6 with the live centroid at 0:
-    # D^2 = 0, 1, 9, 36; prefix 0, 1, 10, 46.
-    P = np.array([[0.0], [1.0], [3.0], [6.0]])
-    C = np.array([[0.0], [0.0]])
-    live = np.array([True, False])
-    u = np.array([[0.0, 0.0, 0.0], [0.01, 0.5, 10.0 / 46.0]])
+    # tests/golden/kpp_hand_example.txt: one slot reseeded, worked by hand
+    g = _fixture("kpp_hand_example.txt")
+    P = np.array(g["rows"]).reshape(-1, 1)
+    live = np.array(g["live"], bool)
+    C = np.zeros((len(live), 1))
+    C[0, 0] = g["centroid0"][0]
+    u = np.array([[0.0, 0.0, 0.0], g["uniforms"]])
     picks = []
     C2, live2 = o.kmeanspp_reseed(P, C, live, 0.0, u, 3, picks)
-    # targets 0.46 -> i=1 ; 23 -> i=3 ; 10 (== prefix[2], not >) -> i=3
-    assert picks[0].cands == [1, 3, 3]
-    # potentials: cand 1 -> 0+0+4+25 = 29 ; cand 3 -> 0+1+9+0 = 10
-    assert picks[0].potentials == [29.0, 10.0, 10.0]
-    assert picks[0].chosen == 1                    # lowest trial among ties
-    assert C2[1, 0] == 6.0 and live2.all()
+    assert picks[0].cands == [int(v) for v in g["candidates"]]
+    assert picks[0].potentials == g["potentials"]
+    assert picks[0].chosen == int(g["chosen"][0])
+    assert C2[1, 0] == g["new_centroid"][0] and live2.all()
 
 
 def test_kpp_first_centre_and_fill_order():
@@ -403,3 +415,26 @@ def test_forgy_big_means_counts_no_reseed_distances():
     st, recs = o.big_means(X, k, draws, init="forgy")
     assert st.live.all() and math.isfinite(st.f_opt)
     assert recs[0].n_d == recs[0].lloyd.n_d              # Forgy evaluates no distances
+
+
+def test_oracle_reproduces_its_recorded_runs():
+    # tests/golden/oracle_small_runs.json was written by
+    # tests/golden/make_golden.py from the oracle alone; a change of the
+    # oracle's arithmetic shows up here and must be justified by the paper
+    import importlib.util
+    import json
+    spec = importlib.util.spec_from_file_location("make_golden",
+                                                  os.path.join(GOLDEN, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    rec = json.load(open(os.path.join(GOLDEN, "oracle_small_runs.json")))
+    assert len(rec["cases"]) == len(mg.CASES)
+    for case in rec["cases"]:
+        got = mg.run(case["m"], case["n"], case["k"], case["s"], case["chunks"],
+                     case["components"], case["seed"], case["box"])
+        want = case["result"]
+        assert got["live"] == want["live"] and got["accepted"] == want["accepted"]
+        assert got["iters"] == want["iters"] and got["labels_sum"] == want["labels_sum"]
+        assert got["f_opt"] == pytest.approx(want["f_opt"], rel=1e-12)
+        assert got["sse"] == pytest.approx(want["sse"], rel=1e-12)
+        assert np.allclose(got["C"], want["C"], rtol=1e-12, atol=1e-12)
