@@ -324,10 +324,14 @@ bm_status bm_assign_rows_prec(const float* X_dev, int64_t m, int32_t n,
  * holds until the process exits.  The first call on each device looks up that
  * array's device address (cudaGetSymbolAddress, with the device current);
  * make that first call before any stream capture begins.  All calls share the
- * one array, so calls that overlap on the GPU (for example on two streams)
- * race and must be serialised by the caller.  A launch that would need more
- * than 2048 CTAs, k > 128, or a centroid table beyond shared memory returns
- * BM_EUNSUPPORTED. */
+ * one array, and calls that overlapped on the GPU would race on it: so every
+ * call holds a lock inside the library from its first use of the array until
+ * its result has been read back (the call blocks until its work is done),
+ * and calls from several host threads of the process, on one stream or on
+ * several, run one after another.  A launch that would need more than 2048
+ * CTAs, k > 128, or a centroid table beyond shared memory (where
+ * bm_assign_rows would switch to the tensor-core kernel, whose scratch grows
+ * with m) returns BM_EUNSUPPORTED. */
 bm_status bm_assign_rows_noalloc(const float* X_dev, int64_t m, int32_t n,
                                  const float* C_dev, const uint8_t* mask_dev,
                                  int32_t k, int32_t* labels_dev,
@@ -341,6 +345,19 @@ bm_status bm_assign_rows_noalloc(const float* X_dev, int64_t m, int32_t n,
  * other status means the bounded wait is broken) and the device stays usable.
  * Nothing faults, traps or hangs.  BM_EINVAL for a limit out of range. */
 bm_status bm_selftest_wait_timeout(int32_t timeout_ms, void* stream);
+
+/* Self-check of the K-means++ reseed (Sec. 3.3) across CTAs.  The values the
+ * CTAs of a chunk launch hand to each other between grid barriers while they
+ * pick a new centre (per-CTA D^2 sums, the candidate rows, the candidates'
+ * potentials) each carry a tag of their launch and slot; a reader checks the
+ * tag before it uses the value, waits (bounded; BM_ETIMEOUT on expiry) if the
+ * value has not been published yet, and counts that event.  Returns the
+ * number of such late reads in this process since the library was loaded,
+ * summed when the status of each launch is read back (end of bm_fit_chunk,
+ * bm_stream_push, bm_fit_workers, bm_fit_host, bm_kpp_reseed, bm_lloyd and
+ * the server's jobs).  0 means every exchange found its value published by
+ * the time the barrier released the reader.  Thread-safe. */
+uint64_t bm_sync_late_reads(void);
 
 /* ------------------------------------------------------------ grouped Lloyd
  * Many independent Lloyd problems (Sec. 2, stop rule of Sec. 5) -- the

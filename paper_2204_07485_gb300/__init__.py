@@ -136,6 +136,7 @@ _SIGS = {
     "bm_assign_rows_noalloc": (_i32, [_vp, _i64, _i32, _vp, _vp, _i32, _vp, _vp,
                                       _P(_dbl), _vp]),
     "bm_selftest_wait_timeout": (_i32, [_i32, _vp]),
+    "bm_sync_late_reads": (_u64, []),
     "bm_server_create": (_i32, [_P(bm_server_config), _P(_vp)]),
     "bm_server_destroy": (_i32, [_vp]),
     "bm_submit": (_i32, [_vp, _P(bm_job), _P(ctypes.c_uint64)]),
@@ -428,6 +429,12 @@ def bm_assign_rows_noalloc(X_dev, m, n, C_dev, mask_dev, k, labels_dev=None,
 def bm_selftest_wait_timeout(timeout_ms=100, stream=None):
     """Status of one grid-barrier wait that runs out (BM_ETIMEOUT expected)."""
     return _lib.bm_selftest_wait_timeout(int(timeout_ms), _stream(stream))
+
+
+def bm_sync_late_reads():
+    """K-means++ exchange values found not yet published after their grid
+    barrier (each waited for), summed over the process so far."""
+    return int(_lib.bm_sync_late_reads())
 
 
 # ------------------------------------------------------------------ serving

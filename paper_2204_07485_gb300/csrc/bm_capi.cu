@@ -9,6 +9,7 @@
 #include <cstring>
 #include <limits>
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <tuple>
 #include <vector>
@@ -182,6 +183,8 @@ struct Workspace {
   int32_t* blk_cnt = nullptr;
   Ctl* ctl = nullptr;
   Stats* stats = nullptr;
+  unsigned long long* kx = nullptr;   // K-means++ exchange tags (ChunkArgs::kx)
+  size_t kx_words = 0;
   double* apart = nullptr;   // assign per-CTA partials
   int apart_cap = 0;
   double* asse = nullptr;    // assign result
@@ -248,6 +251,8 @@ static bm_status ws_create(Workspace* w, long long m, int k, long long s,
   BM_TRY(w->alloc(&w->blk_cnt, (size_t)G));
   BM_TRY(w->alloc(&w->ctl, 1));
   BM_TRY(w->alloc(&w->stats, 1));
+  w->kx_words = 1 + 2 * (size_t)G + kMaxTrials;
+  BM_TRY(w->alloc(&w->kx, w->kx_words));
   // assignment partials: per CTA (FP32 kernels) or per 128-row tile (tensor cores)
   w->apart_cap = (int)std::max<long long>(std::max(p.agrid, 4096), (assign_rows + 127) / 128);
   BM_TRY(w->alloc(&w->apart, (size_t)w->apart_cap));
@@ -269,6 +274,8 @@ static bm_status ws_create(Workspace* w, long long m, int k, long long s,
   cudaMemsetAsync(w->mask_inc, 0, k, st);
   cudaMemsetAsync(w->ctl, 0, sizeof(Ctl), st);
   cudaMemsetAsync(w->stats, 0, sizeof(Stats), st);
+  cudaMemsetAsync(w->kx, 0, w->kx_words * 8, st);
+  cudaMemsetAsync(w->part_f, 0, (size_t)(kMaxTrials + 2) * G * 8, st);
   const double inf = std::numeric_limits<double>::infinity();
   cudaMemcpyAsync(w->f_opt, &inf, sizeof(double), cudaMemcpyHostToDevice, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) { w->release(); return BM_ECUDA; }
@@ -284,7 +291,7 @@ static ChunkArgs chunk_args(const Workspace& w, const Plan& p, const float* X,
   a.idx = w.idx; a.P = w.P; a.C = w.C; a.mask = w.mask;
   a.Cinc = w.Cinc; a.mask_inc = w.mask_inc; a.f_opt = w.f_opt;
   a.part_sum = w.part_sum; a.part_cnt = w.part_cnt; a.part_f = w.part_f;
-  a.blk_cnt = w.blk_cnt; a.ctl = w.ctl; a.stats = w.stats;
+  a.blk_cnt = w.blk_cnt; a.ctl = w.ctl; a.stats = w.stats; a.kx = w.kx;
   a.tc_kb = p.tc_kb; a.tc_n16 = p.tc_n16; a.tc_ncols = p.tc_ncols; a.tc_fb = p.tc_fb;
   a.tc_tpc = p.tc_tpc; a.tc_ns = p.tc_ns;
   a.Cb = w.Cb; a.sqs = w.sqs; a.Pb = w.Pb;
@@ -305,18 +312,29 @@ static bool shape_ok(long long m, int n, int k, long long s) {
 
 // Reads the status word; on error clears the control block so that the
 // workspace can be used again.
+// K-means++ exchange reads that found their value not yet published (each
+// waited for it), summed over every launch checked since the library loaded.
+static std::atomic<unsigned long long> g_late_reads{0};
+
 static bm_status check_status(Workspace& w, cudaStream_t st, long long m) {
   (void)m;
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return BM_ECUDA;
-  int32_t status = 0;
-  e = cudaMemcpy(&status, &w.ctl->status, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  Ctl h{};
+  e = cudaMemcpy(&h, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return BM_ECUDA;
-  if (status != 0) {
-    // an aborted launch may leave barrier counters behind
+  if (h.late != 0) {
+    g_late_reads += h.late;
+    const uint32_t zero = 0;
+    if (cudaMemcpy(&w.ctl->late, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess)
+      return BM_ECUDA;
+  }
+  if (h.status != 0) {
+    // an aborted launch may leave barrier counters and exchange tags behind
     cudaMemset(w.ctl, 0, sizeof(Ctl));
+    if (w.kx) cudaMemset(w.kx, 0, w.kx_words * 8);
     cudaDeviceSynchronize();
-    return (bm_status)status;
+    return (bm_status)h.status;
   }
   return BM_OK;
 }
@@ -447,6 +465,8 @@ void bm_config_default(bm_config* cfg) {
   cfg->init = BM_INIT_KMEANSPP;
   cfg->empty = BM_EMPTY_DEGENERATE;
 }
+
+uint64_t bm_sync_late_reads(void) { return g_late_reads.load(); }
 
 const char* bm_status_string(int32_t s) {
   switch (s) {

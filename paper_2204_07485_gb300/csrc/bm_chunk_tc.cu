@@ -736,7 +736,7 @@ __device__ __forceinline__ void tcc_load_cand(const ChunkArgs& a, const TccS& S,
 // K-means++ reseed of every degenerate slot, ascending (Sec. 3.3, Sec. 5).
 __device__ bool tcc_kpp(const ChunkArgs& a, const TccS& S, GridBarrier& gb, int r0, int nrows,
                         TccBound& bd, uint32_t tmem, TccPipe& pp, long long* nd_out,
-                        uint64_t* tsub) {
+                        uint64_t* tsub, unsigned long long gen) {
   const int k = a.k, G = gridDim.x, b = blockIdx.x, R = a.rows_per_cta;
   const int nlive = S.lidx[k];
   if (nlive == k) return true;
@@ -773,26 +773,31 @@ __device__ bool tcc_kpp(const ChunkArgs& a, const TccS& S, GridBarrier& gb, int 
     __syncthreads();
     nd += a.s;
   }
+  __shared__ int s_rows[kMaxTrials];
   for (int j = 0; j < k && ok; ++j) {
     if (S.live[j]) continue;
+    const unsigned long long tag = kx_tag(gen, j);
     const double mine = dmin_sum(S.dmin, nrows, S.red);
-    if (threadIdx.x == 0) DSUM[b] = mine;
+    kpp_put_dsum(a, DSUM, mine, tag);
     if (!gb.sync()) { ok = false; break; }
-    kpp_locate(a, S.dmin, r0, nrows, DSUM, j);
+    if (!kpp_locate(a, S.dmin, r0, nrows, DSUM, j, tag)) { ok = false; break; }
     if (!gb.sync()) { ok = false; break; }
-    for (int t = 0; t < a.trials; ++t) tcc_load_cand(a, S, t, __ldcg(a.ctl->cand + t));
+    if (!kpp_get_cands(a, s_rows, tag)) { ok = false; break; }
+    for (int t = 0; t < a.trials; ++t) tcc_load_cand(a, S, t, s_rows[t]);
     __syncthreads();
     tcc_sweep_cands(a, S, r0, nrows, a.trials);
+    double pot[kMaxTrials];
     for (int t = 0; t < a.trials; ++t) {
       double v = 0.0;
       for (int i = threadIdx.x; i < nrows; i += blockDim.x)
         v += (double)fminf(S.dmin[i], S.dc[t * R + i]);
-      v = block_sum_f64(v, S.red);
-      if (threadIdx.x == 0) a.part_f[(size_t)t * G + b] = v;
+      pot[t] = block_sum_f64(v, S.red);
     }
+    kpp_put_potentials(a, pot, tag);
     nd += (long long)a.s * a.trials;
     if (!gb.sync()) { ok = false; break; }
-    const int bt = kpp_best(a);
+    const int bt = kpp_best(a, tag);
+    if (bt < 0) { ok = false; break; }
     tcc_set_centroid(a, S, j, S.cand + bt * a.npad);
     for (int i = threadIdx.x; i < nrows; i += blockDim.x)
       S.dmin[i] = fminf(S.dmin[i], S.dc[bt * R + i]);
@@ -949,6 +954,7 @@ __global__ void __launch_bounds__(kTccThreads, 1) chunk_tc_kernel(ChunkArgs a) {
   S.ns = a.tc_ns;
 
   GridBarrier gb{a.ctl->bar + a.bar_sel, &a.ctl->status, 0u};
+  const unsigned long long gen = kx_generation(a);
   const int r0 = min(a.s, (int)blockIdx.x * R);
   const int nrows = min(R, a.s - r0);
   long long nd = 0;
@@ -1001,7 +1007,7 @@ __global__ void __launch_bounds__(kTccThreads, 1) chunk_tc_kernel(ChunkArgs a) {
   phase_tick(a, 1, &tclk);
   if (ok && (a.phases & kPhaseKpp)) {
     uint64_t tsub = tclk;
-    ok = tcc_kpp(a, S, gb, r0, nrows, bd, tmem, pp, &nd, &tsub);
+    ok = tcc_kpp(a, S, gb, r0, nrows, bd, tmem, pp, &nd, &tsub, gen);
     phase_tick(a, 2, &tclk);
   }
   if (ok && (a.phases & kPhaseLloyd))
@@ -1014,6 +1020,7 @@ __global__ void __launch_bounds__(kTccThreads, 1) chunk_tc_kernel(ChunkArgs a) {
       a.ctl->f_out = f;
       a.ctl->iters_out = it;
       a.ctl->bar[a.bar_sel ^ 1] = 0u;   // ready for the next launch
+      kx_advance(a, gen);
     }
     __syncthreads();
     if (s_acc) {

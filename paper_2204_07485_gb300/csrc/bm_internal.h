@@ -37,7 +37,8 @@ struct Ctl {
   int32_t iters_out;                  // Lloyd update steps of the last launch
   double f_out;                       // f(C'', P) of the last launch
   uint32_t assign_ticket;             // last-CTA ticket of the assign kernel
-  uint32_t pad_;
+  uint32_t late;                      // K-means++ exchange reads that found their
+                                      // value not yet published (see bm_kpp.cuh)
 };
 
 // Cumulative counters of a context, updated on the device by CTA 0.
@@ -90,6 +91,10 @@ struct ChunkArgs {
   int32_t* blk_cnt;    // [G]
   Ctl* ctl;
   Stats* stats;
+  // K-means++ exchange tags (bm_kpp.cuh): [0] the launch generation, then
+  // [1, 1 + G) the D^2 block sums', [1 + G, 1 + 2G) the potentials' and
+  // [1 + 2G, 1 + 2G + kMaxTrials) the candidate rows' tags
+  unsigned long long* kx;
   // tensor-core chunk kernel (rows wider than 32 features)
   int tc_kb;              // 64-feature K blocks
   int tc_n16;             // MMA N: k rounded up to 16

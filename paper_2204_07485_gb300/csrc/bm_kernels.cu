@@ -583,7 +583,7 @@ __device__ __forceinline__ void load_cand_row(const ChunkArgs& a, const Smem& S,
 // K-means++ reseed of every degenerate slot, ascending (Sec. 3.3, Sec. 5).
 template <int NP, bool GENERIC>
 __device__ bool phase_kpp(const ChunkArgs& a, const Smem& S, GridBarrier& gb,
-                          int r0, int nrows, long long* nd_out) {
+                          int r0, int nrows, long long* nd_out, unsigned long long gen) {
   const int k = a.k, G = gridDim.x, b = blockIdx.x;
   const int nlive = S.lidx[k];
   if (nlive == k) return true;
@@ -631,30 +631,35 @@ __device__ bool phase_kpp(const ChunkArgs& a, const Smem& S, GridBarrier& gb,
     nd += a.s;
   }
   const int R = a.rows_per_cta;
+  __shared__ int s_rows[kMaxTrials];
   for (int j = 0; j < k; ++j) {
     if (S.live[j]) continue;
+    const unsigned long long tag = kx_tag(gen, j);
     // (A) block sums of D^2
     const double mine = own_dmin_sum(S, nrows);
-    if (threadIdx.x == 0) DSUM[b] = mine;
+    kpp_put_dsum(a, DSUM, mine, tag);
     if (!gb.sync()) return false;
     // (B) targets, the blocks that hold them and the rows inside those blocks
-    kpp_locate(a, S.dmin, r0, nrows, DSUM, j);
+    if (!kpp_locate(a, S.dmin, r0, nrows, DSUM, j, tag)) return false;
     if (!gb.sync()) return false;
     // (C) potentials of the candidates
-    for (int t = 0; t < a.trials; ++t) load_cand_row(a, S, t, __ldcg(a.ctl->cand + t));
+    if (!kpp_get_cands(a, s_rows, tag)) return false;
+    for (int t = 0; t < a.trials; ++t) load_cand_row(a, S, t, s_rows[t]);
     __syncthreads();
     own_rows_to_cands<NP, GENERIC>(a, S, r0, nrows, a.trials);
+    double pot[kMaxTrials];
     for (int t = 0; t < a.trials; ++t) {
       double v = 0.0;
       for (int i = threadIdx.x; i < nrows; i += blockDim.x)
         v += (double)fminf(S.dmin[i], S.dc[t * R + i]);
-      v = block_sum_f64(v, S.red);
-      if (threadIdx.x == 0) a.part_f[(size_t)t * G + b] = v;
+      pot[t] = block_sum_f64(v, S.red);
     }
+    kpp_put_potentials(a, pot, tag);
     nd += (long long)a.s * a.trials;
     if (!gb.sync()) return false;
     // (D) choose the candidate with the lowest potential
-    const int bt = kpp_best(a);
+    const int bt = kpp_best(a, tag);
+    if (bt < 0) return false;
     set_centroid_row<GENERIC>(S, S.cand + bt * a.npad, j, a.npad, a.kpad);
     if (threadIdx.x == 0) S.live[j] = 1;
     if (b == 0) {
@@ -812,6 +817,7 @@ chunk_kernel(ChunkArgs a) {
   const ChunkSmem L = chunk_smem(a.npad, a.k, a.kpad, a.rows_per_cta, GENERIC);
   const Smem S = carve(smem_raw, L);
   GridBarrier gb{a.ctl->bar + a.bar_sel, &a.ctl->status, 0u};
+  const unsigned long long gen = kx_generation(a);
   const int r0 = min(a.s, (int)blockIdx.x * a.rows_per_cta);
   const int nrows = min(a.rows_per_cta, a.s - r0);
   long long nd = 0;
@@ -846,7 +852,7 @@ chunk_kernel(ChunkArgs a) {
     if constexpr (!GENERIC) stage_own_rows<NP>(a, S, r0, nrows);   // P written by the host
   }
   if (ok && (a.phases & kPhaseKpp)) {
-    ok = phase_kpp<NP, GENERIC>(a, S, gb, r0, nrows, &nd);
+    ok = phase_kpp<NP, GENERIC>(a, S, gb, r0, nrows, &nd, gen);
     phase_tick(a, 2, &tclk);
   }
   if (ok && (a.phases & kPhaseLloyd))
@@ -860,6 +866,7 @@ chunk_kernel(ChunkArgs a) {
       a.ctl->f_out = f;
       a.ctl->iters_out = it;
       a.ctl->bar[a.bar_sel ^ 1] = 0u;   // ready for the next launch
+      kx_advance(a, gen);
     }
     __syncthreads();
     if (s_acc) {

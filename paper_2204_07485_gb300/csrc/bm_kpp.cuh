@@ -3,6 +3,16 @@
 // row over the per-CTA D^2 sums and, once the candidates' potentials are
 // summed per CTA, the choice of the lowest potential.  Both run identically
 // in every CTA, so every CTA reaches the same decision without a broadcast.
+//
+// Every value one CTA hands to the others here (its D^2 block sum, its
+// candidates' potentials, a candidate row) is published with a tag: the
+// value is stored, then a tag unique to (launch generation, slot j) is stored
+// with release semantics, and a reader acquires the tag before it reads the
+// value.  The grid barrier between writer and reader already orders them, so
+// the first poll normally finds the tag; a reader that finds an older one
+// counts a late read in Ctl::late and waits (bounded) for the right tag.  A
+// value is therefore never used before it was written, whatever the barrier
+// did, and any such event is visible to the host.
 #pragma once
 
 #include "bm_device.cuh"
@@ -10,18 +20,119 @@
 
 namespace bm {
 
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Launch generation: read by every CTA at the start of a launch (the previous
+// launch on the workspace has completed), advanced by CTA 0 at its end.
+__device__ __forceinline__ unsigned long long kx_generation(const ChunkArgs& a) {
+  return __ldcg(a.kx);
+}
+__device__ __forceinline__ void kx_advance(const ChunkArgs& a, unsigned long long gen) {
+  a.kx[0] = gen + 1ull;
+}
+// Tag of slot j's exchange in launch generation gen (never 0: the tags start
+// zeroed, so no stale tag equals a current one).
+__device__ __forceinline__ unsigned long long kx_tag(unsigned long long gen, int j) {
+  return (gen << 32) | (unsigned long long)(uint32_t)(j + 1);
+}
+__device__ __forceinline__ unsigned long long* kx_dsum(const ChunkArgs& a) { return a.kx + 1; }
+__device__ __forceinline__ unsigned long long* kx_pot(const ChunkArgs& a) {
+  return a.kx + 1 + gridDim.x;
+}
+__device__ __forceinline__ unsigned long long* kx_cand(const ChunkArgs& a) {
+  return a.kx + 1 + 2 * gridDim.x;
+}
+
+// Waits until *tag == want.  Normally the first acquire succeeds.  Otherwise
+// counts a late read and polls with the grid barrier's bounds; gives up with
+// BM_ETIMEOUT in the status word (or when another CTA recorded an error) and
+// returns false.
+static __device__ __noinline__ bool kx_wait(const ChunkArgs& a, const unsigned long long* tag,
+                                     unsigned long long want) {
+  if (ld_acquire_u64(tag) == want) return true;
+  atomicAdd(&a.ctl->late, 1u);
+  uint64_t t0 = 0;
+  uint32_t polls = 0;
+  while (ld_acquire_u64(tag) != want) {
+    ++polls;
+    if ((polls & 255u) == 0) {
+      const uint64_t now = global_timer_ns();
+      if (t0 == 0) t0 = now;
+      if (ld_volatile(&a.ctl->status) != kStatusOk || polls > kSpinLimit ||
+          now - t0 > kSpinTimeoutNs) {
+        atomicCAS(&a.ctl->status, kStatusOk, kStatusTimeout);
+        return false;
+      }
+    }
+    __nanosleep(32);
+  }
+  return true;
+}
+
+// Thread 0 publishes this CTA's D^2 block sum for slot j.
+__device__ __forceinline__ void kpp_put_dsum(const ChunkArgs& a, double* DSUM, double v,
+                                             unsigned long long tag) {
+  if (threadIdx.x == 0) {
+    DSUM[blockIdx.x] = v;
+    st_release_u64(kx_dsum(a) + blockIdx.x, tag);
+  }
+}
+
+// Thread 0 publishes this CTA's candidate potentials (part_f[t][b], t < trials).
+__device__ __forceinline__ void kpp_put_potentials(const ChunkArgs& a, const double* v,
+                                                   unsigned long long tag) {
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < a.trials; ++t) a.part_f[(size_t)t * gridDim.x + blockIdx.x] = v[t];
+    st_release_u64(kx_pot(a) + blockIdx.x, tag);
+  }
+}
+
+__device__ __forceinline__ void kpp_put_cand(const ChunkArgs& a, int t, int row,
+                                             unsigned long long tag) {
+  a.ctl->cand[t] = row;
+  st_release_u64(kx_cand(a) + t, tag);
+}
+
+// Candidate rows of slot j into rows[0..trials) (shared); every thread gets
+// them.  Ends with a block barrier; false if a wait gave up.
+__device__ __forceinline__ bool kpp_get_cands(const ChunkArgs& a, int* rows,
+                                              unsigned long long tag) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) s_ok = 1;
+  __syncthreads();
+  if (threadIdx.x < a.trials) {
+    if (kx_wait(a, kx_cand(a) + threadIdx.x, tag)) rows[threadIdx.x] = __ldcg(a.ctl->cand + threadIdx.x);
+    else s_ok = 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 // Targets u_t * sum(D^2) for the trials of slot j; the CTA holding target t
-// (inclusive prefix over CTAs, then over its own rows in index order) writes
-// the row into ctl->cand[t].  A zero total falls back to a uniform row.
-// DSUM[0..G) holds the CTAs' D^2 sums; dmin[0..nrows) this CTA's D^2.
-// The caller's next grid barrier publishes ctl->cand.
-__device__ __forceinline__ void kpp_locate(const ChunkArgs& a, const float* dmin, int r0,
-                                           int nrows, const double* DSUM, int j) {
+// (inclusive prefix over CTAs, then over its own rows in index order)
+// publishes the row as candidate t.  A zero total falls back to a uniform row.
+// DSUM[0..G) holds the CTAs' D^2 sums (published with tag); dmin[0..nrows)
+// this CTA's D^2.  Returns false (every thread) if a wait gave up.
+__device__ __forceinline__ bool kpp_locate(const ChunkArgs& a, const float* dmin, int r0,
+                                           int nrows, const double* DSUM, int j,
+                                           unsigned long long tag) {
   __shared__ double s_tgt[kMaxTrials], s_excl[kMaxTrials], s_total;
-  __shared__ int s_bstar[kMaxTrials];
+  __shared__ int s_bstar[kMaxTrials], s_ok;
   const int G = gridDim.x, b = blockIdx.x;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (w == 0) {
+    // every block sum's tag first: afterwards the sums are read as published
+    bool ok = true;
+    for (int x = l; x < G; x += 32) ok = kx_wait(a, kx_dsum(a) + x, tag) && ok;
+    ok = __all_sync(0xffffffffu, ok);
+    if (l == 0) s_ok = ok;
     double carry = 0.0;
     for (int base = 0; base < G; base += 32) {
       const double v = (base + l < G) ? __ldcg(DSUM + base + l) : 0.0;
@@ -87,13 +198,14 @@ __device__ __forceinline__ void kpp_locate(const ChunkArgs& a, const float* dmin
     }
   }
   __syncthreads();
+  if (!s_ok) return false;
   // the CTA that owns a target finds the row inside its block
   for (int t = 0; t < a.trials; ++t) {
     if (s_total == 0.0) {
       if (b == 0 && threadIdx.x == 0) {
         const double u = unit_double(philox_word(a.seed, (uint64_t)a.t, 2, 0,
                                                  (uint64_t)(j * a.trials + t)));
-        a.ctl->cand[t] = (int)floor(u * (double)a.s);
+        kpp_put_cand(a, t, (int)floor(u * (double)a.s), tag);
       }
     } else if (s_bstar[t] == b && w == 0) {
       double run = s_excl[t];
@@ -114,18 +226,23 @@ __device__ __forceinline__ void kpp_locate(const ChunkArgs& a, const float* dmin
         run = __shfl_sync(0xffffffffu, incl, 31);
       }
       if (cand < 0) cand = lastp;
-      if (l == 0) a.ctl->cand[t] = r0 + cand;
+      if (l == 0) kpp_put_cand(a, t, r0 + cand, tag);
     }
   }
+  return true;
 }
 
 // Index of the trial with the lowest potential (sum over CTAs of
-// part_f[t][u], fixed order), lowest trial on ties.  Ends with a block barrier.
-__device__ __forceinline__ int kpp_best(const ChunkArgs& a) {
+// part_f[t][u], fixed order, published with tag), lowest trial on ties; -1
+// (every thread) if a wait gave up.  Ends with a block barrier.
+__device__ __forceinline__ int kpp_best(const ChunkArgs& a, unsigned long long tag) {
   __shared__ int s_best;
   const int G = gridDim.x;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (w == 0) {
+    bool ok = true;
+    for (int u = l; u < G; u += 32) ok = kx_wait(a, kx_pot(a) + u, tag) && ok;
+    ok = __all_sync(0xffffffffu, ok);
     double v[kMaxTrials];
 #pragma unroll
     for (int t = 0; t < kMaxTrials; ++t) v[t] = 0.0;
@@ -142,7 +259,7 @@ __device__ __forceinline__ int kpp_best(const ChunkArgs& a) {
         if (t == 0 || phi < bestv) { bestv = phi; best = t; }
       }
     }
-    if (l == 0) s_best = best;
+    if (l == 0) s_best = ok ? best : -1;
   }
   __syncthreads();
   return s_best;

@@ -35,6 +35,13 @@ constexpr int kNoAllocMaxDevices = 64;
 static std::mutex g_noalloc_mu;
 static unsigned char* g_noalloc_addr[kNoAllocMaxDevices] = {};
 
+// Every call of the entry point uses the one scratch array, so a call holds
+// this lock from its first use of the array (the ticket reset) until its
+// result has been read back.  Calls from several host threads -- on one
+// stream or on several -- therefore run one after another and never reset
+// or read each other's ticket and result.
+static std::mutex g_noalloc_call_mu;
+
 static bm_status noalloc_scratch(unsigned char** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return BM_ECUDA;
@@ -65,6 +72,7 @@ extern "C" bm_status bm_assign_rows_noalloc(const float* X_dev, int64_t m,
     return BM_EINVAL;
   if (k > kMaxK) return BM_EUNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> call_lock(g_noalloc_call_mu);
   // at least one live centroid (read into a fixed host buffer)
   uint8_t live_h[kMaxK];
   if (cudaMemcpyAsync(live_h, mask_dev, (size_t)k, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

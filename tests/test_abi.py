@@ -240,7 +240,7 @@ def test_binding_argument_counts_match_the_header():
     import paper_2204_07485_gb300 as bm
     src = open(os.path.join(ROOT, "include", "bigmeans.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    decls = re.findall(r"\b(?:bm_status|void|const char\s*\*|int32_t|int64_t|size_t)\s+"
+    decls = re.findall(r"\b(?:bm_status|void|const char\s*\*|int32_t|int64_t|uint64_t|size_t)\s+"
                        r"(bm_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S)
     assert sorted(d[0] for d in decls) == _declared()
     for name, params in decls:

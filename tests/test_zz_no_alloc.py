@@ -40,9 +40,9 @@ def test_noalloc_assign_matches_allocating_entry_point_on_consecutive_calls():
         lab = torch.full((m,), -1, dtype=torch.int32, device="cuda:0")
         dmin = torch.full((m,), -1.0, dtype=torch.float32, device="cuda:0")
         sse = bm.bm_assign_rows_noalloc(Xd, m, n, Cd, md, k, lab, dmin)
+        # the same kernel and grid as the allocating call: equal bit for bit
         assert torch.equal(lab, lab_ref)
-        np.testing.assert_allclose(host(dmin), host(dmin_ref),
-                                   rtol=(n + 2) * 2.0 ** -24, atol=0)
+        assert torch.equal(dmin, dmin_ref)
         assert rel(sse, sse_ref) <= OBJ_REL
 
 
@@ -56,4 +56,33 @@ def test_noalloc_rejects_bad_arguments():
     C200 = np.zeros((200, 4), np.float32)
     with pytest.raises(bm.BigMeansError) as e:
         bm.bm_assign_rows_noalloc(dev(X), 1000, 4, dev(C200), dev(np.ones(200, np.uint8)), 200)
+    assert e.value.status == bm.BM_EUNSUPPORTED
+
+
+def test_noalloc_sse_only_call_matches():
+    """labels and dmin both NULL: only the objective is produced."""
+    require_gpu()
+    import paper_2204_07485_gb300 as bm
+    m, n, k = 30_011, 12, 17
+    X, C, live = _case(m, n, k, 3)
+    Xd, Cd, md = dev(X), dev(C), dev(live)
+    sse_ref = bm.bm_assign_rows(Xd, m, n, Cd, md, k)
+    for _ in range(2):
+        sse = bm.bm_assign_rows_noalloc(Xd, m, n, Cd, md, k)
+        assert rel(sse, sse_ref) <= OBJ_REL
+
+
+def test_noalloc_refuses_tables_beyond_shared_memory():
+    """n = 384, k = 100: the FP32 centroid table does not fit in shared
+    memory.  bm_assign_rows switches to the tensor-core kernel (whose scratch
+    grows with m); the allocation-free call refuses the shape instead."""
+    require_gpu()
+    import paper_2204_07485_gb300 as bm
+    m, n, k = 4_000, 384, 100
+    X, C, live = _case(m, n, k, 4)
+    Xd, Cd, md = dev(X), dev(C), dev(live)
+    lab_ref = torch.empty(m, dtype=torch.int32, device="cuda:0")
+    bm.bm_assign_rows(Xd, m, n, Cd, md, k, lab_ref)
+    with pytest.raises(bm.BigMeansError) as e:
+        bm.bm_assign_rows_noalloc(Xd, m, n, Cd, md, k)
     assert e.value.status == bm.BM_EUNSUPPORTED
