@@ -1,11 +1,16 @@
 """Benchmark of the GB300 Big-means hot path (one JSON line on stdout).
 
-Workload (default): the m = 1,000,000, n = 28 anisotropic Gaussian mixture
-with 1 % outliers, k = 25, s = 50,000, 100 chunks, then the final full-data
-assignment with its float64 SSE.  One step = one complete Big-means job:
-reset the incumbent, 100 chunks (sample draw, gather, K-means++ reseed, Lloyd
-to the paper's stop rule, keep-the-best), final assignment.  The metric is
-distance throughput: 2 n flops per point-to-centroid distance evaluation
+Workload (default): the precision-form job -- m = 10,000,000 points, n = 128,
+100 isotropic Gaussian components with Dirichlet(0.5) weights (generated on
+the device, 5.12 GB), k = 50, s = 50,000, 100 chunks, then the final
+full-data assignment with its float64 SSE.  One step = one complete Big-means
+job: reset the incumbent, 100 chunks (sample draw, gather, K-means++ reseed,
+Lloyd to the paper's stop rule, keep-the-best), final assignment.
+
+The timed form is BF16 + rescore (split BF16 tensor-core distances with exact
+FP32 rescoring of every row the error bound cannot settle); the plain FP32
+form of the same job is timed beside it (time to the same SSE).  The metric
+is distance throughput: 2 n flops per point-to-centroid distance evaluation
 (the paper's n_d counter) over the step time.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
@@ -16,8 +21,10 @@ method) on a bounded sample of the same workload.
 import argparse
 import json
 import os
+import platform
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -30,32 +37,47 @@ METRIC = ("dist TFLOP/s & time-to-SSE, BF16+rescore vs plain FP32 @≤1e-6 rel; 
           "req p50/p99")
 UNIT = "TFLOP/s"
 
-WORKLOAD = dict(name="hepmass_like_m1e6_n28_k25_s50000_T100", m=1_000_000, n=28,
-                k=25, s=50_000, chunks=100, seed=0)
-CPU_SAMPLE_CHUNKS = 20
-# precision comparison on the m = 1e7, n = 128 mixture (generated on the device)
+# the timed job: m = 1e7, n = 128 mixture (generated on the device)
 C3_WORKLOAD = dict(name="gas_sensor_like_m1e7_n128_k50_s50000_T100", m=10_000_000, n=128,
                    k=50, s=50_000, chunks=100, seed=0)
-# the E4M3 variant: per-feature scales log-uniform in [0.1, 10]
+HEAD_FORM = "bf16x3"
+# further jobs reported beside it
+C2_WORKLOAD = dict(name="hepmass_like_m1e6_n28_k25_s50000_T100", m=1_000_000, n=28,
+                   k=25, s=50_000, chunks=100, seed=0)
 C3_FP8_WORKLOAD = dict(name="scaled_384_m2e6_n384_k100_s50000_T100", m=2_000_000, n=384,
                        k=100, s=50_000, chunks=100, seed=0)
+
+# the oracle's bounded sample of the timed job: the first chunks of the run
+# plus the final assignment of every ASSIGN_STRIDE-th row
+CPU_SAMPLE_CHUNKS = 8
+CPU_ASSIGN_STRIDE = 10
+REF_SAMPLE_CHUNKS = 1        # per step of --impl reference
+REF_ASSIGN_STRIDE = 200
+
+FORM_CODES = {"fp32": 0, "bf16": 1, "fp8": 2, "bf16x3": 3}
+
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one chunk_tc_kernel
+# launch (a typical chunk: gather + split-BF16 planes + Lloyd), n = 128,
+# k = 50, s = 50,000; the gather reads s rows whatever m is
+CHUNK_TC_DRAM_BYTES = 31_585_024
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the further jobs (n = 28, E4M3, launch latency, grouped, serving)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-grouped", action="store_true")
     ap.add_argument("--profile", choices=["chunk_np", "chunk_tc", "assign_tc", "assign_fp8",
                                           "grouped"],
                     default=None,
                     help="run one short job of a kernel family (for ncu captures) and exit")
-    ap.add_argument("--chunks", type=int, default=WORKLOAD["chunks"])
+    ap.add_argument("--chunks", type=int, default=C3_WORKLOAD["chunks"])
     return ap.parse_args()
 
 
@@ -66,21 +88,14 @@ def dist_env():
     return rank, world, local
 
 
-def peaks():
+def measured_peaks():
+    """(HBM GB/s, BF16 dense TFLOP/s burst, source) of the GB300s."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return d.get("hbm_gbs", 6800.0), "measured"
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
     except OSError:
-        return 6800.0, "fallback"
-
-
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one chunk_kernel<28, 0>
-# launch on the default workload (a typical chunk: gather + Lloyd)
-CHUNK_NP28_DRAM_BYTES = 11_244_288
-
-# FP32 ALU peak of GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz.
-FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+        return 6800.0, 1900.0, "fallback"
 
 
 class ClockSampler:
@@ -99,7 +114,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -120,7 +135,7 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        sm, mx, pw, reasons = [], None, [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
@@ -129,6 +144,7 @@ class ClockSampler:
             try:
                 sm.append(float(parts[0]))
                 mx = float(parts[1])
+                pw.append(float(parts[2]))
             except ValueError:
                 continue
             for nm, val in zip(names, parts[4:8]):
@@ -137,77 +153,399 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": float(max(pw)) if pw else None}
 
 
-def make_data(wl):
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
+
+
+# ------------------------------------------------------------ oracle baseline
+
+def oracle_sample_inputs(Xd, wl, chunks, stride, path):
+    """Writes the rows the oracle's bounded sample reads to `path` (.npz): the
+    sample rows of chunks 0..chunks-1 (with their draws, indices remapped into
+    the compact array) and every stride-th row of X for the final assignment."""
+    import torch
     import bminputs
-    return bminputs.mixtures.hepmass_like(wl["seed"], m=wl["m"])
+    m, k, s, seed = wl["m"], wl["k"], wl["s"], wl["seed"]
+    idxs, ufs, us = [], [], []
+    for t in range(chunks):
+        idx, uf, u = bminputs.chunk_draws(seed, t, m, s, k)
+        idxs.append(np.asarray(idx, np.int64))
+        ufs.append(uf)
+        us.append(u)
+    allidx = np.concatenate(idxs)
+    Xs = Xd[torch.from_numpy(allidx).to(Xd.device)].cpu().numpy()
+    rows = np.arange(0, m, stride, dtype=np.int64)
+    Xa = Xd[torch.from_numpy(rows).to(Xd.device)].cpu().numpy()
+    np.savez(path, Xs=Xs, Xa=Xa, uf=np.array(ufs), u=np.stack(us), s=s, k=k, chunks=chunks)
+    return {"chunk_rows": int(len(allidx)), "assign_rows": int(len(rows))}
 
 
-def cpu_baseline(X, wl, chunks):
-    """The FP64 oracle, as it stands, on the first `chunks` chunks + the full
-    final assignment; returns the same metric (distance TFLOP/s)."""
-    import bminputs
+def _oracle_job(args):
+    """One bounded oracle run (child process, one thread): Alg. 1 on the saved
+    chunk draws, then the final assignment of the saved rows.  With start_at,
+    the run waits for that wall-clock time after loading, so concurrent runs
+    start together.  Returns (seconds, distance evaluations, SSE of the sampled
+    rows, wall-clock end)."""
+    path, core, start_at = args
+    if core is not None and hasattr(os, "sched_setaffinity"):
+        try:
+            os.sched_setaffinity(0, {core})
+        except OSError:
+            pass
     import oracle
-    m, n, k, s = wl["m"], wl["n"], wl["k"], wl["s"]
-    draws = [bminputs.chunk_draws(wl["seed"], t, m, s, k) for t in range(chunks)]
+    d = np.load(path)
+    Xs, Xa = d["Xs"], d["Xa"]
+    s, k, chunks = int(d["s"]), int(d["k"]), int(d["chunks"])
+    draws = [(np.arange(t * s, (t + 1) * s), float(d["uf"][t]), d["u"][t]) for t in range(chunks)]
+    if start_at is not None:
+        time.sleep(max(0.0, start_at - time.time()))
     t0 = time.perf_counter()
-    st, recs = oracle.big_means(X, k, draws)
-    _, sse, _, _ = oracle.final_assignment(X, st.C, st.live)
+    st, recs = oracle.big_means(Xs, k, draws)
+    _, sse, _, _ = oracle.final_assignment(Xa, st.C, st.live)
     dt = time.perf_counter() - t0
-    nd = sum(r.n_d for r in recs) + m * int(st.live.sum())
-    return {"value": 2.0 * n * nd / dt / 1e12, "unit": UNIT, "cores": 1,
-            "kind": "oracle",
-            "sample": "first %d of %d chunks + final assignment of all %d rows, "
-                      "numpy/scipy float64, single thread; %.2f s, SSE %.6e"
-                      % (chunks, wl["chunks"], m, dt, sse),
-            "seconds": dt, "n_d": nd}
+    nd = sum(r.n_d for r in recs) + len(Xa) * int(st.live.sum())
+    return dt, nd, sse, time.time()
+
+
+def _oracle_proc(args, q):
+    q.put(_oracle_job(args))
+
+
+def _oracle_pool(path, cores, lead_s=12.0):
+    """Runs len(cores) concurrent one-thread oracle jobs (one spawned process
+    per core, pinned to it, all starting at one wall-clock time after their
+    imports and loads); returns (wall seconds, [(s, n_d, sse, end)])."""
+    import multiprocessing as mp
+    saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                             "MKL_NUM_THREADS")}
+    for v in saved:
+        os.environ[v] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        q = ctx.Queue()
+        start_at = time.time() + lead_s
+        procs = [ctx.Process(target=_oracle_proc, args=((path, c, start_at), q)) for c in cores]
+        for pr in procs:
+            pr.start()
+        res = []
+        try:
+            for _ in procs:
+                res.append(q.get(timeout=900))
+        finally:
+            for pr in procs:
+                pr.join(timeout=30)
+                if pr.is_alive():
+                    pr.terminate()
+    finally:
+        for v, val in saved.items():
+            if val is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = val
+    wall = max(r[3] for r in res) - start_at
+    return wall, res
+
+
+def cpu_baseline(Xd, wl, chunks=CPU_SAMPLE_CHUNKS, stride=CPU_ASSIGN_STRIDE, all_cores=True):
+    """The FP64 oracle, as it stands, on a bounded sample of the timed job
+    (its first `chunks` chunks + the final assignment of every stride-th row),
+    on one core and as one concurrent replica per core; the same metric
+    (distance TFLOP/s), measured on the sample."""
+    n = wl["n"]
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "oracle_sample.npz")
+        info = oracle_sample_inputs(Xd, wl, chunks, stride, path)
+        core0 = sorted(os.sched_getaffinity(0))[0] if hasattr(os, "sched_getaffinity") else None
+        wall1, r1 = _oracle_pool(path, [core0], lead_s=6.0)
+        secs, nd, sse, _ = r1[0]
+        out = {"value": 2.0 * n * nd / secs / 1e12, "unit": UNIT, "cores": 1,
+               "kind": "oracle", "cpu": cpu_model(),
+               "sample": "first %d of %d chunks (%d sample rows) + final assignment of "
+                         "every %dth row (%d of %d), numpy/scipy float64, one thread pinned "
+                         "to one core; %.2f s, sampled SSE %.6e; the metric is a rate, "
+                         "measured on the sample"
+                         % (chunks, wl["chunks"], info["chunk_rows"], stride,
+                            info["assign_rows"], wl["m"], secs, sse),
+               "seconds": secs, "n_d": nd}
+        if all_cores:
+            ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") \
+                else (os.cpu_count() or 1)
+            cores = sorted(os.sched_getaffinity(0))[:ncores] if hasattr(os, "sched_getaffinity") \
+                else list(range(ncores))
+            wallN, rN = _oracle_pool(path, cores)
+            ndN = sum(r[1] for r in rN)
+            out["all_cores"] = {
+                "value": 2.0 * n * ndN / wallN / 1e12, "unit": UNIT, "cores": len(cores),
+                "sample": "%d concurrent one-thread replicas of the same sample, one per "
+                          "core; aggregate distance throughput over the wall time %.2f s"
+                          % (len(cores), wallN)}
+    return out
 
 
 def run_reference(args, wl):
+    """--impl reference: the FP64 oracle on a bounded sample of the timed job
+    per step (rank 0 only)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    X = make_data(wl)
-    vals = []
-    for _ in range(args.warmup):
-        cpu_baseline(X, wl, 2)
-    for _ in range(args.steps):
-        vals.append(cpu_baseline(X, wl, max(2, CPU_SAMPLE_CHUNKS // max(1, args.steps))))
-    v = float(np.mean([b["value"] for b in vals]))
-    secs = float(np.mean([b["seconds"] for b in vals]))
+    import torch
+    import bminputs
+    dev = torch.device("cuda", 0)
+    Xd = bminputs.mixtures.gas_sensor_like_device(wl["seed"], m=wl["m"], n=wl["n"], device=dev)
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "oracle_sample.npz")
+        info = oracle_sample_inputs(Xd, wl, REF_SAMPLE_CHUNKS, REF_ASSIGN_STRIDE, path)
+        del Xd
+        torch.cuda.empty_cache()
+        for _ in range(args.warmup):
+            _oracle_job((path, None, None))
+        runs = [_oracle_job((path, None, None)) for _ in range(args.steps)]
+    secs = float(np.mean([r[0] for r in runs]))
+    nd = runs[0][1]
+    v = 2.0 * wl["n"] * nd / secs / 1e12
+    sample = ("first %d of %d chunks (%d sample rows) + final assignment of every %dth row "
+              "(%d of %d), numpy/scipy float64, single thread, per step; the metric is a "
+              "rate, measured on the sample" % (REF_SAMPLE_CHUNKS, wl["chunks"],
+                                                info["chunk_rows"], REF_ASSIGN_STRIDE,
+                                                info["assign_rows"], wl["m"]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": secs * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl["name"], "m": wl["m"], "n": wl["n"], "k": wl["k"],
-                       "s": wl["s"], "chunks_per_step": vals[0]["sample"]},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": vals[0]["sample"],
-                             "value": v, "unit": UNIT},
+                       "s": wl["s"], "chunks": wl["chunks"], "sample": sample},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "cpu": cpu_model(),
+                             "sample": sample, "value": v, "unit": UNIT},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
+def job_step(bm, ctx, stream, T, labels, ev):
+    """One complete job on ctx: reset, T chunks, final assignment.  ev: three
+    CUDA events recorded on the library's stream around the fit and the
+    assignment."""
+    bm.bm_reset(ctx)
+    ev[0].record(stream)
+    rep = bm.bm_fit_chunk(ctx, T)
+    ev[1].record(stream)
+    sse = bm.bm_assign(ctx, labels)
+    ev[2].record(stream)
+    return rep, sse
+
+
+def run_ours(args, wl):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    import bminputs
+    import paper_2204_07485_gb300 as bm
+
+    m, n, k, s, T = wl["m"], wl["n"], wl["k"], wl["s"], args.chunks
+    seed = wl["seed"] + 1000 * rank          # independent replica per rank
+    Xd = bminputs.mixtures.gas_sensor_like_device(wl["seed"], m=m, n=n, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    labels = torch.empty(m, dtype=torch.int32, device=dev)
+    cfgs = {f: bm.bm_config_default(m=m, n=n, k=k, s=s, seed=seed, precision=FORM_CODES[f])
+            for f in (HEAD_FORM, "fp32")}
+    ctxs = {f: bm.bm_create(cfgs[f], Xd, stream.cuda_stream) for f in cfgs}
+    new_ev = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(3)]   # noqa: E731
+
+    for _ in range(args.warmup):
+        job_step(bm, ctxs[HEAD_FORM], stream, T, labels, new_ev())
+    job_step(bm, ctxs["fp32"], stream, T, labels, new_ev())
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    # X (5.12 GB) is far larger than L2 (129 MB): every step streams it anew
+    events, reps, fevents, freps = [], [], [], []
+    with ClockSampler(local if world > 1 else 0) as clocks:
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            ev = new_ev()
+            reps.append(job_step(bm, ctxs[HEAD_FORM], stream, T, labels, ev))
+            events.append(ev)
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall
+        # the plain FP32 form of the same job, beside it (same sampler window)
+        for _ in range(args.steps):
+            ev = new_ev()
+            freps.append(job_step(bm, ctxs["fp32"], stream, T, labels, ev))
+            fevents.append(ev)
+        torch.cuda.synchronize(dev)
+    fit_ms = [e[0].elapsed_time(e[1]) for e in events]
+    asg_ms = [e[1].elapsed_time(e[2]) for e in events]
+    step_ms = [a + b for a, b in zip(fit_ms, asg_ms)]
+    ffit = [e[0].elapsed_time(e[1]) for e in fevents]
+    fasg = [e[1].elapsed_time(e[2]) for e in fevents]
+    rep, sse = reps[-1]
+    frep, fsse = freps[-1]
+    C = np.zeros((k, n), np.float32)
+    mask = np.zeros(k, np.uint8)
+    f_opt = bm.bm_objective(ctxs[HEAD_FORM], C, mask)
+    nlive = int(mask.sum())
+    nd_fit = rep["n_d"]                      # K-means++ + Lloyd of the step
+    nd_step = nd_fit + m * nlive             # + final assignment
+    flops_step = 2.0 * n * nd_step
+    my_ms = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([my_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    else:
+        total_ms = my_ms
+    value = world * args.steps * flops_step / (total_ms / 1e3) / 1e12
+    phases = traced_phases(bm, Xd, cfgs[HEAD_FORM], stream, T)
+
+    # roofline of the dominant kernel (largest share of the step)
+    fit_per_step = float(np.mean(fit_ms))
+    asg_per_step = float(np.mean(asg_ms))
+    hbm_peak, bf16_peak, peak_src = measured_peaks()
+    chunk_kernel = {
+        "kernel": "chunk_tc_kernel (gather + split-BF16 planes + K-means++ + Lloyd + "
+                  "keep-best; split-BF16 tcgen05 MMAs, exact FP32 rescoring)",
+        "bound": "tensor",
+        "achieved": 2.0 * n * nd_fit / (fit_per_step / 1e3) / 1e12,
+        "peak": bf16_peak, "unit": "TFLOP/s",
+        "peak_source": "%s dense BF16 (burst) of MEASURED_PEAKS" % peak_src,
+        "launch_ms": fit_per_step / T,
+        "launches_per_step": T, "share": fit_per_step / (fit_per_step + asg_per_step),
+        "hbm_bytes_per_launch": s * n * 4,
+        "hbm_gbs": s * n * 4 * T / (fit_per_step / 1e3) / 1e9}
+    chunk_kernel["frac"] = chunk_kernel["achieved"] / chunk_kernel["peak"]
+    abytes = m * n * 4 + m * 4
+    assign_kernel = {
+        "kernel": "assign_tcs_kernel (final assignment, split-BF16 MMAs + exact FP32 "
+                  "rescoring, FP64 SSE)",
+        "bound": "hbm",
+        "achieved": abytes / (asg_per_step / 1e3) / 1e9, "peak": hbm_peak,
+        "peak_source": "%s HBM copy bandwidth" % peak_src,
+        "unit": "GB/s", "launch_ms": asg_per_step,
+        "share": asg_per_step / (fit_per_step + asg_per_step), "algorithmic_bytes": abytes}
+    assign_kernel["frac"] = assign_kernel["achieved"] / assign_kernel["peak"]
+    dom = chunk_kernel if chunk_kernel["share"] >= assign_kernel["share"] else assign_kernel
+    traffic = CHUNK_TC_DRAM_BYTES if dom is chunk_kernel else None
+    roofline = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
+                "unit": dom["unit"], "frac": dom["frac"], "traffic": traffic,
+                "kernel": dom["kernel"], "peak_source": dom["peak_source"],
+                "timing": "CUDA events on the library's stream around bm_fit_chunk "
+                          "(100 chunk launches + 2 sample-draw launches) each timed step"}
+
+    # end to end through the host-memory entry point (pinned X in, results out)
+    Xh = torch.empty((m, n), dtype=torch.float32).pin_memory()
+    Xh.copy_(Xd)
+    lab_h = torch.empty(m, dtype=torch.int32).pin_memory()
+    Ch = np.zeros((k, n), np.float32)
+    mh = np.zeros(k, np.uint8)
+    e2e_times = []
+    for i in range(max(1, min(args.steps, 3)) + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        sse_h, rep_h = bm.bm_fit_host(cfgs[HEAD_FORM], Xh.data_ptr(), T, Ch, mh, lab_h.data_ptr())
+        if i > 0:                            # the first call sets up the host pool
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_val = flops_step / float(np.median(e2e_times)) / 1e12
+    e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": m * n * 4,
+           "d2h_bytes_per_step": m * 4 + k * n * 4 + k + 8,
+           "ms_per_step": float(np.median(e2e_times)) * 1e3,
+           "host_gather_ctas": rep_h["host_gathers"],
+           "sse_equals_device_path": bool(sse_h == sse)}
+    del Xh, lab_h
+
+    out = None
+    if rank == 0:
+        head_ms = total_ms / args.steps
+        fp32_ms = float(np.mean(np.add(ffit, fasg)))
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": head_ms, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f32",
+               "data": "synthetic",
+               "config": {"workload": wl["name"], "m": m, "n": n, "k": k, "s": s,
+                          "chunks": T, "seed": wl["seed"],
+                          "form": "BF16 + rescore (split BF16 tensor-core products, FP32 "
+                                  "accumulation, exact FP32 rescoring)",
+                          "l2": "X is 5.12 GB, 40x L2: each step streams it from HBM",
+                          "parallelism": "replicas (independent job per GPU)"},
+               "time_to_sse_ms": head_ms, "sse": sse,
+               "fp32": {"time_to_sse_ms": fp32_ms, "fit_ms": float(np.mean(ffit)),
+                        "assign_ms": float(np.mean(fasg)), "sse": fsse,
+                        "value": 2.0 * n * (frep["n_d"] + m * nlive) / (fp32_ms / 1e3) / 1e12,
+                        "sse_rel_diff_vs_head": abs(fsse - sse) / fsse,
+                        "same_lloyd_iters": frep["lloyd_iters"] == rep["lloyd_iters"]},
+               "speedup_vs_fp32": fp32_ms / head_ms,
+               "f_opt": f_opt, "live": nlive, "lloyd_iters_per_step": rep["lloyd_iters"],
+               "accepted_per_step": rep["accepted"], "n_d_per_step": nd_step,
+               "fit_ms_per_step": fit_per_step, "assign_ms_per_step": asg_per_step,
+               "chunk_phase_ms_per_step": phases, "wall_s": t_wall,
+               "gpu_launches": args.steps * (T + (T + 63) // 64 + 1),
+               "roofline": roofline,
+               "kernels": {"chunk": chunk_kernel, "assign": assign_kernel},
+               "clocks": clocks.summary(), "e2e": e2e}
+    for c in ctxs.values():
+        bm.bm_destroy(c)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(Xd, wl)
+    del Xd, labels
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_extras:
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        extra = {}
+        w2 = C2_WORKLOAD
+        X2 = torch.from_numpy(bminputs.mixtures.hepmass_like(w2["seed"], m=w2["m"])).to(dev)
+        extra[w2["name"]] = precision_forms(bm, torch, dev, X2, w2["m"], w2["n"], w2["k"],
+                                            w2["s"], w2["chunks"], w2["seed"], 5, 2, flush)
+        del X2
+        v8 = C3_FP8_WORKLOAD
+        Xs = bminputs.mixtures.scaled_384_device(v8["seed"], m=v8["m"], device=dev)
+        extra[v8["name"]] = precision_forms(bm, torch, dev, Xs, v8["m"], v8["n"], v8["k"],
+                                            v8["s"], v8["chunks"], v8["seed"], 3, 1, flush,
+                                            forms=("fp32", "bf16x3", "fp8"))
+        del Xs, flush
+        torch.cuda.empty_cache()
+        out["other_jobs"] = extra
+        out["launch_latency"] = launch_latency(bm, torch, dev)
+        if not args.no_grouped:
+            out["grouped"] = grouped(bm, torch, dev)
+        if not args.no_serving:
+            out["serving"] = serving(bm, torch, dev)
+    if rank == 0:
+        print(json.dumps(out))
+    return 0
+
+
 def time_jobs(bm, torch, ctx, stream, T, steps, warmup, flush, labels):
-    """Runs `warmup` + `steps` complete jobs; per-step CUDA-event times."""
-    def step(ev):
-        bm.bm_reset(ctx)
-        ev[0].record(stream)
-        rep = bm.bm_fit_chunk(ctx, T)
-        ev[1].record(stream)
-        sse = bm.bm_assign(ctx, labels)
-        ev[2].record(stream)
-        return rep, sse
+    """Runs `warmup` + `steps` complete jobs; per-step CUDA-event times (L2
+    flushed between steps)."""
+    def new_ev():
+        return [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     for _ in range(warmup):
-        step([torch.cuda.Event(enable_timing=True) for _ in range(3)])
+        job_step(bm, ctx, stream, T, labels, new_ev())
     torch.cuda.synchronize()
     events, reps = [], []
     for i in range(steps):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        reps.append(step(ev))
+        ev = new_ev()
+        reps.append(job_step(bm, ctx, stream, T, labels, ev))
         events.append(ev)
         with torch.cuda.stream(stream):
             flush.fill_(float(i))
@@ -219,23 +557,25 @@ def time_jobs(bm, torch, ctx, stream, T, steps, warmup, flush, labels):
 
 def precision_forms(bm, torch, dev, X, m, n, k, s, T, seed, steps, warmup, flush,
                     forms=("fp32", "bf16x3")):
-    """Time to SSE of the same job in the FP32 and tensor-core forms."""
-    codes = {"fp32": bm.BM_FP32, "bf16": bm.BM_BF16_RESCORE, "bf16x3": bm.BM_BF16X3_RESCORE,
-             "fp8": bm.BM_FP8_RESCORE}
+    """Time to SSE of the same job in the FP32 and tensor-core forms, with the
+    distance throughput of each."""
     stream = torch.cuda.Stream(device=dev)
     labels = torch.empty(m, dtype=torch.int32, device=dev)
     out = {}
     for form in forms:
-        cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=seed, precision=codes[form])
+        cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=seed, precision=FORM_CODES[form])
         ctx = bm.bm_create(cfg, X, stream.cuda_stream)
         try:
             fit, asg, reps = time_jobs(bm, torch, ctx, stream, T, steps, warmup, flush, labels)
+            mask = np.zeros(k, np.uint8)
+            bm.bm_objective(ctx, None, mask)
         finally:
             bm.bm_destroy(ctx)
         rep, sse = reps[-1]
-        out[form] = {"time_to_sse_ms": float(np.mean(np.add(fit, asg))),
-                     "fit_ms": float(np.mean(fit)), "assign_ms": float(np.mean(asg)),
-                     "sse": sse, "f_opt": rep["f_opt"]}
+        ms = float(np.mean(np.add(fit, asg)))
+        out[form] = {"time_to_sse_ms": ms, "fit_ms": float(np.mean(fit)),
+                     "assign_ms": float(np.mean(asg)), "sse": sse,
+                     "tflops": 2.0 * n * (rep["n_d"] + m * int(mask.sum())) / (ms / 1e3) / 1e12}
     base = out["fp32"]
     for form, r in out.items():
         r["sse_rel_diff_vs_fp32"] = abs(r["sse"] - base["sse"]) / base["sse"]
@@ -243,16 +583,16 @@ def precision_forms(bm, torch, dev, X, m, n, k, s, T, seed, steps, warmup, flush
     return out
 
 
-def traced_phases(bm, torch, Xd, cfg, stream, T):
-    """Device time per chunk phase of one extra job run with tracing on (the
-    timed steps run without it: the timer reads sit on the barrier path)."""
+def traced_phases(bm, Xd, cfg, stream, T):
+    """Device time (ms) per chunk phase of one extra job run with tracing on
+    (the timed steps run without it: the timer reads sit on the barrier path)."""
     tcfg = bm.bm_config_default(**{f: getattr(cfg, f) for f, _ in cfg._fields_})
     tcfg.trace = 1
     ctx = bm.bm_create(tcfg, Xd, stream.cuda_stream)
     try:
         bm.bm_reset(ctx)
         bm.bm_fit_chunk(ctx, T)
-        return bm.bm_trace(ctx)
+        return {p: round(v, 4) for p, v in bm.bm_trace(ctx).items()}
     finally:
         bm.bm_destroy(ctx)
 
@@ -460,18 +800,14 @@ def serving(bm, torch, dev, spec=SERVING):
         sel = [r["latency_s"] * 1e3 for j, r in enumerate(results)
                if r is not None and r["status"] == 0 and precs[j] == code]
         by_prec[name] = {"jobs": len(sel), "p50_ms": pct(sel, 50), "p99_ms": pct(sel, 99)}
-    by_n = {}
+    run_ms_by_n = {}
     for nv in spec["n_set"]:
-        for name, code in (("fp32", bm.BM_FP32), ("bf16x3", bm.BM_BF16X3_RESCORE)):
-            sel = [(r["run_s"] * 1e3, ms[j]) for j, r in enumerate(results)
-                   if r is not None and r["status"] == 0 and ns[j] == nv and precs[j] == code]
-            if sel:
-                by_n["n%d_%s" % (nv, name)] = {
-                    "jobs": len(sel), "run_ms_mean": float(np.mean([a for a, _ in sel])),
-                    "run_ms_max": float(np.max([a for a, _ in sel])),
-                    "mean_m": float(np.mean([b for _, b in sel]))}
+        sel = [r["run_s"] * 1e3 for j, r in enumerate(results)
+               if r is not None and r["status"] == 0 and ns[j] == nv]
+        if sel:
+            run_ms_by_n["n%d" % nv] = round(float(np.mean(sel)), 2)
     return {"workload": "poisson_%d_per_s_%d_jobs_mixed_shapes" % (spec["rate"], R),
-            "run_by_shape": by_n,
+            "run_ms_mean_by_n": run_ms_by_n,
             "requests": R, "offered_rps": spec["rate"],
             "submitted_rps": R / max(submit_t[-1], 1e-9), "completed": len(ok),
             "failed": len(done) - len(ok), "wall_s": wall, "jobs_per_s": len(ok) / wall,
@@ -481,187 +817,10 @@ def serving(bm, torch, dev, spec=SERVING):
             "queue_ms": {"p50": pct(que, 50), "p99": pct(que, 99)},
             "by_precision": by_prec, "failures": failures,
             "workers": spec["workers"], "chunks": spec["chunks"],
-            "server": stats,
+            "server_rejected": {"busy": stats["rejected_busy"], "memory": stats["rejected_memory"]},
             "data": "one seeded 100-component isotropic mixture per n, synthesized on "
                     "the device before the clock starts; job j reads m rows from a "
                     "seeded offset"}
-
-
-def run_ours(args, wl):
-    import torch
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local if world > 1 else 0)
-    torch.cuda.set_device(dev)
-    import paper_2204_07485_gb300 as bm
-
-    m, n, k, s, T = wl["m"], wl["n"], wl["k"], wl["s"], args.chunks
-    seed = wl["seed"] + 1000 * rank          # independent replica per rank
-    X = make_data(wl)
-    Xd = torch.from_numpy(X).to(dev)
-    stream = torch.cuda.Stream(device=dev)
-    cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=seed)
-    ctx = bm.bm_create(cfg, Xd, stream.cuda_stream)
-    labels = torch.empty(m, dtype=torch.int32, device=dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    def step(ev):
-        bm.bm_reset(ctx)
-        ev[0].record(stream)
-        rep = bm.bm_fit_chunk(ctx, T)
-        ev[1].record(stream)
-        sse = bm.bm_assign(ctx, labels)
-        ev[2].record(stream)
-        return rep, sse
-
-    for _ in range(args.warmup):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        step(ev)
-    with torch.cuda.stream(stream):
-        flush.fill_(1.0)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
-    events, reps = [], []
-    with ClockSampler(local if world > 1 else 0) as clocks:
-        t_wall = time.perf_counter()
-        for i in range(args.steps):
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            reps.append(step(ev))
-            events.append(ev)
-            with torch.cuda.stream(stream):      # flush L2 between steps
-                flush.fill_(float(i))
-        torch.cuda.synchronize(dev)
-        t_wall = time.perf_counter() - t_wall
-    fit_ms = [e[0].elapsed_time(e[1]) for e in events]
-    asg_ms = [e[1].elapsed_time(e[2]) for e in events]
-    step_ms = [a + b for a, b in zip(fit_ms, asg_ms)]
-    rep, sse = reps[-1]
-    phases = traced_phases(bm, torch, Xd, cfg, stream, T)
-    C = np.zeros((k, n), np.float32)
-    mask = np.zeros(k, np.uint8)
-    f_opt = bm.bm_objective(ctx, C, mask)
-    nlive = int(mask.sum())
-    nd_fit = rep["n_d"]                      # Lloyd + K-means++ of the step
-    nd_step = nd_fit + m * nlive             # + final assignment
-    flops_step = 2.0 * n * nd_step
-    my_ms = float(np.sum(step_ms))
-    if world > 1:
-        t = torch.tensor([my_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    else:
-        total_ms = my_ms
-    value = world * args.steps * flops_step / (total_ms / 1e3) / 1e12
-
-    # roofline of the dominant kernel (largest share of the step)
-    fit_per_step = float(np.mean(fit_ms))
-    asg_per_step = float(np.mean(asg_ms))
-    hbm_peak, peak_src = peaks()
-    chunk_kernel = {
-        "kernel": "chunk_kernel (draw+gather+K-means++ + Lloyd + keep-best)",
-        "bound": "alu", "achieved": 2.0 * n * nd_fit / (fit_per_step / 1e3) / 1e12,
-        "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "launch_ms": fit_per_step / T, "share": fit_per_step / (fit_per_step + asg_per_step)}
-    chunk_kernel["frac"] = chunk_kernel["achieved"] / chunk_kernel["peak"]
-    abytes = m * n * 4 + m * 4
-    assign_kernel = {
-        "kernel": "assign_np_kernel<28> (final assignment + FP64 SSE)", "bound": "hbm",
-        "achieved": abytes / (asg_per_step / 1e3) / 1e9, "peak": hbm_peak,
-        "unit": "GB/s", "launch_ms": asg_per_step,
-        "share": asg_per_step / (fit_per_step + asg_per_step), "algorithmic_bytes": abytes}
-    assign_kernel["frac"] = assign_kernel["achieved"] / assign_kernel["peak"]
-    dom = chunk_kernel if chunk_kernel["share"] >= assign_kernel["share"] else assign_kernel
-    # DRAM bytes per chunk launch from ncu (dram__bytes_read + write of one
-    # typical chunk, profiles/chunk_kernel_np28_hepmass_like.md)
-    traffic = CHUNK_NP28_DRAM_BYTES if dom is chunk_kernel else None
-    roofline = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
-                "unit": dom["unit"], "frac": dom["frac"], "traffic": traffic,
-                "kernel": dom["kernel"],
-                "peak_source": ("derived FP32 FMA peak (152 SMs x 128 lanes x 2 x 2.07 GHz)"
-                                if dom["bound"] == "alu" else peak_src)}
-
-    # end to end through the host-memory entry point (pinned X in, labels out)
-    Xh = torch.from_numpy(X).pin_memory()
-    lab_h = torch.empty(m, dtype=torch.int32).pin_memory()
-    Ch = np.zeros((k, n), np.float32)
-    mh = np.zeros(k, np.uint8)
-    e2e_times = []
-    for i in range(max(1, min(args.steps, 3))):
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        sse_h, rep_h = bm.bm_fit_host(cfg, Xh.data_ptr(), T, Ch, mh, lab_h.data_ptr())
-        e2e_times.append(time.perf_counter() - t0)
-    e2e_val = flops_step / float(np.median(e2e_times)) / 1e12
-    e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": m * n * 4,
-           "host_gather_ctas": rep_h["host_gathers"],
-           "sse_equals_device_path": bool(sse_h == sse),
-           "d2h_bytes_per_step": m * 4 + k * n * 4 + k,
-           "ms_per_step": float(np.median(e2e_times)) * 1e3}
-
-    out = None
-    if rank == 0:
-        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-               "steps": args.steps, "warmup": args.warmup,
-               "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-               "data": "synthetic",
-               "config": {"workload": wl["name"], "m": m, "n": n, "k": k, "s": s,
-                          "chunks": T, "seed": wl["seed"], "precision": "fp32",
-                          "l2": "256 MB buffer written between steps (X is 112 MB)",
-                          "parallelism": "replicas (independent job per GPU)"},
-               "time_to_sse_ms": total_ms / args.steps,
-               "sse": sse, "f_opt": f_opt, "live": nlive,
-               "lloyd_iters_per_step": rep["lloyd_iters"],
-               "accepted_per_step": rep["accepted"], "n_d_per_step": nd_step,
-               "fit_ms_per_step": fit_per_step, "assign_ms_per_step": asg_per_step,
-               "chunk_phase_ms_per_step": phases,
-               "wall_s": t_wall,
-               "gpu_launches": args.steps * (T + (T + 63) // 64 + 1),
-               "roofline": roofline,
-               "kernels": {"chunk": chunk_kernel, "assign": assign_kernel},
-               "clocks": clocks.summary(),
-               "e2e": e2e}
-    bm.bm_destroy(ctx)
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
-    if rank == 0 and not args.no_precision:
-        # same job, tensor-core form; and the m = 1e7, n = 128 workload
-        pw = min(args.steps, 3)
-        out["precision_forms"] = {
-            wl["name"]: precision_forms(bm, torch, dev, Xd, m, n, k, s, T, seed, pw, 1, flush)}
-        del Xd
-        torch.cuda.empty_cache()
-        import bminputs
-        big = C3_WORKLOAD
-        Xg = bminputs.mixtures.gas_sensor_like_device(big["seed"], m=big["m"], n=big["n"],
-                                                       device=dev)
-        out["precision_forms"][big["name"]] = precision_forms(
-            bm, torch, dev, Xg, big["m"], big["n"], big["k"], big["s"], big["chunks"],
-            big["seed"], pw, 1, flush)
-        del Xg
-        torch.cuda.empty_cache()
-        v8 = C3_FP8_WORKLOAD
-        Xs = bminputs.mixtures.scaled_384_device(v8["seed"], m=v8["m"], device=dev)
-        out["precision_forms"][v8["name"]] = precision_forms(
-            bm, torch, dev, Xs, v8["m"], v8["n"], v8["k"], v8["s"], v8["chunks"], v8["seed"],
-            pw, 1, flush, forms=("fp32", "bf16x3", "fp8"))
-        del Xs
-    if rank == 0 and not args.no_precision:
-        out["launch_latency"] = launch_latency(bm, torch, dev)
-    if rank == 0 and not args.no_grouped:
-        out["grouped"] = grouped(bm, torch, dev)
-    if rank == 0 and not args.no_serving:
-        out["serving"] = serving(bm, torch, dev)
-    if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(X, wl, CPU_SAMPLE_CHUNKS)
-    if rank == 0:
-        print(json.dumps(out))
-    return 0
 
 
 PROFILE_CASES = {
@@ -731,7 +890,7 @@ def main():
     args = parse()
     if args.profile:
         return profile_case(args.profile)
-    wl = dict(WORKLOAD)
+    wl = dict(C3_WORKLOAD)
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_ours(args, wl)
