@@ -6,8 +6,8 @@ touches it.
 """
 from .bigmeans import (big_means_workers, forgy_reseed, sq_distances, nearest, objective, kmeanspp_reseed,
                        lloyd, big_means, big_means_chunk, final_assignment,
-                       BigMeansState, KppPick, LloydResult, ChunkRecord)
+                       BigMeansState, KppPick, LloydResult, ChunkRecord, Decisions)
 
 __all__ = ["big_means_workers", "forgy_reseed", "sq_distances", "nearest", "objective", "kmeanspp_reseed", "lloyd",
            "big_means", "big_means_chunk", "final_assignment",
-           "BigMeansState", "KppPick", "LloydResult", "ChunkRecord"]
+           "BigMeansState", "KppPick", "LloydResult", "ChunkRecord", "Decisions"]

@@ -45,6 +45,16 @@ design notes):
       ties, and a shared incumbent changes only when strictly improved (as
       R2).  The paper gives no round structure for mode 3; rounds are
       synchronous here.
+  R17 Decision following (parity, not the method): a decision whose two
+      outcomes are both correct up to FP32 rounding -- an argmin whose top
+      two distances differ by less than 1e-5 relative, a stop test or
+      keep-the-best comparison within 1e-6 relative of its threshold, a
+      K-means++ target within 5e-8 * sum(D^2) of a prefix boundary, or two
+      candidate potentials within 1e-6 relative -- is "exempt".  With a
+      ``Decisions`` object the run reports every exempt decision it meets
+      and takes the other outcome of those named in its ``flips``; the
+      arithmetic of every step is unchanged.  A test chooses the flips that
+      reproduce the GPU's observed outcome and reports how many it needed.
   R16 The alternative empty-cluster rule ("keep"; the paper names the
       handling of empty clusters as an interchangeable ingredient without
       fixing one): a centroid that loses all members keeps its position and
@@ -55,6 +65,28 @@ import math
 
 import numpy as np
 from scipy.spatial.distance import cdist
+
+# Exemption bands of R17.
+TIE_REL = 1e-5          # argmin: (d2 - d1) < TIE_REL * d2
+SCALAR_REL = 1e-6       # stop test, keep-the-best, candidate potentials
+KPP_BAND = 5e-8         # K-means++ target within KPP_BAND * sum(D^2) of a boundary
+
+
+class Decisions:
+    """Exempt decisions of a run (R17).  ``flips``: keys of the exempt
+    decisions that take their other outcome.  ``met`` lists the key of every
+    exempt decision the run met, in order.  Keys: ("label", t, it, row),
+    ("stop", t, it), ("kpp_target", t, slot, trial), ("kpp_best", t, slot),
+    ("keep", t)."""
+
+    def __init__(self, flips=()):
+        self.flips = set(flips)
+        self.met = []          # (key, relative margin to the decision's threshold)
+
+    def other(self, key, margin):
+        """Records an exempt decision; True if it takes the other outcome."""
+        self.met.append((key, float(margin)))
+        return key in self.flips
 
 
 # ---------------------------------------------------------------- primitives
@@ -123,12 +155,16 @@ def forgy_reseed(P, C, live, u):
     return C, live
 
 
-def kmeanspp_reseed(P, C, live, u_first, u, trials=3, picks=None):
+def kmeanspp_reseed(P, C, live, u_first, u, trials=3, picks=None, decisions=None, t=0):
     """Reinitialise every degenerate centroid of (C, live) on sample P (R7).
 
     P: s x n, C: k x n (rows of degenerate slots are ignored), live: k bools,
     u_first: float, u: k x trials uniforms.  Returns new (C, live) copies.
     ``picks`` (optional list) receives one KppPick per reseeded slot.
+    ``decisions`` (optional, R17) may take the other outcome of an exempt
+    inverse-CDF pick (the neighbouring row with positive D^2 across the
+    boundary the target is near) or of an exempt choice between candidates
+    (the candidate with the next lowest potential); t names the chunk.
     """
     P = np.asarray(P, dtype=np.float64)
     C = np.array(C, dtype=np.float64, copy=True)
@@ -162,11 +198,27 @@ def kmeanspp_reseed(P, C, live, u_first, u, trials=3, picks=None):
                 if cand >= s:                       # rounding: last positive D^2
                     cand = int(np.flatnonzero(D2 > 0)[-1])
                 lo = prefix[cand - 1] if cand > 0 else 0.0
-                margins.append(min(target - lo, prefix[cand] - target) / total)
+                below, above = target - lo, prefix[cand] - target
+                margins.append(min(below, above) / total)
+                if decisions is not None and min(below, above) < KPP_BAND * total:
+                    if decisions.other(("kpp_target", t, j, l), min(below, above) / total):
+                        pos = np.flatnonzero(D2 > 0)
+                        if below <= above:          # the row before the boundary
+                            prev = pos[pos < cand]
+                            cand = int(prev[-1]) if prev.size else cand
+                        else:                       # the row after it
+                            nxt = pos[pos > cand]
+                            cand = int(nxt[0]) if nxt.size else cand
             dc = sq_distances(P, P[cand:cand + 1])[:, 0]
             cands.append(cand)
             pots.append(float(np.minimum(D2, dc).sum()))
         best = int(np.argmin(pots))                 # lowest trial on ties
+        if decisions is not None and trials > 1:
+            order = sorted(range(trials), key=lambda q: (pots[q], q))
+            b0, b1 = order[0], order[1]
+            if pots[b1] - pots[b0] < SCALAR_REL * pots[b0] and cands[b1] != cands[b0]:
+                if decisions.other(("kpp_best", t, j), (pots[b1] - pots[b0]) / pots[b0]):
+                    best = b1
         C[j] = P[cands[best]]
         live[j] = True
         D2 = np.minimum(D2, sq_distances(P, C[j:j + 1])[:, 0])
@@ -189,10 +241,12 @@ class LloydResult:
         self.stop_margin = stop_margin  # min relative distance to the stop threshold
 
 
-def lloyd(P, C, live, tol=1e-4, max_iter=300, empty="degenerate"):
+def lloyd(P, C, live, tol=1e-4, max_iter=300, empty="degenerate", decisions=None, t=0):
     """K-means local search on sample P from centroids C (Sec. 2; R3, R4, R5).
     ``empty`` is what happens to a live centroid without members: it becomes
-    degenerate (R5) or, with "keep", stays where it is and live (R16)."""
+    degenerate (R5) or, with "keep", stays where it is and live (R16).
+    ``decisions`` (optional, R17) may give an exempt row its second-nearest
+    live centroid or reverse an exempt stop test; t names the chunk."""
     if empty not in ("degenerate", "keep"):
         raise ValueError("empty must be 'degenerate' or 'keep'")
     P = np.asarray(P, dtype=np.float64)
@@ -208,16 +262,29 @@ def lloyd(P, C, live, tol=1e-4, max_iter=300, empty="degenerate"):
     while True:
         n_d += P.shape[0] * int(live.sum())
         labels, d1, d2 = nearest(P, C, live)
-        f = float(d1.sum())
-        f_trace.append(f)
         with np.errstate(invalid="ignore", divide="ignore"):
             gaps = np.where(np.isfinite(d2),
                             np.where(d2 > 0, (d2 - d1) / d2, 0.0), np.inf)
         if gaps.size:
             min_gap = min(min_gap, float(np.nanmin(gaps)))
+        if decisions is not None:
+            for r in np.flatnonzero(gaps < TIE_REL):
+                if decisions.other(("label", t, it, int(r)), gaps[r]):
+                    dr = sq_distances(P[r:r + 1], C)[0]
+                    dr[~live] = np.inf
+                    dr[labels[r]] = np.inf
+                    labels[r] = int(np.argmin(dr))
+                    d1[r] = dr[labels[r]]
+        f = float(d1.sum())
+        f_trace.append(f)
+        stop = f == 0.0 or (it > 0 and f_prev - f <= tol * f_prev) or it == max_iter
         if it > 0 and f_prev > 0:
-            stop_margin = min(stop_margin, abs((f_prev - f) - tol * f_prev) / f_prev)
-        if f == 0.0 or (it > 0 and f_prev - f <= tol * f_prev) or it == max_iter:
+            margin = abs((f_prev - f) - tol * f_prev) / f_prev
+            stop_margin = min(stop_margin, margin)
+            if (decisions is not None and margin < SCALAR_REL and f != 0.0
+                    and it != max_iter and decisions.other(("stop", t, it), margin)):
+                stop = not stop
+        if stop:
             break
         for j in range(k):
             if not live[j]:
@@ -268,11 +335,11 @@ class BigMeansState:
 
 
 def big_means_chunk(X, state, idx, u_first, u, tol=1e-4, max_iter=300,
-                    trials=3, t=0, init="kmeans++", empty="degenerate"):
+                    trials=3, t=0, init="kmeans++", empty="degenerate", decisions=None):
     """One pass of Alg. 1's loop body on the sample X[idx]; updates ``state``.
     ``init`` chooses the reinitialisation of degenerate centroids: K-means++
     (the paper's choice, R7) or Forgy (R13); ``empty`` the empty-cluster rule
-    of Lloyd (R5 or R16)."""
+    of Lloyd (R5 or R16); ``decisions`` the exempt decisions of R17."""
     P = np.asarray(X, dtype=np.float32)[np.asarray(idx)].astype(np.float64)
     picks = []
     s = P.shape[0]
@@ -289,11 +356,15 @@ def big_means_chunk(X, state, idx, u_first, u, tol=1e-4, max_iter=300,
     if init == "forgy":
         C1, live1 = forgy_reseed(P, state.C, state.live, u)
     else:
-        C1, live1 = kmeanspp_reseed(P, state.C, state.live, u_first, u, trials, picks)
-    res = lloyd(P, C1, live1, tol, max_iter, empty)
+        C1, live1 = kmeanspp_reseed(P, state.C, state.live, u_first, u, trials, picks,
+                                    decisions, t)
+    res = lloyd(P, C1, live1, tol, max_iter, empty, decisions, t)
     accepted = res.f < state.f_opt
     keep_margin = (abs(res.f - state.f_opt) / state.f_opt
                    if math.isfinite(state.f_opt) and state.f_opt > 0 else math.inf)
+    if (decisions is not None and keep_margin < SCALAR_REL
+            and decisions.other(("keep", t), keep_margin)):
+        accepted = not accepted
     if accepted:
         state.C = res.C
         state.live = res.live
@@ -303,7 +374,7 @@ def big_means_chunk(X, state, idx, u_first, u, tol=1e-4, max_iter=300,
 
 
 def big_means(X, k, draws, tol=1e-4, max_iter=300, trials=3, state=None,
-              t0=0, init="kmeans++", empty="degenerate"):
+              t0=0, init="kmeans++", empty="degenerate", decisions=None):
     """Alg. 1 over the given chunk draws [(idx, u_first, u), ...].
 
     Returns (state, records).  The final assignment is ``final_assignment``.
@@ -315,7 +386,7 @@ def big_means(X, k, draws, tol=1e-4, max_iter=300, trials=3, state=None,
     for q, (idx, u_first, u) in enumerate(draws):
         records.append(big_means_chunk(X, state, idx, u_first, u, tol,
                                        max_iter, trials, t=t0 + q, init=init,
-                                       empty=empty))
+                                       empty=empty, decisions=decisions))
     return state, records
 
 
