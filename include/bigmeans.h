@@ -48,7 +48,10 @@ typedef enum bm_status {
   BM_ETIMEOUT = 4,      /* a bounded device-side wait gave up                 */
   BM_EBUSY = 5,         /* server full / resource in use                      */
   BM_ECANCELLED = 6,    /* job cancelled before completion                   */
-  BM_EUNSUPPORTED = 7   /* shape outside what this build's kernels cover      */
+  BM_EUNSUPPORTED = 7,  /* shape outside what this build's kernels cover      */
+  BM_EGUARD = 8         /* debug builds only (BM_DEBUG_GUARDS): a device index
+                           guard found an access outside its buffer and
+                           skipped it                                        */
 } bm_status;
 
 typedef enum bm_precision {
@@ -158,8 +161,9 @@ bm_status bm_fit_chunk(bm_ctx* ctx, int32_t chunks, bm_fit_report* out);
  * accumulated in float64.  With a tensor-core precision form (BM_BF16_RESCORE,
  * BM_BF16X3_RESCORE, BM_FP8_RESCORE) the distances run on the tensor cores in
  * that arithmetic with exact FP32 rescoring (see bm_assign_rows_prec); the
- * chunks of such a context screen with split BF16 whatever the form.  Blocks
- * until done. */
+ * chunks of a BM_BF16_RESCORE context screen with BF16 products, those of
+ * the other tensor-core forms with split BF16 products (labels and distances
+ * are those of FP32 either way).  Blocks until done. */
 bm_status bm_assign(bm_ctx* ctx, int32_t* labels_dev, double* sse_out);
 
 /* Streaming (stream processing of newly arriving data portions, Sec. 1 and

@@ -12,7 +12,9 @@ import os
 import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libbigmeans.so")
+# BM_LIBRARY names a checking build of the same sources (the tests' index-
+# guard and sanitizer variants); by default the in-tree product library.
+LIB_PATH = os.environ.get("BM_LIBRARY") or os.path.join(_HERE, "libbigmeans.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
@@ -22,7 +24,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 BM_OK, BM_EINVAL, BM_ENOMEM, BM_ECUDA, BM_ETIMEOUT, BM_EBUSY, BM_ECANCELLED, \
-    BM_EUNSUPPORTED = range(8)
+    BM_EUNSUPPORTED, BM_EGUARD = range(9)
 BM_FP32, BM_BF16_RESCORE, BM_FP8_RESCORE, BM_BF16X3_RESCORE = range(4)
 BM_INIT_KMEANSPP, BM_INIT_FORGY = 0, 1
 BM_EMPTY_DEGENERATE, BM_EMPTY_KEEP = 0, 1

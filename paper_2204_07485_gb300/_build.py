@@ -30,8 +30,31 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _compile(src, extra):
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+# Build variants: the product library, and two checking builds of the same
+# sources that the tests load in child processes (never the product path):
+#   guards: device index guards compiled in (BM_DEBUG_GUARDS; an access outside
+#           its buffer is skipped and reported as BM_EGUARD);
+#   asan:   host code instrumented with AddressSanitizer and
+#           UndefinedBehaviorSanitizer (the process must preload their
+#           runtimes).
+VARIANTS = {
+    "release": ([], [], "libbigmeans.so"),
+    "guards": (["-DBM_DEBUG_GUARDS"], [], "libbigmeans_guards.so"),
+    # (nvcc splits -Xcompiler values at commas: one flag per option)
+    "asan": (["-Xcompiler", "-fsanitize=address", "-Xcompiler", "-fsanitize=undefined",
+              "-Xcompiler", "-fno-omit-frame-pointer", "-Xcompiler", "-fno-sanitize=vptr"],
+             ["-lasan", "-lubsan"], "libbigmeans_asan.so"),
+}
+
+
+def variant_path(variant):
+    """Where build(variant=...) puts that variant's library."""
+    name = VARIANTS[variant][2]
+    return LIB if variant == "release" else os.path.join(BUILD, variant, name)
+
+
+def _compile(src, extra, outdir):
+    obj = os.path.join(outdir, os.path.basename(src)[:-3] + ".o")
     cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -39,25 +62,29 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
-def build(verbose=False, ptxas_info=False):
-    """Compile every .cu under csrc/ and link libbigmeans.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+def build(verbose=False, ptxas_info=False, variant="release"):
+    """Compile every .cu under csrc/ and link the variant's library (the
+    in-tree libbigmeans.so for "release"); returns its path."""
+    cflags, libs, _ = VARIANTS[variant]
+    outdir = BUILD if variant == "release" else os.path.join(BUILD, variant)
+    os.makedirs(outdir, exist_ok=True)
+    extra = list(cflags) + (["-Xptxas", "-v"] if ptxas_info else [])
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        results = list(ex.map(lambda s: _compile(s, extra), srcs))
+        results = list(ex.map(lambda s: _compile(s, extra, outdir), srcs))
     objs = [o for o, _ in results]
     if verbose or ptxas_info:
         for _, err in results:
             if err:
                 sys.stderr.write(err)
-    tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    lib = variant_path(variant)
+    tmp = lib + ".tmp"
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", *libs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s" % r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

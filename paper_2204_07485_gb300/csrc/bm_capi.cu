@@ -35,6 +35,7 @@ struct Plan {
   int agrid = 0;     // CTAs of the FP32 assign kernel (0: tensor cores only)
   size_t asmem = 0;
   int tc_kb = 0, tc_n16 = 0, tc_ncols = 0, tc_fb = 0, tc_ns = 0, tc_tpc = 0;
+  int tc_planes = 2; // BF16 planes of the chunk kernel's screening (1 or 2)
   int cap = 0;       // CTA cap of the job (bm_config.max_ctas), 0 = none
 };
 
@@ -49,10 +50,11 @@ static int sm_count() {
 
 // Tensor-core chunk plan: one CTA per SM (TMEM, grid barrier), at least one
 // 128-row tile per CTA, the widest staged feature block that fits.
-static bm_status make_plan_tc(int n, int k, long long s, Plan* out, int cap) {
+static bm_status make_plan_tc(int n, int k, long long s, Plan* out, int cap, int planes) {
   if (k > kMaxK || n > 512) return BM_EUNSUPPORTED;
   Plan p;
   p.tc = true;
+  p.tc_planes = planes;
   p.generic = true;
   p.npad = align_up(n, 4);
   p.kpad = align_up(k, 32);
@@ -73,7 +75,7 @@ static bm_status make_plan_tc(int n, int k, long long s, Plan* out, int cap) {
     // widest staged block first, then a three-slot ring if it still fits
     for (int f : {64, 32, 16, 8, 4}) {
       for (int r : {3, 2}) {
-        smem = chunk_tc_smem(p.npad, k, R, p.tc_n16, f, r);
+        smem = chunk_tc_smem(p.npad, k, R, p.tc_n16, f, r, planes);
         if (smem + 2048 <= kSmemLimit) { fb = f; ns = r; break; }   // + static smem
       }
       if (fb) break;
@@ -105,13 +107,15 @@ static bm_status make_plan_simt(int n, int k, long long s, Plan* out, int cap);
 
 // Kernel family for (n, k, s): the row-in-register path for n <= 32; for
 // wider rows the tensor-core path when asked for (tc) or when the FP32
-// tables do not fit in shared memory, else the tiled FP32 path.
+// tables do not fit in shared memory, else the tiled FP32 path.  planes: the
+// tensor-core path's screening arithmetic (1: BF16, 2: split BF16).
 // cap > 0 limits the CTAs of a chunk launch (the job then leaves the other
 // SMs to concurrent jobs); it gives way where shared memory needs more CTAs.
-static bm_status make_plan(int n, int k, long long s, Plan* out, bool tc = false, int cap = 0) {
-  if (n > kNpMax && tc) return make_plan_tc(n, k, s, out, cap);
+static bm_status make_plan(int n, int k, long long s, Plan* out, bool tc = false, int cap = 0,
+                           int planes = 2) {
+  if (n > kNpMax && tc) return make_plan_tc(n, k, s, out, cap, planes);
   const bm_status st = make_plan_simt(n, k, s, out, cap);
-  if (st == BM_EUNSUPPORTED && n > kNpMax) return make_plan_tc(n, k, s, out, cap);
+  if (st == BM_EUNSUPPORTED && n > kNpMax) return make_plan_tc(n, k, s, out, cap, planes);
   return st;
 }
 
@@ -169,7 +173,7 @@ static bm_status make_plan_simt(int n, int k, long long s, Plan* out, int cap) {
 // ------------------------------------------------------------ workspace
 struct Workspace {
   int32_t* idx = nullptr;       // sample plan: [plan_cap][s] sorted rows
-  uint32_t* bitmap = nullptr;   // [plan_cap][ceil(m / 32)], zero between draws
+  uint32_t* bitmap = nullptr;   // [plan_cap][draw_bitmap_words(m)], zero between draws
   int plan_cap = 1;             // chunks drawn per sample-plan launch
   float* P = nullptr;
   float* C = nullptr;
@@ -224,7 +228,7 @@ struct Workspace {
 
 // Chunks per sample-plan launch: up to 64, within 256 MB of plan memory.
 static int plan_capacity(long long m, long long s) {
-  const long long per = ((m + 31) / 32) * 4 + s * 4;
+  const long long per = (long long)draw_bitmap_words(m) * 4 + s * 4;
   long long cap = (256LL << 20) / std::max<long long>(per, 1);
   return (int)std::max<long long>(1, std::min<long long>(64, cap));
 }
@@ -232,7 +236,7 @@ static int plan_capacity(long long m, long long s) {
 static bm_status ws_create(Workspace* w, long long m, int k, long long s,
                            const Plan& p, cudaStream_t st, int plan_cap = 1,
                            long long assign_rows = 0) {
-  const size_t words = (size_t)((m + 31) / 32);
+  const size_t words = draw_bitmap_words(m);
   const int G = p.grid;
   w->plan_cap = plan_cap;
   cudaError_t e = cudaSuccess;
@@ -262,7 +266,7 @@ static bm_status ws_create(Workspace* w, long long m, int k, long long s,
   if (p.tc) {
     BM_TRY(w->alloc(&w->Cb, cb_bytes));
     BM_TRY(w->alloc(&w->sqs, (size_t)k * ((p.npad + 7) / 8)));
-    BM_TRY(w->alloc(&w->Pb, (size_t)p.grid * p.tc_tpc * p.tc_kb * 32768));
+    BM_TRY(w->alloc(&w->Pb, (size_t)p.grid * p.tc_tpc * p.tc_kb * p.tc_planes * 16384));
   }
 #undef BM_TRY
   if (w->dry) return BM_OK;
@@ -293,7 +297,7 @@ static ChunkArgs chunk_args(const Workspace& w, const Plan& p, const float* X,
   a.part_sum = w.part_sum; a.part_cnt = w.part_cnt; a.part_f = w.part_f;
   a.blk_cnt = w.blk_cnt; a.ctl = w.ctl; a.stats = w.stats; a.kx = w.kx;
   a.tc_kb = p.tc_kb; a.tc_n16 = p.tc_n16; a.tc_ncols = p.tc_ncols; a.tc_fb = p.tc_fb;
-  a.tc_tpc = p.tc_tpc; a.tc_ns = p.tc_ns;
+  a.tc_tpc = p.tc_tpc; a.tc_ns = p.tc_ns; a.tc_planes = p.tc_planes;
   a.Cb = w.Cb; a.sqs = w.sqs; a.Pb = w.Pb;
   return a;
 }
@@ -402,8 +406,12 @@ static bool wants_tc(const bm_config* cfg) {
          cfg->precision == BM_FP8_RESCORE;
 }
 
+// BF16 planes of the tensor-core chunk kernel's screening for a precision
+// form: one for BF16, two (split BF16) for the others, E4M3 included.
+static int chunk_planes(int precision) { return precision == BM_BF16_RESCORE ? 1 : 2; }
+
 // Screening arithmetic of the tensor-core final assignment for a precision
-// form (the chunk kernels' tensor-core path always screens with split BF16).
+// form.
 static int assign_terms(int precision) {
   return precision == BM_BF16_RESCORE ? 1 : precision == BM_FP8_RESCORE ? kTermsFp8 : 3;
 }
@@ -419,7 +427,8 @@ bm_status ctx_create(const bm_config* cfg, const float* X_dev, cudaStream_t stre
   c->cfg = *cfg;
   c->X = X_dev;
   c->stream = stream;
-  st = make_plan(cfg->n, cfg->k, cfg->s, &c->plan, wants_tc(cfg), cfg->max_ctas);
+  st = make_plan(cfg->n, cfg->k, cfg->s, &c->plan, wants_tc(cfg), cfg->max_ctas,
+                 chunk_planes(cfg->precision));
   if (st != BM_OK) { delete c; return st; }
   c->ws.pool = pool;
   c->ws.pool_stream = stream;
@@ -436,7 +445,8 @@ bm_status ctx_footprint(const bm_config* cfg, size_t* bytes) {
   bm_status st = check_config(cfg);
   if (st != BM_OK) return st;
   Plan p;
-  st = make_plan(cfg->n, cfg->k, cfg->s, &p, wants_tc(cfg), cfg->max_ctas);
+  st = make_plan(cfg->n, cfg->k, cfg->s, &p, wants_tc(cfg), cfg->max_ctas,
+                 chunk_planes(cfg->precision));
   if (st != BM_OK) return st;
   Workspace w;
   w.dry = true;
@@ -478,6 +488,7 @@ const char* bm_status_string(int32_t s) {
     case BM_EBUSY: return "busy";
     case BM_ECANCELLED: return "cancelled";
     case BM_EUNSUPPORTED: return "unsupported shape";
+    case BM_EGUARD: return "device index guard tripped (debug build)";
     default: return "unknown status";
   }
 }
@@ -508,7 +519,7 @@ bm_status bm_reset(bm_ctx* c) {
   cudaMemsetAsync(c->ws.mask_inc, 0, k, st);
   cudaMemsetAsync(c->ws.ctl, 0, sizeof(Ctl), st);
   cudaMemsetAsync(c->ws.stats, 0, sizeof(Stats), st);
-  const size_t words = (size_t)((c->cfg.m + 31) / 32);
+  const size_t words = draw_bitmap_words(c->cfg.m);
   cudaMemsetAsync(c->ws.bitmap, 0, words * 4 * c->ws.plan_cap, st);
   c->plan_t0 = -1;
   static const double inf = std::numeric_limits<double>::infinity();
@@ -528,7 +539,7 @@ static bm_status queue_chunks(bm_ctx* c, ChunkArgs a, long long chunks, long lon
     if (c->plan_t0 < 0 || c->t < c->plan_t0 || c->t >= c->plan_t0 + c->plan_n) {
       DrawArgs d{};
       d.m = c->cfg.m; d.s = (int)c->cfg.s; d.seed = c->cfg.seed; d.t0 = c->t;
-      d.idx = c->ws.idx; d.bitmaps = c->ws.bitmap;
+      d.idx = c->ws.idx; d.bitmaps = c->ws.bitmap; d.status = &c->ws.ctl->status;
       int batch = c->ws.plan_cap;
       if (left >= 0) batch = (int)std::min<long long>(batch, left - done);
       if (launch_draw(d, batch, c->stream) != cudaSuccess) return BM_ECUDA;
@@ -623,14 +634,25 @@ bm_status bm_fit_chunk(bm_ctx* c, int32_t chunks, bm_fit_report* out) {
       st = queue_chunks(c, a, chunks, chunks);
     }
   } else {
-    // the paper's time budget: one chunk at a time, checked between chunks
-    while (st == BM_OK) {
+    // the paper's time budget (Sec. 5): chunks until the budget has elapsed.
+    // One chunk stays queued ahead of the one the host waits for, so the GPU
+    // never idles while the host reads the clock; the chunk queued when the
+    // budget runs out still completes.
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess)
+      st = BM_ECUDA;
+    for (long long q = 0; st == BM_OK; ++q) {
       st = queue_chunks(c, a, 1, -1);
       if (st != BM_OK) break;
-      if (cudaStreamSynchronize(c->stream) != cudaSuccess) { st = BM_ECUDA; break; }
+      if (cudaEventRecord(ev[q & 1], c->stream) != cudaSuccess) { st = BM_ECUDA; break; }
+      if (q == 0) continue;   // two chunks in flight before the first wait
+      if (cudaEventSynchronize(ev[(q - 1) & 1]) != cudaSuccess) { st = BM_ECUDA; break; }
       const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       if (el >= c->cfg.time_budget_s) break;
     }
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
   }
   const bm_status st2 = check_status(c->ws, c->stream, c->cfg.m);
   if (st == BM_OK) st = st2;
@@ -660,6 +682,7 @@ static bm_status assign_impl(const float* X, long long m, int n, int k,
   a.X = X; a.m = m; a.n = n; a.npad = p.npad; a.k = k; a.kpad = p.kpad;
   a.C = C; a.cstride = cstride; a.mask = mask; a.labels = labels; a.dmin = dmin;
   a.part = w.apart; a.sse = w.asse; a.ticket = &w.ctl->assign_ticket;
+  a.status = &w.ctl->status;
   const long long rows_per = p.generic ? 64 : 256;  // rows per CTA pass
   int grid = (int)std::max<long long>(1, std::min<long long>(p.agrid, (m + rows_per - 1) / rows_per));
   if (p.cap > 0) grid = std::min(grid, p.cap * std::max(1, p.agrid / std::max(1, sm_count())));
@@ -668,6 +691,10 @@ static bm_status assign_impl(const float* X, long long m, int n, int k,
   if (cudaMemcpyAsync(&sse, w.asse, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return BM_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return BM_ECUDA;
+#ifdef BM_DEBUG_GUARDS
+  const bm_status gs = check_status(w, st, m);   // an index guard that tripped
+  if (gs != BM_OK) return gs;
+#endif
   if (sse_out) *sse_out = sse;
   return BM_OK;
 }
@@ -1305,7 +1332,7 @@ bm_status bm_draw_chunk(int64_t m, int64_t s, uint64_t seed, int64_t t,
   std::lock_guard<std::mutex> g(g_ops_mu);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint32_t* bitmap = nullptr;
-  const size_t words = (size_t)((m + 31) / 32);
+  const size_t words = draw_bitmap_words(m);
   if (cudaMalloc(&bitmap, words * 4) != cudaSuccess) return BM_ENOMEM;
   bm_status rc = BM_OK;
   if (cudaMemsetAsync(bitmap, 0, words * 4, st) != cudaSuccess) rc = BM_ECUDA;

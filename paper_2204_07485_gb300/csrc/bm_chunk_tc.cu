@@ -54,14 +54,14 @@ struct TccLayout {
 };
 
 // Shared-memory layout.  The region at offset 0 holds either the ns-slot
-// MMA ring (A block: 128 rows x 64 BF16 x 2 planes; B block: n16 rows x 64
-// BF16 x 2 planes) or the staged feature block of the exact passes (R rows
+// MMA ring (A block: 128 rows x 64 BF16 x `planes` planes; B block: n16 rows
+// x 64 BF16 x `planes` planes) or the staged feature block of the exact passes (R rows
 // and k centroid rows of fb floats, row stride fb + 4).
 __host__ __device__ inline TccLayout tcc_layout(int npad, int k, int R, int n16, int fb,
-                                                int ns) {
+                                                int ns, int planes) {
   TccLayout L;
-  L.ring_a = 2 * kTccM * 128;
-  L.ring_b = 2 * n16 * 128;
+  L.ring_a = planes * kTccM * 128;
+  L.ring_b = planes * n16 * 128;
   L.ring_slot = L.ring_a + L.ring_b;
   L.sstride = fb + 4;
   L.stage_c = align_up(R * L.sstride * 4, 16);
@@ -188,29 +188,33 @@ __device__ void load_norms(const ChunkArgs& a, const TccS& S, TccBound* bd) {
   __syncthreads();
   float mx = 0.f;
   for (int i = 0; i < kTccWarps; ++i) mx = fmaxf(mx, (float)S.red[i]);
-  // split BF16 products: the dropped lo*lo term and the second roundings,
-  // plus FP32 accumulation over n products
-  const float eps = 3.1f * 0x1.0p-16f + (float)(3 * a.n + 16) * 0x1.0p-22f;
+  // one BF16 rounding per operand, or for split BF16 products the dropped
+  // lo*lo term and the second roundings; plus FP32 accumulation over n
+  // products
+  const float eps = a.tc_planes == 1 ? 1.01f * 0x1.0p-7f + (float)(a.n + 16) * 0x1.0p-22f
+                                     : 3.1f * 0x1.0p-16f + (float)(3 * a.n + 16) * 0x1.0p-22f;
   bd->b0 = 2.f * eps * sqrtf(mx) * 1.0001f;
   bd->b1 = (float)(a.n + 2) * 0x1.0p-22f * mx;
   __syncthreads();
 }
 
 // ---------------------------------------------------------------- planes
-// Own rows -> split BF16 (hi, lo) tiles in global memory, once per chunk (P
-// does not change across Lloyd iterations): tile t, K block kb of this CTA is
-// one contiguous 32 KB block (hi plane, then lo plane) in the 128-byte-
-// swizzled K-major layout of the MMA; ||x||^2 of every own row -> S.xx.
+// Own rows -> BF16 tiles in global memory, once per chunk (P does not
+// change across Lloyd iterations): tile t, K block kb of this CTA is one
+// contiguous block of 16 KB per plane (the hi plane, then for split BF16 the
+// lo plane) in the 128-byte-swizzled K-major layout of the MMA; ||x||^2 of
+// every own row -> S.xx.
 __device__ void tcc_convert_own(const ChunkArgs& a, const TccS& S, int r0, int nrows) {
   const int tid = threadIdx.x, kb = a.tc_kb, npad = a.npad;
+  const int blk = a.tc_planes * kTccM * 128;
   for (int i = tid; i < nrows; i += blockDim.x) S.xx[i] = 0.f;
   __syncthreads();
-  unsigned char* base = a.Pb + (size_t)blockIdx.x * a.tc_tpc * kb * 32768;
+  unsigned char* base = a.Pb + (size_t)blockIdx.x * a.tc_tpc * kb * blk;
   for (int t0 = 0; t0 < nrows; t0 += kTccM) {
     const int rows = min(kTccM, nrows - t0);
     const float* src = a.P + (size_t)(r0 + t0) * npad;
     for (int b = 0; b < kb; ++b) {
-      unsigned char* dst = base + (size_t)((t0 / kTccM) * kb + b) * 32768;
+      unsigned char* dst = base + (size_t)((t0 / kTccM) * kb + b) * blk;
       // 8 threads per row, one 8-feature chunk each
       float v[4][8];
 #pragma unroll
@@ -248,7 +252,8 @@ __device__ void tcc_convert_own(const ChunkArgs& a, const TccS& S, int r0, int n
         }
         const int off = sw128_offset(r, ch * 8);
         *reinterpret_cast<uint4*>(dst + off) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4*>(dst + kTccM * 128 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        if (a.tc_planes == 2)
+          *reinterpret_cast<uint4*>(dst + kTccM * 128 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         // the 8 threads of a row are consecutive lanes
         nq += __shfl_xor_sync(0xffffffffu, nq, 1);
         nq += __shfl_xor_sync(0xffffffffu, nq, 2);
@@ -275,7 +280,9 @@ __device__ bool tcc_pass_a(const ChunkArgs& a, const TccS& S, int r0, int nrows,
   const int kb = a.tc_kb, N = a.tc_n16, ns = S.ns;
   const uint32_t idesc = idesc_bf16_f32(kTccM, N);
   const float e_d = (float)(a.n + 4) * 0x1.0p-22f;
-  const uint32_t abytes = 2 * kTccM * 128, bbytes = 2 * N * 128;
+  const int planes = a.tc_planes;
+  const uint32_t abytes = planes * kTccM * 128, bbytes = planes * N * 128;
+  const size_t cb_stride = 2 * (size_t)N * 128;   // the global centroid planes keep both
   const unsigned char* pbase = a.Pb + (size_t)blockIdx.x * a.tc_tpc * kb * abytes;
   const int ntl = (nrows + kTccM - 1) / kTccM;
   const uint32_t first = pp.ring, total = (uint32_t)(ntl * kb);
@@ -296,7 +303,7 @@ __device__ bool tcc_pass_a(const ChunkArgs& a, const TccS& S, int r0, int nrows,
           unsigned char* sa = S.ring + sl * S.ring_slot;
           mbar_expect_tx(S.bfull + sl, abytes + bbytes);
           bulk_g2s(sa, pbase + (size_t)(tt * kb + b) * abytes, abytes, S.bfull + sl);
-          bulk_g2s(sa + S.ring_a, a.Cb + (size_t)b * bbytes, bbytes, S.bfull + sl);
+          bulk_g2s(sa + S.ring_a, a.Cb + (size_t)b * cb_stride, bbytes, S.bfull + sl);
         }
         __syncwarp();
       }
@@ -315,8 +322,10 @@ __device__ bool tcc_pass_a(const ChunkArgs& a, const TccS& S, int r0, int nrows,
         for (int ks = 0; ks < 4; ++ks) {
           const uint64_t off = (uint64_t)((ks * 32) >> 4);
           tc_mma_bf16(tmem, da + off, db + off, idesc, (b > 0 || ks > 0) ? 1u : 0u);
-          tc_mma_bf16(tmem, da + off, db + blo + off, idesc, 1u);
-          tc_mma_bf16(tmem, da + alo + off, db + off, idesc, 1u);
+          if (planes == 2) {
+            tc_mma_bf16(tmem, da + off, db + blo + off, idesc, 1u);
+            tc_mma_bf16(tmem, da + alo + off, db + off, idesc, 1u);
+          }
         }
         tc_commit(S.sfree + sl);
         if (b == kb - 1) tc_commit(S.accb);
@@ -591,7 +600,8 @@ __device__ void tcc_sweep(const ChunkArgs& a, const TccS& S, int r0, int nrows, 
           const int e1 = S.start[j + 1];
 #pragma unroll 4
           for (int e = S.start[j]; e < e1; ++e) sum += S.sP[S.order[e] * ss + ff] - c;
-          a.part_sum[((size_t)b * k + j) * npad + f] = sum;
+          if (BM_GUARD(j >= 0 && j < k, &a.ctl->status))
+            a.part_sum[((size_t)b * k + j) * npad + f] = sum;
         }
       }
     }
@@ -729,6 +739,7 @@ __device__ void tcc_set_centroid(const ChunkArgs& a, const TccS& S, int j, const
 }
 
 __device__ __forceinline__ void tcc_load_cand(const ChunkArgs& a, const TccS& S, int c, int row) {
+  if (!BM_GUARD(row >= 0 && row < a.s, &a.ctl->status)) row = 0;
   for (int f = threadIdx.x; f < a.npad; f += blockDim.x)
     S.cand[c * a.npad + f] = __ldcg(a.P + (size_t)row * a.npad + f);
 }
@@ -879,7 +890,9 @@ __device__ void tcc_gather(const ChunkArgs& a, const TccS& S, int r0, int nrows)
         const int u = u0 + q * kTccThreads;
         if (u < units) {
           const int i = u / q4, c = u - i * q4;
-          v[q] = __ldg(X4 + (size_t)S.order[i] * q4 + c);
+          int row = S.order[i];
+          if (!BM_GUARD(row >= 0 && row < a.m, &a.ctl->status)) row = 0;
+          v[q] = __ldg(X4 + (size_t)row * q4 + c);
         }
       }
 #pragma unroll
@@ -899,7 +912,9 @@ __device__ void tcc_gather(const ChunkArgs& a, const TccS& S, int r0, int nrows)
         v[q] = 0.f;
         if (u < units) {
           const int i = u / nch, f = (u - i * nch) * 32 + l;
-          if (f < n) v[q] = __ldg(X + (size_t)S.order[i] * n + f);
+          const int row = S.order[i];
+          if (f < n && BM_GUARD(row >= 0 && row < a.m, &a.ctl->status))
+            v[q] = __ldg(X + (size_t)row * n + f);
         }
       }
 #pragma unroll
@@ -920,7 +935,7 @@ __global__ void __launch_bounds__(kTccThreads, 1) chunk_tc_kernel(ChunkArgs a) {
   extern __shared__ __align__(1024) unsigned char tcc_raw[];
   unsigned char* base = tcc_raw + ((1024u - (smem_u32(tcc_raw) & 1023u)) & 1023u);
   const int R = a.rows_per_cta, k = a.k;
-  const TccLayout L = tcc_layout(a.npad, k, R, a.tc_n16, a.tc_fb, a.tc_ns);
+  const TccLayout L = tcc_layout(a.npad, k, R, a.tc_n16, a.tc_fb, a.tc_ns, a.tc_planes);
   TccS S;
   S.ring = base + L.region;
   S.sP = reinterpret_cast<float*>(base + L.region);
@@ -1049,8 +1064,8 @@ __global__ void __launch_bounds__(kTccThreads, 1) chunk_tc_kernel(ChunkArgs a) {
 }
 
 // ---------------------------------------------------------------- host side
-size_t chunk_tc_smem(int npad, int k, int R, int n16, int fb, int ns) {
-  const TccLayout L = tcc_layout(npad, k, R, n16, fb, ns);
+size_t chunk_tc_smem(int npad, int k, int R, int n16, int fb, int ns, int planes) {
+  const TccLayout L = tcc_layout(npad, k, R, n16, fb, ns, planes);
   return (size_t)L.total + 1024;   // + alignment slack of the dynamic base
 }
 

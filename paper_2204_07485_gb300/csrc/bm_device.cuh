@@ -15,6 +15,21 @@ constexpr int kMaxRounds = 64;           // sample-draw rounds (never reached)
 // Status codes written to the device status word (same values as bm_status).
 constexpr int kStatusOk = 0;
 constexpr int kStatusTimeout = 4;
+constexpr int kStatusGuard = 8;
+
+// Index guards of the debug build (compiled with BM_DEBUG_GUARDS): a guarded
+// access whose index falls outside its buffer is skipped and records
+// kStatusGuard in the status word (when the kernel has one); nothing traps.
+// Release builds compile every guard to `true`.
+#ifdef BM_DEBUG_GUARDS
+__device__ __forceinline__ bool guard_ok(bool in_bounds, int* status) {
+  if (!in_bounds && status) atomicCAS(status, kStatusOk, kStatusGuard);
+  return in_bounds;
+}
+#define BM_GUARD(cond, status) (::bm::guard_ok((cond), (status)))
+#else
+#define BM_GUARD(cond, status) (true)
+#endif
 
 // Bounds of every device-side spin: the wait gives up after this many polls
 // or this much wall time (read from %globaltimer), whichever comes first.

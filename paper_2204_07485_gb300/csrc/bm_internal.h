@@ -102,9 +102,11 @@ struct ChunkArgs {
   int tc_fb;              // features per staged block of the exact passes
   int tc_tpc;             // 128-row tiles per CTA: ceil(rows_per_cta / 128)
   int tc_ns;              // MMA ring slots (2 or 3)
+  int tc_planes;          // BF16 planes of the screening products: 1 (BF16) or
+                          // 2 (split BF16: hi*hi + hi*lo + lo*hi)
   unsigned char* Cb;      // [tc_kb][2][tc_n16][128 B] centroid BF16 planes (hi, lo), swizzled
   float* sqs;             // [k][ceil(npad / 8)] squared norms of 8-feature slices of C
-  unsigned char* Pb;      // [G][tc_tpc][tc_kb][2][128][128 B] own-row BF16 planes, swizzled
+  unsigned char* Pb;      // [G][tc_tpc][tc_kb][tc_planes][128][128 B] own-row BF16 planes, swizzled
 };
 
 struct AssignArgs {
@@ -119,7 +121,14 @@ struct AssignArgs {
   double* part;        // [G]
   double* sse;         // device scalar
   uint32_t* ticket;    // zero between launches
+  int* status;         // debug builds: index-guard status word (may be null)
 };
+
+// Words of one chunk's bitmap in global memory: ceil(m / 32) rounded up to a
+// multiple of four, so every chunk's bitmap starts on a 16-byte boundary.
+__host__ __device__ inline size_t draw_bitmap_words(long long m) {
+  return (size_t)(((m + 31) / 32 + 3) / 4 * 4);
+}
 
 struct DrawArgs {
   long long m;
@@ -127,8 +136,9 @@ struct DrawArgs {
   unsigned long long seed;
   long long t0;        // first chunk of the batch; CTA b draws chunk t0 + b
   int32_t* idx;        // [batch][s] sorted sample rows
-  uint32_t* bitmaps;   // [batch][ceil(m / 32)], all zero between launches
+  uint32_t* bitmaps;   // [batch][draw_bitmap_words(m)], all zero between launches
   int smem_bitmap;     // set by launch_draw: the bitmap fits in shared memory
+  int* status;         // debug builds: index-guard status word (may be null)
 };
 
 struct AssignTcArgs {
@@ -290,7 +300,7 @@ cudaError_t launch_chunk(const ChunkArgs& a, int grid, bool generic, int np,
                          size_t smem, cudaStream_t st);
 // tensor-core chunk kernel: shared memory for (npad, k, R, n16, fb, ring
 // slots); CTAs that can be co-resident; launch
-size_t chunk_tc_smem(int npad, int k, int R, int n16, int fb, int ns);
+size_t chunk_tc_smem(int npad, int k, int R, int n16, int fb, int ns, int planes);
 int chunk_tc_max_grid(size_t smem);
 cudaError_t launch_chunk_tc(const ChunkArgs& a, int grid, size_t smem, cudaStream_t st);
 size_t polish_smem(int k, int fw, int wu);

@@ -444,7 +444,7 @@ __device__ void lloyd_own_rows(const ChunkArgs& a, const Smem& S,
       ps[3 * (size_t)G] = s3;
     }
     for (int j = threadIdx.x; j < k; j += blockDim.x)
-      a.part_cnt[(size_t)j * G + b] = start[j + 1] - start[j];
+      if (BM_GUARD(j < a.k, &a.ctl->status)) a.part_cnt[(size_t)j * G + b] = start[j + 1] - start[j];
     __syncthreads();
     if (threadIdx.x == 0) {   // the merge left one exact pair per warp in S.red
       double t = 0.0;
@@ -486,13 +486,14 @@ __device__ void lloyd_own_rows(const ChunkArgs& a, const Smem& S,
       if (f < n) {
         float sum = 0.f;
         for (int g = 0; g < ng; ++g) sum += S.sw[g * k * npad + q];
-        a.part_sum[((size_t)jj * npad + f) * G + b] = sum;
+        if (BM_GUARD(jj < a.k && f < npad, &a.ctl->status))
+          a.part_sum[((size_t)jj * npad + f) * G + b] = sum;
       }
     }
     for (int jj = threadIdx.x; jj < k; jj += blockDim.x) {
       int c = 0;
       for (int g = 0; g < ng; ++g) c += S.cw[g * k + jj];
-      a.part_cnt[(size_t)jj * G + b] = c;
+      if (BM_GUARD(jj < a.k, &a.ctl->status)) a.part_cnt[(size_t)jj * G + b] = c;
     }
     __syncthreads();
   }
@@ -532,7 +533,8 @@ __device__ void phase_gather(const ChunkArgs& a, const Smem& S, int r0, int nrow
   if constexpr (!GENERIC) {
     const bool vec4 = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-      const long long row = __ldcg(a.idx + r0 + i);
+      long long row = __ldcg(a.idx + r0 + i);
+      if (!BM_GUARD(row >= 0 && row < a.m, &a.ctl->status)) row = 0;
       float p[NP];
       load_row_np<NP>(p, X + (size_t)row * n, n, vec4, false);
       float4* dst = reinterpret_cast<float4*>(a.P + (size_t)(r0 + i) * NP);
@@ -554,7 +556,9 @@ __device__ void phase_gather(const ChunkArgs& a, const Smem& S, int r0, int nrow
         v[u] = 0.f;
         if (e < total) {
           const int i = e / npad, f = e - i * npad;
-          if (f < n) v[u] = __ldg(X + (size_t)__ldcg(a.idx + r0 + i) * n + f);
+          const long long row = __ldcg(a.idx + r0 + i);
+          if (f < n && BM_GUARD(row >= 0 && row < a.m, &a.ctl->status))
+            v[u] = __ldg(X + (size_t)row * n + f);
         }
       }
 #pragma unroll
@@ -576,6 +580,7 @@ __device__ __forceinline__ void set_centroid_row(const Smem& S, const float* src
 
 __device__ __forceinline__ void load_cand_row(const ChunkArgs& a, const Smem& S,
                                               int c, int row) {
+  if (!BM_GUARD(row >= 0 && row < a.s, &a.ctl->status)) row = 0;
   for (int f = threadIdx.x; f < a.npad; f += blockDim.x)
     S.cand[c * a.npad + f] = __ldcg(a.P + (size_t)row * a.npad + f);
 }
@@ -940,8 +945,10 @@ assign_np_kernel(AssignArgs a) {
     int ja, jb;
     float da, db;
     nearest2_np<NP>(pa, pb, cen, lidx, 0, lidx[a.k], ja, da, jb, db);
-    if (a.labels) a.labels[i] = ja;
-    if (a.dmin) a.dmin[i] = da;
+    if (BM_GUARD(i < a.m, a.status)) {
+      if (a.labels) a.labels[i] = ja;
+      if (a.dmin) a.dmin[i] = da;
+    }
     acc += (double)da;
     if (two) {
       if (a.labels) a.labels[i2] = jb;
@@ -975,8 +982,10 @@ assign_generic_kernel(AssignArgs a) {
     float d;
     if (nearest_tile(stage, cenT, live, a.k, a.kpad, a.n, rows, j, d)) {
       const long long i = r0 + (threadIdx.x >> 5) * 8 + (threadIdx.x & 31);
-      if (a.labels) a.labels[i] = j;
-      if (a.dmin) a.dmin[i] = d;
+      if (BM_GUARD(i < a.m && i < r0 + rows, a.status)) {
+        if (a.labels) a.labels[i] = j;
+        if (a.dmin) a.dmin[i] = d;
+      }
       acc += (double)d;
     }
     __syncthreads();

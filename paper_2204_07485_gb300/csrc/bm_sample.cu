@@ -7,12 +7,12 @@
 //   round r draws (target - |S|) Philox words (purpose 0, counter
 //   (i / 4, r, t, 0)), maps each to a row by the high word of w * m, and adds
 //   it to S with atomicOr on the chunk's bitmap (in shared memory when it
-//   fits); |S| after round 0 is a popcount of the bitmap, after later rounds
-//   the count of bits that were clear.  Rounds continue until |S| = target (64 rounds at most; the
-//   smallest absent rows complete S after that, which never happens in
-//   practice for target <= m / 2).  target = s, or m - s rows to leave out
-//   when 2s > m.  A fixed-order scan of the bitmap then writes the sample's
-//   rows in ascending order (and clears a global bitmap for the next use).
+//   fits); |S| grows by the count of atomics that found their bit clear.
+//   Rounds continue until |S| = target (64 rounds at most; the smallest
+//   absent rows complete S after that, which never happens in practice for
+//   target <= m / 2).  target = s, or m - s rows to leave out when 2s > m.
+//   A fixed-order scan of the bitmap then writes the sample's rows in
+//   ascending order (and clears a global bitmap for the next use).
 // Nothing here waits on another CTA.
 #include <cuda_runtime.h>
 
@@ -45,14 +45,26 @@ __device__ __forceinline__ int block_excl_scan_i32(int v, int* buf, int* total) 
   return before + x - v;
 }
 
+// Bits of bitmap word w that mark sample rows: the word itself, or for a
+// complement draw the rows left unmarked (within [0, m)).
+__device__ __forceinline__ uint32_t sample_bits(uint32_t raw, long long w, long long W,
+                                                long long m, bool complement) {
+  if (!complement) return raw;
+  if (w >= W) return 0u;
+  uint32_t v = ~raw;
+  const long long lo = w * 32;
+  if (lo + 32 > m) v &= (1u << (m - lo)) - 1u;
+  return v;
+}
+
 __global__ void __launch_bounds__(kDrawThreads) draw_kernel(DrawArgs a) {
-  extern __shared__ uint32_t sbits[];   // the chunk's bitmap, when it fits
+  extern __shared__ __align__(16) uint32_t sbits[];   // the chunk's bitmap, when it fits
   __shared__ int red[32];
   __shared__ int scan[32];
   const long long W = (a.m + 31) / 32;
   const long long t = a.t0 + blockIdx.x;
   const bool in_smem = a.smem_bitmap != 0;
-  uint32_t* bm = in_smem ? sbits : a.bitmaps + (size_t)blockIdx.x * W;
+  uint32_t* bm = in_smem ? sbits : a.bitmaps + (size_t)blockIdx.x * draw_bitmap_words(a.m);
   int32_t* out = a.idx + (size_t)blockIdx.x * a.s;
   const bool complement = 2 * (long long)a.s > a.m;
   const uint32_t target = complement ? (uint32_t)(a.m - a.s) : (uint32_t)a.s;
@@ -61,32 +73,28 @@ __global__ void __launch_bounds__(kDrawThreads) draw_kernel(DrawArgs a) {
     __syncthreads();
   }
 
-  // Round 0 sets its bits without waiting for the old values, then counts
-  // the set bits; the set after a round does not depend on the order of the
-  // atomics, so neither does anything below.  Later rounds (a few draws)
-  // count new bits from the atomics' old values.
+  // Round r draws (target - |S|) values.  One Philox evaluation gives the
+  // four words of counter c = i / 4, so a thread takes four consecutive
+  // draws at a time.  |S| grows by the number of atomics that found their
+  // bit clear: a value drawn several times flips its bit exactly once, so
+  // the count does not depend on the order of the atomics.
   uint32_t have = 0;
-  if (target > 0) {
-    for (uint32_t i = threadIdx.x; i < target; i += blockDim.x) {
-      const uint64_t w = philox_word(a.seed, (uint64_t)t, 0, 0, i);
-      const uint64_t v = __umul64hi(w, (uint64_t)a.m);
-      atomicOr(bm + (v >> 5), 1u << (v & 31));   // result unused: a reduction
-    }
-    __syncthreads();
-    int c = 0;
-    for (long long w = threadIdx.x; w < W; w += blockDim.x)
-      c += __popc(in_smem ? bm[w] : __ldcg(bm + w));
-    have = (uint32_t)block_sum_i32(c, red);
-  }
-  for (int r = 1; r < kRoundSlots && have < target; ++r) {
+  for (int r = 0; r < kRoundSlots && have < target; ++r) {
     const uint32_t need = target - have;
+    const uint32_t blocks = (need + 3u) / 4u;
     int got = 0;
-    for (uint32_t i = threadIdx.x; i < need; i += blockDim.x) {
-      const uint64_t w = philox_word(a.seed, (uint64_t)t, 0, (uint64_t)r, i);
-      const uint64_t v = __umul64hi(w, (uint64_t)a.m);
-      const uint32_t bit = 1u << (v & 31);
-      const uint32_t old = atomicOr(bm + (v >> 5), bit);
-      got += (old & bit) ? 0 : 1;
+    for (uint32_t c = threadIdx.x; c < blocks; c += blockDim.x) {
+      const U64x4 w4 = philox4x64_10(c, (uint64_t)r, (uint64_t)t, 0, a.seed, 0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (4u * c + (uint32_t)q < need) {
+          const uint64_t v = __umul64hi(w4.x[q], (uint64_t)a.m);
+          const uint32_t bit = 1u << (v & 31);
+          if (!BM_GUARD(v < (uint64_t)a.m, a.status)) continue;
+          const uint32_t old = atomicOr(bm + (v >> 5), bit);
+          got += (old & bit) ? 0 : 1;
+        }
+      }
     }
     have += (uint32_t)block_sum_i32(got, red);
   }
@@ -102,7 +110,58 @@ __global__ void __launch_bounds__(kDrawThreads) draw_kernel(DrawArgs a) {
   }
   __syncthreads();
 
-  // compaction: kWordsPerThread consecutive words per thread per tile
+  if (!in_smem) {
+    // global bitmap: thread i owns the contiguous 16-byte groups [g0, g1);
+    // a first pass counts its sample rows (eight loads in flight), an
+    // exclusive scan gives its first output position, a second pass writes
+    // its rows in ascending order and clears the words for the next draw
+    const long long G4 = (long long)draw_bitmap_words(a.m) / 4;
+    const long long span = (G4 + blockDim.x - 1) / blockDim.x;
+    const long long g0 = min(G4, (long long)threadIdx.x * span), g1 = min(G4, g0 + span);
+    uint4* b4 = reinterpret_cast<uint4*>(bm);
+    int cnt = 0;
+    for (long long g = g0; g < g1; g += 8) {
+      uint4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = g + u < g1 ? __ldcg(b4 + g + u) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const long long w = 4 * (g + u);
+        if (g + u < g1)
+          cnt += __popc(sample_bits(v[u].x, w, W, a.m, complement)) +
+                 __popc(sample_bits(v[u].y, w + 1, W, a.m, complement)) +
+                 __popc(sample_bits(v[u].z, w + 2, W, a.m, complement)) +
+                 __popc(sample_bits(v[u].w, w + 3, W, a.m, complement));
+      }
+    }
+    int total;
+    int pos = block_excl_scan_i32(cnt, scan, &total);
+    for (long long g = g0; g < g1; g += 8) {
+      uint4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = g + u < g1 ? __ldcg(b4 + g + u) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (g + u >= g1) continue;
+        const uint32_t raw[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const long long w = 4 * (g + u) + e;
+          uint32_t bits = sample_bits(raw[e], w, W, a.m, complement);
+          while (bits) {
+            const int bp = __ffs(bits) - 1;
+            if (pos < a.s) out[pos] = (int32_t)(w * 32 + bp);
+            ++pos;
+            bits &= bits - 1;
+          }
+        }
+        if (v[u].x | v[u].y | v[u].z | v[u].w) b4[g + u] = make_uint4(0, 0, 0, 0);
+      }
+    }
+    return;
+  }
+
+  // shared-memory bitmap: kWordsPerThread consecutive words per thread per tile
   int base = 0;
   const long long tile = (long long)blockDim.x * kWordsPerThread;
   for (long long t0 = 0; t0 < W; t0 += tile) {
@@ -112,17 +171,7 @@ __global__ void __launch_bounds__(kDrawThreads) draw_kernel(DrawArgs a) {
 #pragma unroll
     for (int u = 0; u < kWordsPerThread; ++u) {
       const long long w = wb + u;
-      uint32_t v = 0u;
-      if (w < W) {
-        const uint32_t raw = in_smem ? bm[w] : __ldcg(bm + w);
-        v = raw;
-        if (complement) {
-          v = ~raw;
-          const long long lo = w * 32;
-          if (lo + 32 > a.m) v &= (1u << (a.m - lo)) - 1u;
-        }
-        if (!in_smem) bm[w] = 0u;   // ready for the next draw
-      }
+      const uint32_t v = w < W ? sample_bits(bm[w], w, W, a.m, complement) : 0u;
       words[u] = v;
       c += __popc(v);
     }

@@ -73,7 +73,7 @@ __host__ __device__ inline TcLayout tc_layout(int n, int kb, int npad16, int k, 
   L.xF = o;    o += (stages == 0 && n <= 64) ? kTcRows * align_up(n, 4) * 4 : 0;
   L.cF = o;    o += cf ? align_up(k * n * 4, 16) : 0;   // FP32 centroids
   L.cc = o;    o += align_up(npad16 * 4, 16);           // ||c_j||^2, +inf if not live
-  L.xx = o;    o += kTcRows * 4;                        // ||x||^2 of the tile's rows
+  L.xx = o;    o += 2 * kTcRows * 4;                    // ||x||^2 of the tile's rows (two halves)
   L.sc = o;    o += (kTcRows + 128) * 4;                // E4M3 form: 1/scale of rows, centroids
   L.red = o;   o += 40 * 8;
   L.bars = o;  o += 8 * 3;                              // MMA completion, stage arrivals
@@ -392,15 +392,12 @@ assign_tc_kernel(AssignTcArgs a) {
         if (planes == 2)
           *reinterpret_cast<uint4*>(sA + planeA + off) = make_uint4(l[0], l[1], l[2], l[3]);
       }
-      // the cslots consecutive lanes of a row hold its partial norms (a row
-      // wider than a warp adds its two warp sums into the zeroed xx[r])
+      // the cslots consecutive lanes of a row hold its partial norms; a row
+      // wider than a warp leaves its second warp's sum in xx[kTcRows + r],
+      // added to the first in that order by the epilogue
       const int span = cslots < 32 ? cslots : 32;
       for (int o = span >> 1; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-      if (cslots <= 32) {
-        if (ch == 0) xx[r] = q;
-      } else if ((ch & 31) == 0) {
-        atomicAdd(xx + r, q);
-      }
+      if ((ch & 31) == 0) xx[(ch >> 5) * kTcRows + r] = q;
     }
     fence_proxy_async_smem();
     __syncthreads();
@@ -441,7 +438,7 @@ assign_tc_kernel(AssignTcArgs a) {
     const int r = tid;
     const bool valid = r < rows;
     const float* xrow = S == 2 ? tile + (size_t)r * n : xf ? xF + r * xs : src + (size_t)r * n;
-    const float xq = xx[r] * 1.00002f;
+    const float xq = (cslots > 32 ? __fadd_rn(xx[r], xx[kTcRows + r]) : xx[r]) * 1.00002f;
     const float E1 = fmaf(sqrtf(xq), s_bound[0], s_bound[1]);
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     // approximate distance minus ||x||^2 from accumulator column j (the E4M3
@@ -487,8 +484,10 @@ assign_tc_kernel(AssignTcArgs a) {
     // depend on how tiles are spread over CTAs
     float th = valid ? best : 0.f, tl = 0.f;
     if (valid) {
-      if (a.labels) a.labels[r0 + r] = bj;
-      if (a.dmin) a.dmin[r0 + r] = best;
+      if (BM_GUARD(r0 + r < a.m, a.status)) {
+        if (a.labels) a.labels[r0 + r] = bj;
+        if (a.dmin) a.dmin[r0 + r] = best;
+      }
       rescored += ncand > 1;
     }
     warp_two_sum(th, tl);

@@ -370,8 +370,10 @@ assign_tcs_kernel(const __grid_constant__ CUtensorMap xmap, TcsArgs a) {
       }
       float th = valid ? best : 0.f, tl = 0.f;
       if (valid) {
-        if (a.labels) a.labels[row] = bj;
-        if (a.dmin) a.dmin[row] = best;
+        if (BM_GUARD(row < a.m && (bj == INT_MAX || bj < k), a.status)) {
+          if (a.labels) a.labels[row] = bj;
+          if (a.dmin) a.dmin[row] = best;
+        }
         rescored += ncand > 1;
       }
       // the tile's SSE as an exact (hi, lo) pair: warps of the warpgroup,

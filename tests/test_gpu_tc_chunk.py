@@ -18,7 +18,7 @@ from gpu_helpers import (CEN_REL, OBJ_REL, centroids_close, dev, host, labels_ma
 from test_gpu_parity import _assert_decisive
 
 pytestmark = pytest.mark.gpu
-BF16X3 = 3
+BF16, BF16X3 = 1, 3
 
 
 @pytest.fixture(scope="module")
@@ -51,6 +51,12 @@ def _run(bm, X, cfg, T):
     (5000, 68, 100, 2500, 0, 2, BF16X3),
     (3000, 384, 100, 1500, 0, 2, BF16X3),   # six K blocks, n16 = 112
     (3000, 384, 100, 1500, 0, 2, 0),        # FP32 form: tables too large, same kernel
+    # BF16 screening (one plane, one MMA per product; looser bound, more rescoring)
+    (4000, 128, 50, 2000, 1, 3, BF16),
+    (2500, 200, 17, 1300, 0, 3, BF16),
+    (1000, 33, 7, 999, 0, 2, BF16),
+    (3000, 384, 100, 1500, 0, 2, BF16),
+    (1200, 40, 1, 400, 0, 3, BF16),
 ])
 def test_tc_chunks_match_oracle(bm, m, n, k, s, seed, T, prec):
     X, _ = bi.mixtures.isotropic_blobs(m, n, max(k, 2), seed, box=8.0)
@@ -71,14 +77,15 @@ def test_tc_chunks_match_oracle(bm, m, n, k, s, seed, T, prec):
     assert rel(sse, sse_ref) <= OBJ_REL
 
 
-@pytest.mark.parametrize("seed,chunks", [(2, (1, 2, 3, 4, 5))])
-def test_tc_full_size_chunks_teacher_forced(bm, seed, chunks):
+@pytest.mark.parametrize("seed,chunks,prec", [(2, (1, 2, 3, 4, 5), BF16X3),
+                                              (2, (1, 2, 3, 4, 5), BF16)])
+def test_tc_full_size_chunks_teacher_forced(bm, seed, chunks, prec):
     """m = 200,000, n = 128, k = 50, s = 50,000 (a 100-component mixture with
     Dirichlet(0.5) weights): every chunk starts from the oracle's incumbent
     and must end at the oracle's."""
     m, n, k, s = 200_000, 128, 50, 50_000
     X, _ = bi.mixtures.isotropic_blobs(m, n, 100, 0, alpha=0.5)
-    cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=seed, precision=BF16X3)
+    cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=seed, precision=prec)
     ctx = bm.bm_create(cfg, dev(X))
     st = o.BigMeansState(k, n)
     try:
@@ -110,14 +117,15 @@ def test_tc_and_fp32_kernels_agree(bm):
     m, n, k, s, T, seed = 3000, 64, 33, 1000, 3, 0
     X, _ = bi.mixtures.isotropic_blobs(m, n, k, seed, box=8.0)
     out = []
-    for prec in (0, BF16X3):
+    for prec in (0, BF16X3, BF16):
         cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=seed, precision=prec)
         out.append(_run(bm, X, cfg, T))
-    (r0, C0, m0, f0, l0, s0), (r1, C1, m1, f1, l1, s1) = out
-    assert r0["lloyd_iters"] == r1["lloyd_iters"] and r0["accepted"] == r1["accepted"]
-    assert np.array_equal(m0, m1)
-    assert rel(f0, f1) <= OBJ_REL
-    assert centroids_close(C1, C0.astype(np.float64), m0) <= CEN_REL
+    r0, C0, m0, f0, l0, s0 = out[0]
+    for r1, C1, m1, f1, l1, s1 in out[1:]:
+        assert r0["lloyd_iters"] == r1["lloyd_iters"] and r0["accepted"] == r1["accepted"]
+        assert np.array_equal(m0, m1)
+        assert rel(f0, f1) <= OBJ_REL
+        assert centroids_close(C1, C0.astype(np.float64), m0) <= CEN_REL
 
 
 def test_tc_runs_are_bitwise_deterministic(bm):
