@@ -7,9 +7,10 @@ full-data assignment with its float64 SSE.  One step = one complete Big-means
 job: reset the incumbent, 100 chunks (sample draw, gather, K-means++ reseed,
 Lloyd to the paper's stop rule, keep-the-best), final assignment.
 
-The timed form is BF16 + rescore (split BF16 tensor-core distances with exact
-FP32 rescoring of every row the error bound cannot settle); the plain FP32
-form of the same job is timed beside it (time to the same SSE).  The metric
+The timed form is BF16 + rescore (BF16 tensor-core products with FP32
+accumulation, exact FP32 rescoring of every row the error bound cannot
+settle); the plain FP32 form and the split-BF16 form of the same job are
+timed beside it (time to the same SSE).  The metric
 is distance throughput: 2 n flops per point-to-centroid distance evaluation
 (the paper's n_d counter) over the step time.
 
@@ -40,7 +41,8 @@ UNIT = "TFLOP/s"
 # the timed job: m = 1e7, n = 128 mixture (generated on the device)
 C3_WORKLOAD = dict(name="gas_sensor_like_m1e7_n128_k50_s50000_T100", m=10_000_000, n=128,
                    k=50, s=50_000, chunks=100, seed=0)
-HEAD_FORM = "bf16x3"
+HEAD_FORM = "bf16"
+SIDE_FORMS = ("fp32", "bf16x3")     # timed beside it, same window
 # further jobs reported beside it
 C2_WORKLOAD = dict(name="hepmass_like_m1e6_n28_k25_s50000_T100", m=1_000_000, n=28,
                    k=25, s=50_000, chunks=100, seed=0)
@@ -59,7 +61,7 @@ FORM_CODES = {"fp32": 0, "bf16": 1, "fp8": 2, "bf16x3": 3}
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one chunk_tc_kernel
 # launch (a typical chunk: gather + split-BF16 planes + Lloyd), n = 128,
 # k = 50, s = 50,000; the gather reads s rows whatever m is
-CHUNK_TC_DRAM_BYTES = 31_585_024
+CHUNK_TC_DRAM_BYTES = None
 
 
 def parse():
@@ -364,18 +366,20 @@ def run_ours(args, wl):
     stream = torch.cuda.Stream(device=dev)
     labels = torch.empty(m, dtype=torch.int32, device=dev)
     cfgs = {f: bm.bm_config_default(m=m, n=n, k=k, s=s, seed=seed, precision=FORM_CODES[f])
-            for f in (HEAD_FORM, "fp32")}
+            for f in (HEAD_FORM,) + SIDE_FORMS}
     ctxs = {f: bm.bm_create(cfgs[f], Xd, stream.cuda_stream) for f in cfgs}
     new_ev = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(3)]   # noqa: E731
 
     for _ in range(args.warmup):
         job_step(bm, ctxs[HEAD_FORM], stream, T, labels, new_ev())
-    job_step(bm, ctxs["fp32"], stream, T, labels, new_ev())
+    for f in SIDE_FORMS:
+        job_step(bm, ctxs[f], stream, T, labels, new_ev())
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
     # X (5.12 GB) is far larger than L2 (129 MB): every step streams it anew
-    events, reps, fevents, freps = [], [], [], []
+    events, reps = [], []
+    side = {f: ([], []) for f in SIDE_FORMS}   # form -> (events, reports)
     with ClockSampler(local if world > 1 else 0) as clocks:
         t_wall = time.perf_counter()
         for _ in range(args.steps):
@@ -384,19 +388,17 @@ def run_ours(args, wl):
             events.append(ev)
         torch.cuda.synchronize(dev)
         t_wall = time.perf_counter() - t_wall
-        # the plain FP32 form of the same job, beside it (same sampler window)
-        for _ in range(args.steps):
-            ev = new_ev()
-            freps.append(job_step(bm, ctxs["fp32"], stream, T, labels, ev))
-            fevents.append(ev)
-        torch.cuda.synchronize(dev)
+        # the other forms of the same job, beside it (same sampler window)
+        for f in SIDE_FORMS:
+            for _ in range(args.steps):
+                ev = new_ev()
+                side[f][1].append(job_step(bm, ctxs[f], stream, T, labels, ev))
+                side[f][0].append(ev)
+            torch.cuda.synchronize(dev)
     fit_ms = [e[0].elapsed_time(e[1]) for e in events]
     asg_ms = [e[1].elapsed_time(e[2]) for e in events]
     step_ms = [a + b for a, b in zip(fit_ms, asg_ms)]
-    ffit = [e[0].elapsed_time(e[1]) for e in fevents]
-    fasg = [e[1].elapsed_time(e[2]) for e in fevents]
     rep, sse = reps[-1]
-    frep, fsse = freps[-1]
     C = np.zeros((k, n), np.float32)
     mask = np.zeros(k, np.uint8)
     f_opt = bm.bm_objective(ctxs[HEAD_FORM], C, mask)
@@ -419,8 +421,8 @@ def run_ours(args, wl):
     asg_per_step = float(np.mean(asg_ms))
     hbm_peak, bf16_peak, peak_src = measured_peaks()
     chunk_kernel = {
-        "kernel": "chunk_tc_kernel (gather + split-BF16 planes + K-means++ + Lloyd + "
-                  "keep-best; split-BF16 tcgen05 MMAs, exact FP32 rescoring)",
+        "kernel": "chunk_tc_kernel (gather + BF16 planes + K-means++ + Lloyd + "
+                  "keep-best; BF16 tcgen05 MMAs, exact FP32 rescoring)",
         "bound": "tensor",
         "achieved": 2.0 * n * nd_fit / (fit_per_step / 1e3) / 1e12,
         "peak": bf16_peak, "unit": "TFLOP/s",
@@ -432,7 +434,7 @@ def run_ours(args, wl):
     chunk_kernel["frac"] = chunk_kernel["achieved"] / chunk_kernel["peak"]
     abytes = m * n * 4 + m * 4
     assign_kernel = {
-        "kernel": "assign_tcs_kernel (final assignment, split-BF16 MMAs + exact FP32 "
+        "kernel": "assign_tcs_kernel (final assignment, BF16 MMAs + exact FP32 "
                   "rescoring, FP64 SSE)",
         "bound": "hbm",
         "achieved": abytes / (asg_per_step / 1e3) / 1e9, "peak": hbm_peak,
@@ -472,25 +474,33 @@ def run_ours(args, wl):
     out = None
     if rank == 0:
         head_ms = total_ms / args.steps
-        fp32_ms = float(np.mean(np.add(ffit, fasg)))
+        side_forms = {}
+        for f in SIDE_FORMS:
+            evs, rps = side[f]
+            ffit = [e[0].elapsed_time(e[1]) for e in evs]
+            fasg = [e[1].elapsed_time(e[2]) for e in evs]
+            frep, fsse = rps[-1]
+            fms = float(np.mean(np.add(ffit, fasg)))
+            side_forms[f] = {
+                "time_to_sse_ms": fms, "fit_ms": float(np.mean(ffit)),
+                "assign_ms": float(np.mean(fasg)), "sse": fsse,
+                "value": 2.0 * n * (frep["n_d"] + m * nlive) / (fms / 1e3) / 1e12,
+                "sse_rel_diff_vs_head": abs(fsse - sse) / fsse,
+                "same_lloyd_iters": frep["lloyd_iters"] == rep["lloyd_iters"]}
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": head_ms, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f32",
+               "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32",
                "data": "synthetic",
                "config": {"workload": wl["name"], "m": m, "n": n, "k": k, "s": s,
                           "chunks": T, "seed": wl["seed"],
-                          "form": "BF16 + rescore (split BF16 tensor-core products, FP32 "
+                          "form": "BF16 + rescore (BF16 tensor-core products, FP32 "
                                   "accumulation, exact FP32 rescoring)",
                           "l2": "X is 5.12 GB, 40x L2: each step streams it from HBM",
                           "parallelism": "replicas (independent job per GPU)"},
                "time_to_sse_ms": head_ms, "sse": sse,
-               "fp32": {"time_to_sse_ms": fp32_ms, "fit_ms": float(np.mean(ffit)),
-                        "assign_ms": float(np.mean(fasg)), "sse": fsse,
-                        "value": 2.0 * n * (frep["n_d"] + m * nlive) / (fp32_ms / 1e3) / 1e12,
-                        "sse_rel_diff_vs_head": abs(fsse - sse) / fsse,
-                        "same_lloyd_iters": frep["lloyd_iters"] == rep["lloyd_iters"]},
-               "speedup_vs_fp32": fp32_ms / head_ms,
+               "forms": side_forms,
+               "speedup_vs_fp32": side_forms["fp32"]["time_to_sse_ms"] / head_ms,
                "f_opt": f_opt, "live": nlive, "lloyd_iters_per_step": rep["lloyd_iters"],
                "accepted_per_step": rep["accepted"], "n_d_per_step": nd_step,
                "fit_ms_per_step": fit_per_step, "assign_ms_per_step": asg_per_step,
@@ -826,8 +836,8 @@ def serving(bm, torch, dev, spec=SERVING):
 PROFILE_CASES = {
     # kernel family: (m, n, k, s, precision, chunks); small jobs for ncu captures
     "chunk_np": (1_000_000, 28, 25, 50_000, 0, 4),     # chunk_kernel<28, 0>
-    "chunk_tc": (1_000_000, 128, 50, 50_000, 3, 3),    # chunk_tc_kernel
-    "assign_tc": (2_000_000, 128, 50, 50_000, 3, 1),   # assign_tcs_kernel (final assignment)
+    "chunk_tc": (1_000_000, 128, 50, 50_000, 1, 3),    # chunk_tc_kernel, BF16 screening
+    "assign_tc": (2_000_000, 128, 50, 50_000, 1, 1),   # assign_tcs_kernel, BF16 (final assignment)
     "assign_fp8": (2_000_000, 384, 100, 50_000, 2, 1),  # assign_tc_kernel<true> (E4M3)
 }
 
