@@ -534,6 +534,7 @@ def run_ours(args, wl):
         del Xs, flush
         torch.cuda.empty_cache()
         out["other_jobs"] = extra
+        out["tile_pipeline"] = tile_pipeline(bm)
         out["launch_latency"] = launch_latency(bm, torch, dev)
         if not args.no_grouped:
             out["grouped"] = grouped(bm, torch, dev)
@@ -605,6 +606,29 @@ def traced_phases(bm, Xd, cfg, stream, T):
         return {p: round(v, 4) for p, v in bm.bm_trace(ctx).items()}
     finally:
         bm.bm_destroy(ctx)
+
+
+def tile_pipeline(bm, steps=16384):
+    """The distance-tile pipeline alone, operands resident in shared memory
+    (bm_tile_bench): MMA throughput with the candidate epilogue and without,
+    at k = 50 (MMA N = 64) for n = 64, 128, 256; against the measured BF16
+    peak.  Algorithmic flops count 2 n k per point-centroid pair."""
+    _, bf16_peak, src = measured_peaks()
+    out = {"peak_tflops": bf16_peak, "peak_source": src, "k": 50, "steps_per_cta": steps}
+    for n in (64, 128, 256):
+        for planes in (1, 2):
+            for epi in (0, 1):
+                bm.bm_tile_bench(n, 50, planes, 64, bool(epi))        # warm-up
+                r = bm.bm_tile_bench(n, 50, planes, steps, bool(epi))
+                secs = r["ms"] / 1e3
+                mma = r["grid"] * steps * 2.0 * 128 * 64 * n * (3 if planes == 2 else 1)
+                alg = r["grid"] * steps * 2.0 * 128 * 50 * n
+                out["n%d_%s_%s" % (n, "bf16" if planes == 1 else "bf16x3",
+                                   "epilogue" if epi else "mma_only")] = {
+                    "ms": r["ms"], "mma_tflops": mma / secs / 1e12,
+                    "mma_frac": mma / secs / 1e12 / bf16_peak,
+                    "dist_tflops": alg / secs / 1e12, "tiles_resident": r["tiles"]}
+    return out
 
 
 def launch_latency(bm, torch, dev, jobs=10, warmup=3):

@@ -350,6 +350,27 @@ bm_status bm_assign_rows_noalloc(const float* X_dev, int64_t m, int32_t n,
  * Nothing faults, traps or hangs.  BM_EINVAL for a limit out of range. */
 bm_status bm_selftest_wait_timeout(int32_t timeout_ms, void* stream);
 
+/* Measurement of the distance-tile pipeline alone (the paper has no
+ * counterpart; it separates the tensor-core tile design from the data
+ * movement around it).  One CTA per SM keeps `tiles` 128-row A tiles of n
+ * features (n = 64, 128, 192 or 256) and a block of k centroids (1..128) in
+ * shared memory as BF16 (planes = 1) or split BF16 (planes = 2) operands of
+ * small integers, loaded once; then runs `steps` tile steps, each the
+ * tcgen05.mma of one tile into one of two TMEM accumulators and, with
+ * epilogue != 0, the candidate epilogue of the chunk kernel on it (per row:
+ * the minimum of ||c_j||^2 - 2 x.c_j, then the count of columns within 0.5
+ * of it), the MMA of the next step overlapping the epilogue.  *ms_out = the
+ * launch's time (CUDA events on `stream`); *checksum_out = the sum over CTAs,
+ * steps and rows of argmin + 1024 x count (exact: the operands are integers);
+ * *grid_out = CTAs; *tiles_out = resident tiles (step s uses tile s mod
+ * tiles).  A tile's A operand is tb_a(tile, r, f) = ((7 r + 3 f + 5 tile) mod
+ * 5) - 2 and centroid j's feature f is ((11 j + 13 f) mod 7) - 3.  Allocates
+ * 16 bytes of scratch; blocks until done.  BM_EINVAL for shapes outside the
+ * ranges above. */
+bm_status bm_tile_bench(int32_t n, int32_t k, int32_t planes, int32_t steps,
+                        int32_t epilogue, double* ms_out, uint64_t* checksum_out,
+                        int32_t* grid_out, int32_t* tiles_out, void* stream);
+
 /* Self-check of the K-means++ reseed (Sec. 3.3) across CTAs.  The values the
  * CTAs of a chunk launch hand to each other between grid barriers while they
  * pick a new centre (per-CTA D^2 sums, the candidate rows, the candidates'

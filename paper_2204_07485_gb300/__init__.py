@@ -139,6 +139,8 @@ _SIGS = {
                                       _P(_dbl), _vp]),
     "bm_selftest_wait_timeout": (_i32, [_i32, _vp]),
     "bm_sync_late_reads": (_u64, []),
+    "bm_tile_bench": (_i32, [_i32, _i32, _i32, _i32, _i32, _P(_dbl), _P(_u64), _P(_i32),
+                             _P(_i32), _vp]),
     "bm_server_create": (_i32, [_P(bm_server_config), _P(_vp)]),
     "bm_server_destroy": (_i32, [_vp]),
     "bm_submit": (_i32, [_vp, _P(bm_job), _P(ctypes.c_uint64)]),
@@ -431,6 +433,16 @@ def bm_assign_rows_noalloc(X_dev, m, n, C_dev, mask_dev, k, labels_dev=None,
 def bm_selftest_wait_timeout(timeout_ms=100, stream=None):
     """Status of one grid-barrier wait that runs out (BM_ETIMEOUT expected)."""
     return _lib.bm_selftest_wait_timeout(int(timeout_ms), _stream(stream))
+
+
+def bm_tile_bench(n, k, planes=1, steps=4096, epilogue=True, stream=None):
+    """The distance-tile pipeline with resident operands: dict(ms, checksum,
+    grid, tiles)."""
+    ms, cks, grid, tiles = _dbl(), _u64(), _i32(), _i32()
+    _check(_lib.bm_tile_bench(int(n), int(k), int(planes), int(steps), 1 if epilogue else 0,
+                              ctypes.byref(ms), ctypes.byref(cks), ctypes.byref(grid),
+                              ctypes.byref(tiles), _stream(stream)), "bm_tile_bench")
+    return {"ms": ms.value, "checksum": cks.value, "grid": grid.value, "tiles": tiles.value}
 
 
 def bm_sync_late_reads():
