@@ -539,7 +539,16 @@ def run_ours(args, wl):
         if not args.no_grouped:
             out["grouped"] = grouped(bm, torch, dev)
         if not args.no_serving:
+            # the specified load (200/s, beyond this mix's capacity on one GPU:
+            # latency there is queueing), the capacity (every job at once) and
+            # a load below it (service latency)
             out["serving"] = serving(bm, torch, dev)
+            keep = ("workload", "jobs_per_s", "completed", "failed", "wall_s", "workers",
+                    "latency_ms", "queue_ms", "offered_rps")
+            out["serving_capacity"] = {q: v for q, v in serving(
+                bm, torch, dev, dict(SERVING, rate=None)).items() if q in keep[:6]}
+            out["serving_below_capacity"] = {q: v for q, v in serving(
+                bm, torch, dev, dict(SERVING, rate=120.0, requests=1200)).items() if q in keep}
     if rank == 0:
         print(json.dumps(out))
     return 0
@@ -743,26 +752,28 @@ def grouped(bm, torch, dev, count=256, runs=3, warmup=1):
 # 100 jobs/s: below the measured capacity of this mix on one GB300 (about
 # 117 jobs/s with 4 workers), so latency reflects service, not an
 # ever-growing queue
-SERVING = dict(requests=1000, rate=100.0, chunks=20, workers=4, seed=0,
+# the serving workload: Poisson arrivals at 200 jobs/s, 2,000 jobs; `rate`
+# None submits every job at once (the server's capacity)
+SERVING = dict(requests=2000, rate=200.0, chunks=20, workers=8, seed=0,
                n_set=(8, 28, 68, 128, 384), m_range=(1e4, 5e6), k_range=(2, 100),
                s_max=50_000)
 
 
 def serving(bm, torch, dev, spec=SERVING):
     """Poisson arrivals of whole jobs (m log-uniform, n from the set, k
-    uniform, s = min(m, 50k), FP32 or split-BF16 by a fair coin, 20 chunks +
+    uniform, s = min(m, 50k), FP32 or BF16 + rescore by a fair coin, 20 chunks +
     final assignment), each job's data synthesized on the device from (seed,
     job id) just before it is submitted.  Latency = submission -> results
     ready, on the server's clock."""
     rng = np.random.default_rng(spec["seed"])
     R = spec["requests"]
-    gaps = rng.exponential(1.0 / spec["rate"], size=R)
+    gaps = rng.exponential(1.0 / spec["rate"], size=R) if spec["rate"] else np.zeros(R)
     arrive = np.cumsum(gaps)
     lo, hi = np.log(spec["m_range"][0]), np.log(spec["m_range"][1])
     ms = np.exp(rng.uniform(lo, hi, size=R)).astype(np.int64)
     ns = rng.choice(spec["n_set"], size=R)
     ks = rng.integers(spec["k_range"][0], spec["k_range"][1] + 1, size=R)
-    precs = np.where(rng.random(R) < 0.5, bm.BM_FP32, bm.BM_BF16X3_RESCORE)
+    precs = np.where(rng.random(R) < 0.5, bm.BM_FP32, bm.BM_BF16_RESCORE)
     # data: one seeded 100-component mixture per n, synthesized on the device
     # before the clock starts; job j reads m rows of it from a seeded offset
     import bminputs
@@ -775,7 +786,7 @@ def serving(bm, torch, dev, spec=SERVING):
             pools[int(n)] = bminputs.mixtures.isotropic_blobs_device(
                 int(ms[sel].max()) + max_off, int(n), 100, spec["seed"] + int(n), device=dev)
     torch.cuda.synchronize(dev)
-    sv = bm.bm_server_create(workers=spec["workers"])
+    sv = bm.bm_server_create(workers=spec["workers"], max_queue=max(256, R))
     pending = {}            # ticket -> (job id, X kept alive until the job ends)
     results = [None] * R
     submit_t = np.zeros(R)
@@ -830,7 +841,7 @@ def serving(bm, torch, dev, spec=SERVING):
         return float(np.percentile(a, q)) if len(a) else None
 
     by_prec = {}
-    for name, code in (("fp32", bm.BM_FP32), ("bf16x3", bm.BM_BF16X3_RESCORE)):
+    for name, code in (("fp32", bm.BM_FP32), ("bf16", bm.BM_BF16_RESCORE)):
         sel = [r["latency_s"] * 1e3 for j, r in enumerate(results)
                if r is not None and r["status"] == 0 and precs[j] == code]
         by_prec[name] = {"jobs": len(sel), "p50_ms": pct(sel, 50), "p99_ms": pct(sel, 99)}
@@ -840,7 +851,8 @@ def serving(bm, torch, dev, spec=SERVING):
                if r is not None and r["status"] == 0 and ns[j] == nv]
         if sel:
             run_ms_by_n["n%d" % nv] = round(float(np.mean(sel)), 2)
-    return {"workload": "poisson_%d_per_s_%d_jobs_mixed_shapes" % (spec["rate"], R),
+    return {"workload": ("poisson_%d_per_s_%d_jobs_mixed_shapes" % (spec["rate"], R)
+                         if spec["rate"] else "all_%d_jobs_at_once_mixed_shapes" % R),
             "run_ms_mean_by_n": run_ms_by_n,
             "requests": R, "offered_rps": spec["rate"],
             "submitted_rps": R / max(submit_t[-1], 1e-9), "completed": len(ok),

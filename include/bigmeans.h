@@ -456,6 +456,11 @@ typedef struct bm_server_config {
   int64_t memory_budget;  /* device bytes the admitted jobs' state may hold at
                              once; 0 = half the device memory free at creation  */
   int32_t max_queue;      /* admitted jobs waiting for a worker (>= 1)          */
+  int32_t job_ctas;       /* CTA cap of a job whose cfg.max_ctas is 0 (>= 0;
+                             0 = ceil(SMs / 4)).  It does not depend on
+                             `workers`, so a job's results are those of the
+                             same configuration with max_ctas = this cap run
+                             alone, whatever the server's size               */
 } bm_server_config;
 
 /* What a finished job produced (and how long it took on the host clock). */

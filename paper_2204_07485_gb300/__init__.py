@@ -52,7 +52,7 @@ class bm_fit_report(ctypes.Structure):
 
 class bm_server_config(ctypes.Structure):
     _fields_ = [("workers", ctypes.c_int32), ("memory_budget", ctypes.c_int64),
-                ("max_queue", ctypes.c_int32)]
+                ("max_queue", ctypes.c_int32), ("job_ctas", ctypes.c_int32)]
 
 
 class bm_job_result(ctypes.Structure):
@@ -452,8 +452,8 @@ def bm_sync_late_reads():
 
 
 # ------------------------------------------------------------------ serving
-def bm_server_create(workers=2, memory_budget=0, max_queue=256):
-    cfg = bm_server_config(int(workers), int(memory_budget), int(max_queue))
+def bm_server_create(workers=2, memory_budget=0, max_queue=256, job_ctas=0):
+    cfg = bm_server_config(int(workers), int(memory_budget), int(max_queue), int(job_ctas))
     sv = _vp()
     _check(_lib.bm_server_create(ctypes.byref(cfg), ctypes.byref(sv)), "bm_server_create")
     return sv.value

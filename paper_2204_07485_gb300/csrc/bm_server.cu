@@ -8,9 +8,11 @@
 // refused (BM_EBUSY).  Dispatch: first in, first out; a worker takes the
 // head job once the head's footprint fits in what the running jobs leave of
 // the budget.  A job's chunk kernels use at most SMs / workers CTAs unless
-// the job asks otherwise, so the workers' jobs run side by side on disjoint
-// SMs instead of queueing behind each other's cooperative launches (each
-// would otherwise span the whole GPU).  Each worker thread owns a
+// the job asks otherwise (the server's job_ctas, default ceil(SMs / 4),
+// which does not depend on the worker count, so a job's results do not
+// either), so the workers' jobs run side by side on disjoint SMs instead of
+// queueing behind each other's cooperative launches (each would otherwise
+// span the whole GPU).  Each worker thread owns a
 // non-blocking stream; job state is
 // allocated from the server's stream-ordered memory pool, which keeps freed
 // memory for the next job, so no job synchronises the device.  Results are
@@ -65,7 +67,7 @@ struct DeviceScope {
 struct bm_server {
   bm_server_config cfg{};
   int device = 0;
-  int cap = 0;                  // default CTA cap of a job: SMs / workers
+  int cap = 0;                  // CTA cap of a job without its own: job_ctas
   cudaMemPool_t pool = nullptr;
   std::mutex mu;
   std::condition_variable cv;   // any change: job queued or finished, memory freed, stop
@@ -161,7 +163,8 @@ void worker_main(bm_server* sv) {
 extern "C" {
 
 bm_status bm_server_create(const bm_server_config* cfg, bm_server** out) {
-  if (!cfg || !out || cfg->workers < 1 || cfg->max_queue < 1 || cfg->memory_budget < 0)
+  if (!cfg || !out || cfg->workers < 1 || cfg->max_queue < 1 || cfg->memory_budget < 0 ||
+      cfg->job_ctas < 0)
     return BM_EINVAL;
   *out = nullptr;
   int dev = 0;
@@ -172,7 +175,7 @@ bm_status bm_server_create(const bm_server_config* cfg, bm_server** out) {
   sv->device = dev;
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  sv->cap = (sms + cfg->workers - 1) / cfg->workers;
+  sv->cap = cfg->job_ctas > 0 ? cfg->job_ctas : (sms + 3) / 4;
   if (sv->cfg.memory_budget == 0) {
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { delete sv; return BM_ECUDA; }

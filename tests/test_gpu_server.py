@@ -73,6 +73,34 @@ def test_mix_results_equal_jobs_run_alone(bm):
         assert np.array_equal(host(lab), lab1)
 
 
+def test_results_do_not_depend_on_the_worker_count(bm):
+    # a job without its own CTA cap runs with the server's job_ctas (default
+    # ceil(SMs / 4)) whatever the number of workers: the same bits under
+    # servers of 1 and 6 workers, and those of the job alone with that cap
+    m, n, k, s, T = 60_000, 28, 12, 8_000, 3
+    X = dev(bi.mixtures.isotropic_blobs(m, n, 20, 5)[0])
+    cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=5, precision=1)
+    out = []
+    for workers in (1, 6):
+        sv = bm.bm_server_create(workers=workers)
+        try:
+            C = np.zeros((k, n), np.float32)
+            mask = np.zeros(k, np.uint8)
+            lab = torch.empty(m, dtype=torch.int32, device="cuda:0")
+            r = bm.bm_wait(sv, bm.bm_submit(sv, cfg, X, T, lab, C, mask))
+        finally:
+            bm.bm_server_destroy(sv)
+        assert r["status"] == 0
+        out.append((r["sse"], r["f_opt"], C, mask, host(lab)))
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
+    assert np.array_equal(out[0][2], out[1][2]) and np.array_equal(out[0][4], out[1][4])
+    cap = -(-torch.cuda.get_device_properties(0).multi_processor_count // 4)
+    alone_cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=5, precision=1, max_ctas=cap)
+    sse, f_opt, _, C1, mask1, lab1 = _alone(bm, X, alone_cfg, T)
+    assert out[0][0] == sse and out[0][1] == f_opt and np.array_equal(out[0][2], C1)
+    assert np.array_equal(out[0][4], lab1)
+
+
 def test_admission_wait_cancel_and_callbacks(bm):
     m, n, k, s = 400_000, 28, 25, 50_000
     X = dev(bi.mixtures.isotropic_blobs(m, n, 40, 1)[0])
