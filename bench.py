@@ -707,9 +707,12 @@ def grouped(bm, torch, dev, count=256, runs=3, warmup=1):
                 p["C"].copy_(C0)
                 p["mask"].fill_(1)
 
-    for balance in (1, 0):
+    # (balance, tile mode): cost-balanced partition with autotuned tile shapes,
+    # the same with the fixed lane-per-centroid tile, one CTA per problem
+    for balance, mode in ((1, 0), (1, 1), (0, 1)):
         g = bm.bm_group_create(probs, balance=bool(balance), stream=stream)
         try:
+            bm.bm_group_set_tiles(g, mode)
             info = bm.bm_group_info(g)
             times, res, steps = [], None, 0
             for i in range(warmup + runs):
@@ -721,6 +724,7 @@ def grouped(bm, torch, dev, count=256, runs=3, warmup=1):
                 torch.cuda.synchronize(dev)
                 if i >= warmup:
                     times.append(e0.elapsed_time(e1))
+            shapes = bm.bm_group_tiles(g, count)
         finally:
             bm.bm_group_destroy(g)
         ms = float(np.median(times))
@@ -730,8 +734,13 @@ def grouped(bm, torch, dev, count=256, runs=3, warmup=1):
                  "max_iters": max(iters), "mean_iters": float(np.mean(iters)),
                  "dist_tflops": flops / (ms / 1e3) / 1e12, "grid": info["grid"],
                  "segments": info["segments"]}
-        out["balanced" if balance else "one_cta_per_problem"] = entry
-        if balance:
+        if balance and mode == 0:
+            rows_lanes = sorted({(q["n"], q["k"]) for q, sh in zip(spec, shapes) if sh == 1})
+            entry["row_lane_tiles_for_nk"] = [list(x) for x in rows_lanes]
+        key = ("balanced_autotuned_tiles" if mode == 0 else "balanced_fixed_tile") if balance \
+            else "one_cta_per_problem"
+        out[key] = entry
+        if balance and mode == 0:
             balanced_res = res
     # parity per problem against the same problem alone
     worst, same = 0.0, True

@@ -387,8 +387,9 @@ uint64_t bm_sync_late_reads(void);
 /* ------------------------------------------------------------ grouped Lloyd
  * Many independent Lloyd problems (Sec. 2, stop rule of Sec. 5) -- the
  * chunks of many Big-means jobs, say -- advanced together: each Lloyd step
- * of every unfinished problem is one launch that assigns all their rows and
- * one launch that updates all their centroids, and a recorded CUDA graph
+ * of every unfinished problem is one cooperative launch that assigns all
+ * their rows, waits at a grid barrier and updates all their centroids (two
+ * launches when the grid cannot be co-resident), and a recorded CUDA graph
  * replays the steps.  The rows of all problems are cut into per-CTA ranges
  * of equal cost, so one large problem spreads over many SMs and small ones
  * share an SM; between replays the unfinished problems are cut again over
@@ -436,6 +437,18 @@ bm_status bm_group_run(bm_group* group, bm_group_result* results_host, int32_t* 
  * problems, dynamic shared memory. */
 bm_status bm_group_info(bm_group* group, int32_t* grid_out, int32_t* segments_out,
                         int64_t* smem_out);
+
+/* Tile shape of the assignment's 64-row tiles: mode 0 (default) lets the
+ * group's first run time, for every (n, k) with k <= 16, a lane per centroid
+ * against four lanes per row and keep the faster for those problems; mode 1
+ * keeps a lane per centroid everywhere; mode 2 takes four lanes per row
+ * wherever k <= 16.  The shapes add the same terms in the same order, so the
+ * results do not depend on the mode.  The next bm_group_run applies it. */
+bm_status bm_group_set_tiles(bm_group* group, int32_t mode);
+
+/* The tile shape each problem uses (count entries, host): 0 = a lane per
+ * centroid, 1 = four lanes per row; meaningful after a run. */
+bm_status bm_group_tiles(bm_group* group, int32_t* shapes_host);
 
 /* Frees the group (NULL is a no-op). */
 bm_status bm_group_destroy(bm_group* group);

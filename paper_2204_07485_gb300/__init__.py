@@ -150,6 +150,8 @@ _SIGS = {
     "bm_group_run": (_i32, [_vp, _P(bm_group_result), _P(_i32)]),
     "bm_group_info": (_i32, [_vp, _P(_i32), _P(_i32), _P(_i64)]),
     "bm_group_destroy": (_i32, [_vp]),
+    "bm_group_set_tiles": (_i32, [_vp, _i32]),
+    "bm_group_tiles": (_i32, [_vp, _P(_i32)]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -386,6 +388,19 @@ def bm_group_info(group):
     _check(_lib.bm_group_info(group, ctypes.byref(grid), ctypes.byref(segs),
                               ctypes.byref(smem)), "bm_group_info")
     return {"grid": grid.value, "segments": segs.value, "smem": smem.value}
+
+
+def bm_group_set_tiles(group, mode):
+    """0: autotune the tile shape per (n, k); 1: a lane per centroid; 2: four
+    lanes per row where k <= 16."""
+    _check(_lib.bm_group_set_tiles(group, int(mode)), "bm_group_set_tiles")
+
+
+def bm_group_tiles(group, count):
+    """The tile shape of each problem after a run (0 or 1)."""
+    buf = (_i32 * count)()
+    _check(_lib.bm_group_tiles(group, buf), "bm_group_tiles")
+    return [int(v) for v in buf]
 
 
 def bm_group_destroy(group):

@@ -1,6 +1,6 @@
 // Grouped Lloyd: many independent Lloyd problems (Sec. 2, stop rule of
-// Sec. 5) advanced together, one pair of launches per Lloyd step for all of
-// them (bm_group_create / bm_group_run / bm_group_destroy).
+// Sec. 5) advanced together, one launch per Lloyd step for all of them
+// (bm_group_create / bm_group_run / bm_group_destroy).
 //
 // Work layout.  Every problem's rows form 64-row tiles; the tiles of all
 // problems, problem after problem, form one list, and the list is cut into
@@ -9,17 +9,30 @@
 // many SMs and small ones share an SM.  The part of a CTA's range that lies
 // in one problem is a segment; a segment owns a slot of partial results.
 //
-//   group_assign_kernel  (grid: the CTAs of the partition)
-//     per segment of an unfinished problem: the problem's centroids into
-//     shared memory, then per tile the nearest live centroid of each row
-//     (the tiled FP32 arithmetic of the chunk kernels, lowest index on
-//     ties), the row's label, and the row's (x - c_label) added into
-//     per-row-group accumulators in a fixed row order; at the end the
-//     segment's sums, member counts and objective go to its slot.
-//   group_update_kernel  (grid: one CTA per problem)
-//     per unfinished problem: its slots added in CTA order (the objective in
-//     float64), the stop test, degenerate marking of live centroids without
-//     members, the centroid update unless stopping, and the problem's state.
+//   group_step_kernel  (one cooperative launch per Lloyd step)
+//     assignment: per segment of an unfinished problem: the problem's
+//     centroids into shared memory, then per tile the nearest live centroid
+//     of each row (FP32 direct differences summed over features in order,
+//     lowest index on ties), the row's label, and the row's (x - c_label)
+//     added into per-row-group accumulators in a fixed row order; at the end
+//     the segment's sums, member counts and objective go to its slot;
+//     a grid barrier;
+//     update: CTA b takes problems b, b + G, ...: the problem's slots added
+//     in CTA order (the objective in float64), the stop test, degenerate
+//     marking of live centroids without members, the centroid update unless
+//     stopping, and the problem's state.
+//   (group_assign_kernel + group_update_kernel: the same two phases as two
+//   launches, for a grid that cannot be co-resident -- one CTA per problem
+//   beyond the GPU's capacity -- and for the tile autotuner.)
+//
+// Tile shapes.  A 64-row tile's distances are computed either with one lane
+// per centroid (8 rows per warp, centroids in groups of 32) or, for k <= 16,
+// with four lanes per row (each lane a quarter of the centroids), which
+// keeps lanes busy when k is small.  Both add the same squared differences
+// in the same order and settle ties the same way, and the row's distance is
+// credited to the same thread, so the shape changes no bit of the results.
+// On its first run a group times both shapes on the problems of each (n, k)
+// with k <= 16 and keeps the faster (bm_group_set_tiles can fix a shape).
 //
 // A CUDA graph of a few steps is recorded once and replayed until no
 // problem is left; finished problems cost a flag test per segment, and after
@@ -30,7 +43,9 @@
 #include <algorithm>
 #include <climits>
 #include <cstdint>
+#include <map>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -55,6 +70,7 @@ struct GroupProb {
   int n, npad, k, kpad;
   int ng;            // row groups with private accumulators
   int slot0, slot1;  // the problem's slots [slot0, slot1), in CTA order
+  int rows_tile;     // tile shape: 0 = a lane per centroid, 1 = four lanes per row (k <= 16)
 };
 
 struct GroupSeg {
@@ -86,10 +102,13 @@ struct GroupArgs {
   int count, max_iter;
   double tol;
   int npad_max, kpad_max, acc_floats;   // shared-memory layout
+  uint32_t* bar;              // [2] grid-barrier counters of the step kernel
+  int* status;                // BM_ETIMEOUT when a barrier wait gave up
+  int bar_sel;                // which counter this launch uses
 };
 
 struct GroupSmem {
-  int cenT, stage, acc, cnt, live, lab, red, total;
+  int cenT, stage, acc, cnt, live, lab, dtl, red, total;
 };
 
 __host__ __device__ inline GroupSmem group_smem(int npad_max, int kpad_max, int acc_floats) {
@@ -101,13 +120,61 @@ __host__ __device__ inline GroupSmem group_smem(int npad_max, int kpad_max, int 
   L.cnt = o;   o += align_up(8 * kpad_max * 4, 16);          // [ng][k] counts
   L.live = o;  o += align_up(kpad_max * 4, 16);
   L.lab = o;   o += 64 * 4;
+  L.dtl = o;   o += 64 * 4;                                  // row-lane shape: distances
   L.red = o;   o += 40 * 8;
   L.total = o;
   return L;
 }
 
-__global__ void __launch_bounds__(kGroupThreads)
-group_assign_kernel(GroupArgs a) {
+// Nearest live centroid of the 64 staged rows with four lanes per row (k <=
+// 16): thread t takes row t / 4 and centroids t % 4, t % 4 + 4, ...; each
+// distance is the sum over features in order of the squared differences,
+// as in nearest_tile, and ties go to the lowest index.  The result reaches
+// the thread that nearest_tile would give it (lane r of warp w for row
+// 8w + r), through shared memory; same contract as nearest_tile.
+__device__ __forceinline__ bool nearest_tile_rows(const float* stage, const float* cenT,
+                                                  const int* live, int k, int cs, int n,
+                                                  int rows, int* lab_s, float* d_s,
+                                                  int& bj, float& bd) {
+  const int t = threadIdx.x, r = t >> 2, sub = t & 3;
+  const int nq = (k + 3) >> 2;   // centroids per lane (at most 4)
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int f = 0; f < n; ++f) {
+    const float x = stage[f * 64 + (r ^ swz(f))];
+    const float* cf = cenT + f * cs + sub;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < nq) acc[q] = sq(x - cf[4 * q], acc[q]);
+  }
+  float d = INFINITY;
+  int j = INT_MAX;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int jj = sub + 4 * q;
+    if (q < nq && jj < k && live[jj] && (j == INT_MAX || acc[q] < d)) {
+      d = acc[q];
+      j = jj;
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < 4; o <<= 1) {
+    const float od = __shfl_xor_sync(0xffffffffu, d, o);
+    const int oj = __shfl_xor_sync(0xffffffffu, j, o);
+    if (better(od, oj, d, j)) { d = od; j = oj; }
+  }
+  if (sub == 0) { lab_s[r] = j; d_s[r] = d; }
+  __syncthreads();
+  const int w = t >> 5, l = t & 31;
+  if (l < 8) {
+    bj = lab_s[w * 8 + l];
+    bd = d_s[w * 8 + l];
+    return w * 8 + l < rows;
+  }
+  return false;
+}
+
+// The assignment phase: every segment of this CTA (see the file comment).
+__device__ void group_assign_segments(const GroupArgs& a) {
   extern __shared__ __align__(16) char gsm[];
   const GroupSmem L = group_smem(a.npad_max, a.kpad_max, a.acc_floats);
   float* cenT = reinterpret_cast<float*>(gsm + L.cenT);
@@ -116,6 +183,7 @@ group_assign_kernel(GroupArgs a) {
   int* cnt = reinterpret_cast<int*>(gsm + L.cnt);
   int* live = reinterpret_cast<int*>(gsm + L.live);
   int* lab = reinterpret_cast<int*>(gsm + L.lab);
+  float* dtl = reinterpret_cast<float*>(gsm + L.dtl);
   double* red = reinterpret_cast<double*>(gsm + L.red);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   for (int sg = a.cta_seg[blockIdx.x]; sg < a.cta_seg[blockIdx.x + 1]; ++sg) {
@@ -145,7 +213,11 @@ group_assign_kernel(GroupArgs a) {
       int j;
       float d;
       // (nearest_tile takes the row stride as its kpad: cs >> 5 == kpad >> 5)
-      if (nearest_tile(stage, cenT, live, k, cs, n, rows, j, d)) {
+      const bool mine = p.rows_tile ? nearest_tile_rows(stage, cenT, live, k, cs, n, rows, lab,
+                                                        dtl, j, d)
+                                    : nearest_tile(stage, cenT, live, k, cs, n, rows, j, d);
+      __syncthreads();   // the row-lane shape's results are read before lab is rewritten
+      if (mine) {
         const int r = w * 8 + l;
         lab[r] = j;
         fa += (double)d;
@@ -185,10 +257,14 @@ group_assign_kernel(GroupArgs a) {
 }
 
 __global__ void __launch_bounds__(kGroupThreads)
-group_update_kernel(GroupArgs a) {
-  const int pi = blockIdx.x;
+group_assign_kernel(GroupArgs a) {
+  group_assign_segments(a);
+}
+
+// The update phase of problem pi (one CTA).
+__device__ void group_update_one(const GroupArgs& a, int pi) {
   GroupState* st = a.st + pi;
-  if (__ldcg(&st->done)) return;
+  if (__ldcg(&st->done)) return;   // uniform over the CTA
   const GroupProb p = a.probs[pi];
   const int n = p.n, npad = p.npad, k = p.k;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -248,6 +324,22 @@ group_update_kernel(GroupArgs a) {
       st->it = it + 1;
     }
   }
+  __syncthreads();   // the CTA's next problem reuses the shared scalars
+}
+
+__global__ void __launch_bounds__(kGroupThreads)
+group_update_kernel(GroupArgs a) {
+  group_update_one(a, blockIdx.x);
+}
+
+// One Lloyd step of every unfinished problem in one cooperative launch.
+__global__ void __launch_bounds__(kGroupThreads)
+group_step_kernel(GroupArgs a) {
+  group_assign_segments(a);
+  GridBarrier gb{a.bar + a.bar_sel, a.status, 0u};
+  if (!gb.sync()) return;
+  for (int pi = blockIdx.x; pi < a.count; pi += gridDim.x) group_update_one(a, pi);
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.bar[a.bar_sel ^ 1] = 0u;   // ready for the next launch
 }
 
 __global__ void group_reset_kernel(GroupState* st, int count, int* active) {
@@ -264,6 +356,9 @@ struct bm_group {
   int device = 0;
   cudaStream_t stream = nullptr;
   int count = 0, grid = 0, nseg = 0, max_seg = 0;
+  bool coop = false;            // the grid is co-resident: one launch per step
+  int tiles_mode = 0;           // 0: autotune, 1: lane per centroid, 2: lanes per row (k <= 16)
+  bool tuned = false;           // the tile shapes are chosen
   int nseg_all = 0;             // segments of the partition of every problem
   bool balance = true;
   size_t smem = 0;
@@ -289,11 +384,31 @@ bm_status group_free(bm_group* g) {
   return BM_OK;
 }
 
+// One cooperative launch per Lloyd step (the grid barrier alternates
+// between two counters: step i uses counter i % 2 and clears the other; the
+// step count of a recorded graph is even), else an assignment and an update
+// launch per step.
 bm_status enqueue_steps(bm_group* g, int steps) {
   const int gu = g->count;
   for (int i = 0; i < steps; ++i) {
-    group_assign_kernel<<<g->grid, kGroupThreads, g->smem, g->stream>>>(g->args);
-    group_update_kernel<<<gu, kGroupThreads, 0, g->stream>>>(g->args);
+    if (g->coop) {
+      GroupArgs a = g->args;
+      a.bar_sel = i & 1;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(g->grid);
+      cfg.blockDim = dim3(kGroupThreads);
+      cfg.dynamicSmemBytes = g->smem;
+      cfg.stream = g->stream;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if (cudaLaunchKernelEx(&cfg, group_step_kernel, a) != cudaSuccess) return BM_ECUDA;
+    } else {
+      group_assign_kernel<<<g->grid, kGroupThreads, g->smem, g->stream>>>(g->args);
+      group_update_kernel<<<gu, kGroupThreads, 0, g->stream>>>(g->args);
+    }
   }
   return cudaGetLastError() == cudaSuccess ? BM_OK : BM_ECUDA;
 }
@@ -377,9 +492,71 @@ bm_status group_partition(bm_group* g, const std::vector<char>& active) {
   return BM_OK;
 }
 
+// Tile shapes (see the file comment).  Mode 1 keeps a lane per centroid, mode
+// 2 takes four lanes per row wherever k <= 16; mode 0 times both on the
+// problems of each (n, k) with k <= 16 -- one assignment launch each after a
+// warm-up, CUDA events on the group's stream -- and keeps the faster.  The
+// shapes give the same bits, so the choice only changes the time.
+bm_status group_tune(bm_group* g) {
+  const int count = g->count;
+  std::map<std::pair<int, int>, std::vector<int>> shapes;
+  for (int i = 0; i < count; ++i) {
+    GroupProb& p = g->hp[i];
+    p.rows_tile = (g->tiles_mode == 2 && p.k <= 16) ? 1 : 0;
+    if (g->tiles_mode == 0 && p.k <= 16) shapes[{p.n, p.k}].push_back(i);
+  }
+  if (shapes.empty()) return BM_OK;
+  cudaStream_t st = g->stream;
+  group_reset_kernel<<<(count + 255) / 256, 256, 0, st>>>(g->args.st, count, g->args.active);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaGetLastError() != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return BM_ECUDA;
+  }
+  bm_status rc = BM_OK;
+  for (auto& kv : shapes) {
+    std::vector<char> act(count, 0);
+    for (int i : kv.second) act[i] = 1;
+    float ms[2] = {0.f, 0.f};
+    for (int shape = 0; shape < 2 && rc == BM_OK; ++shape) {
+      for (int i : kv.second) g->hp[i].rows_tile = shape;
+      rc = group_partition(g, act);
+      if (rc != BM_OK) break;
+      group_assign_kernel<<<g->grid, kGroupThreads, g->smem, st>>>(g->args);   // warm-up
+      cudaEventRecord(e0, st);
+      group_assign_kernel<<<g->grid, kGroupThreads, g->smem, st>>>(g->args);
+      cudaEventRecord(e1, st);
+      if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms[shape], e0, e1) != cudaSuccess)
+        rc = BM_ECUDA;
+    }
+    const int pick = ms[1] < ms[0] ? 1 : 0;
+    for (int i : kv.second) g->hp[i].rows_tile = pick;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != BM_OK) cudaGetLastError();
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
+
+bm_status bm_group_set_tiles(bm_group* g, int32_t mode) {
+  if (!g || mode < 0 || mode > 2) return BM_EINVAL;
+  g->tiles_mode = mode;
+  g->tuned = false;
+  return BM_OK;
+}
+
+bm_status bm_group_tiles(bm_group* g, int32_t* shapes_host) {
+  if (!g || !shapes_host) return BM_EINVAL;
+  for (int i = 0; i < g->count; ++i) shapes_host[i] = g->hp[i].rows_tile;
+  return BM_OK;
+}
 
 bm_status bm_group_create(const bm_group_problem* probs, int32_t count, int32_t max_iter,
                           double tol, int32_t balance, void* stream, bm_group** out) {
@@ -406,12 +583,17 @@ bm_status bm_group_create(const bm_group_problem* probs, int32_t count, int32_t 
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return BM_ECUDA; }
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (allow_max_smem(group_assign_kernel) != cudaSuccess) return BM_ECUDA;
-  int per_sm = 0;
+  if (allow_max_smem(group_assign_kernel) != cudaSuccess ||
+      allow_max_smem(group_step_kernel) != cudaSuccess)
+    return BM_ECUDA;
+  int per_sm = 0, per_sm_step = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, group_assign_kernel,
                                                     kGroupThreads, L.total) != cudaSuccess ||
-      per_sm < 1)
+      per_sm < 1 ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_step, group_step_kernel,
+                                                    kGroupThreads, L.total) != cudaSuccess)
     return BM_EUNSUPPORTED;
+  per_sm = std::min(per_sm, std::max(per_sm_step, 1));
 
   bm_group* g = new (std::nothrow) bm_group();
   if (!g) return BM_ENOMEM;
@@ -420,6 +602,7 @@ bm_status bm_group_create(const bm_group_problem* probs, int32_t count, int32_t 
   g->count = count;
   g->balance = balance != 0;
   g->grid = g->balance ? per_sm * sms : count;
+  g->coop = per_sm_step >= 1 && g->grid <= per_sm_step * sms;
   g->smem = L.total;
   g->max_iter = max_iter;
   g->hp.resize(count);
@@ -439,6 +622,7 @@ bm_status bm_group_create(const bm_group_problem* probs, int32_t count, int32_t 
     p.kpad = align_up(q.k, 32);
     int ng = std::min(kGroupThreads / p.npad, acc_floats / (p.k * p.npad));
     p.ng = std::max(1, std::min(ng, 8));
+    p.rows_tile = 0;
     g->tiles[i] = (int)((q.s + 63) / 64);
     g->tile_cost[i] = (double)q.n * (double)(p.kpad / 32 + 1);
   }
@@ -462,7 +646,9 @@ bm_status bm_group_create(const bm_group_problem* probs, int32_t count, int32_t 
   const size_t b_f = al(sizeof(double) * g->max_seg);
   const size_t b_st = al(sizeof(GroupState) * count);
   const size_t b_act = al(sizeof(int));
-  const size_t bytes = b_probs + b_segs + b_offs + b_cta + b_sum + b_cnt + b_f + b_st + b_act;
+  const size_t b_ctl = al(4 * sizeof(int));   // barrier counters [2], status
+  const size_t bytes = b_probs + b_segs + b_offs + b_cta + b_sum + b_cnt + b_f + b_st + b_act +
+                       b_ctl;
   if (cudaMalloc(&g->dev_block, bytes) != cudaSuccess ||
       cudaMallocHost(&g->active_host, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -480,7 +666,14 @@ bm_status bm_group_create(const bm_group_problem* probs, int32_t count, int32_t 
   ga.part_cnt = reinterpret_cast<int*>(base + o); o += b_cnt;
   ga.part_f = reinterpret_cast<double*>(base + o); o += b_f;
   ga.st = reinterpret_cast<GroupState*>(base + o); o += b_st;
-  ga.active = reinterpret_cast<int*>(base + o);
+  ga.active = reinterpret_cast<int*>(base + o); o += b_act;
+  ga.bar = reinterpret_cast<uint32_t*>(base + o);
+  ga.status = reinterpret_cast<int*>(base + o + 2 * sizeof(uint32_t));
+  if (cudaMemset(ga.bar, 0, b_ctl) != cudaSuccess) {
+    cudaGetLastError();
+    group_free(g);
+    return BM_ECUDA;
+  }
   ga.count = count;
   ga.max_iter = max_iter;
   ga.tol = tol;
@@ -500,6 +693,11 @@ bm_status bm_group_create(const bm_group_problem* probs, int32_t count, int32_t 
 bm_status bm_group_run(bm_group* g, bm_group_result* results, int32_t* steps_out) {
   if (!g) return BM_EINVAL;
   cudaStream_t st = g->stream;
+  if (!g->tuned) {
+    const bm_status trc = group_tune(g);
+    if (trc != BM_OK) return trc;
+    g->tuned = true;
+  }
   std::vector<char> active(g->count, 1);
   bm_status rc = group_partition(g, active);
   if (rc != BM_OK) return rc;
@@ -541,6 +739,17 @@ bm_status bm_group_run(bm_group* g, bm_group_result* results, int32_t* steps_out
       return BM_ECUDA;
     }
     const int now = *g->active_host;
+    int status = 0;
+    if (g->coop && cudaMemcpy(&status, g->args.status, sizeof(int), cudaMemcpyDeviceToHost) !=
+                       cudaSuccess) {
+      cudaGetLastError();
+      return BM_ECUDA;
+    }
+    if (status != 0) {   // a barrier wait gave up: clear the counters for the next run
+      cudaMemset(g->args.bar, 0, 4 * sizeof(int));
+      cudaDeviceSynchronize();
+      return (bm_status)status;
+    }
     if (now <= 0) break;
     if (steps >= max_steps + kGroupStepsPerGraph) return BM_ECUDA;   // cannot happen
     if (now < last_active && g->balance) {

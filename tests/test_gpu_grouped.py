@@ -48,8 +48,10 @@ def _oracle(P, C0, max_iter=300):
     return res
 
 
-def _group(bm, probs, balance=True, max_iter=300, stream="own"):
-    """probs: list of (P, C0); returns per problem (result, C, mask, labels), steps."""
+def _group(bm, probs, balance=True, max_iter=300, stream="own", tiles=None, shapes_out=None):
+    """probs: list of (P, C0); returns per problem (result, C, mask, labels), steps.
+    tiles: tile-shape mode (None: the default autotuning); shapes_out (list)
+    receives the shape each problem ran with."""
     specs, keep = [], []
     for P, C0 in probs:
         s, n = P.shape
@@ -64,8 +66,12 @@ def _group(bm, probs, balance=True, max_iter=300, stream="own"):
         stream = torch.cuda.Stream()
     g = bm.bm_group_create(specs, max_iter=max_iter, balance=balance, stream=stream)
     try:
+        if tiles is not None:
+            bm.bm_group_set_tiles(g, tiles)
         res, steps = bm.bm_group_run(g, len(specs))
         info = bm.bm_group_info(g)
+        if shapes_out is not None:
+            shapes_out.extend(bm.bm_group_tiles(g, len(specs)))
     finally:
         bm.bm_group_destroy(g)
     out = [(r, host(C), host(m).astype(bool), host(l)) for r, (_, C, m, l) in zip(res, keep)]
@@ -158,3 +164,27 @@ def test_legacy_stream_without_graphs(bm):
     out, _, _ = _group(bm, probs, stream=None)
     for (P, _), ro, (r, C, mask, labels) in zip(probs, refs, out):
         _check_against_oracle(P, ro, r, C, mask, labels)
+
+
+def test_tile_shapes_give_the_same_bits(bm):
+    """A lane per centroid, four lanes per row (k <= 16) and the autotuned
+    choice: every problem's result identical bit for bit, and the oracle's."""
+    shapes = [(3000, 16, 5, 8, 0), (5000, 32, 10, 14, 1), (2345, 33, 12, 15, 7),
+              (1500, 3, 2, 3, 5), (4100, 64, 16, 20, 9), (2000, 64, 25, 30, 2)]
+    probs = [_problem(*sh) for sh in shapes]
+    refs = [_oracle(P, C0) for P, C0 in probs]
+    runs, used = [], []
+    for mode in (1, 2, 0):
+        got = []
+        out, steps, _ = _group(bm, probs, tiles=mode, shapes_out=got)
+        runs.append(out)
+        used.append(got)
+    assert used[0] == [0] * len(shapes)
+    assert used[1] == [1 if sh[2] <= 16 else 0 for sh in shapes]
+    assert all(u == 0 or sh[2] <= 16 for u, sh in zip(used[2], shapes))
+    for a, b in ((runs[0], runs[1]), (runs[0], runs[2])):
+        for (ra, Ca, ma, la), (rb, Cb, mb, lb) in zip(a, b):
+            assert ra == rb
+            assert np.array_equal(Ca, Cb) and np.array_equal(ma, mb) and np.array_equal(la, lb)
+    for (P, _), res_o, (r, C, mask, labels) in zip(probs, refs, runs[1]):
+        _check_against_oracle(P, res_o, r, C, mask, labels)
