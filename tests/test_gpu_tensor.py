@@ -190,3 +190,21 @@ def test_small_and_ragged_inputs(bm, m, n, k, prec):
     assert bad == 0
     np.testing.assert_allclose(host(dmin), d1, rtol=(n + 2) * 2.0 ** -24, atol=1e-30)
     assert rel(sse, float(d1.sum())) <= OBJ_REL or float(d1.sum()) == 0.0
+
+
+@pytest.mark.parametrize("m,n,k,seed", [(300_007, 128, 50, 21), (100_003, 64, 100, 22),
+                                        (50_000, 96, 17, 23), (70_001, 32, 128, 24)])
+def test_bf16_tile_resident_kernel_equals_split_form(bm, m, n, k, seed):
+    """BF16 (the tile-resident streaming kernel) and split BF16 (the other
+    streaming kernel) settle every row by the same exact FP32 arithmetic:
+    labels, distances and SSE equal bit for bit."""
+    X, C, live = _case(m, n, k, seed)
+    Xd, Cd, md = dev(X), dev(C), dev(live)
+    out = []
+    for prec in (BF16, BF16X3):
+        lab = torch.empty(m, dtype=torch.int32, device="cuda:0")
+        dmin = torch.empty(m, dtype=torch.float32, device="cuda:0")
+        sse, _ = bm.bm_assign_rows_prec(Xd, m, n, Cd, md, k, prec, lab, dmin)
+        out.append((lab, dmin, sse))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
