@@ -530,7 +530,7 @@ def run_ours(args, wl):
         Xs = bminputs.mixtures.scaled_384_device(v8["seed"], m=v8["m"], device=dev)
         extra[v8["name"]] = precision_forms(bm, torch, dev, Xs, v8["m"], v8["n"], v8["k"],
                                             v8["s"], v8["chunks"], v8["seed"], 3, 1, flush,
-                                            forms=("fp32", "bf16x3", "fp8"))
+                                            forms=("fp32", "bf16", "bf16x3", "fp8"))
         del Xs, flush
         torch.cuda.empty_cache()
         out["other_jobs"] = extra

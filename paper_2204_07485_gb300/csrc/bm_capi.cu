@@ -35,7 +35,8 @@ struct Plan {
   int agrid = 0;     // CTAs of the FP32 assign kernel (0: tensor cores only)
   size_t asmem = 0;
   int tc_kb = 0, tc_n16 = 0, tc_ncols = 0, tc_fb = 0, tc_ns = 0, tc_tpc = 0;
-  int tc_planes = 2; // BF16 planes of the chunk kernel's screening (1 or 2)
+  int tc_planes = 2; // planes of the chunk kernel's screening (1 or 2)
+  int tc_fp8 = 0;    // 1: the chunk kernel screens with E4M3 products
   int cap = 0;       // CTA cap of the job (bm_config.max_ctas), 0 = none
 };
 
@@ -50,15 +51,17 @@ static int sm_count() {
 
 // Tensor-core chunk plan: one CTA per SM (TMEM, grid barrier), at least one
 // 128-row tile per CTA, the widest staged feature block that fits.
-static bm_status make_plan_tc(int n, int k, long long s, Plan* out, int cap, int planes) {
+static bm_status make_plan_tc(int n, int k, long long s, Plan* out, int cap, int planes,
+                              bool fp8) {
   if (k > kMaxK || n > 512) return BM_EUNSUPPORTED;
   Plan p;
   p.tc = true;
-  p.tc_planes = planes;
+  p.tc_fp8 = fp8 ? 1 : 0;
+  p.tc_planes = fp8 ? 1 : planes;
   p.generic = true;
   p.npad = align_up(n, 4);
   p.kpad = align_up(k, 32);
-  p.tc_kb = (n + 63) / 64;
+  p.tc_kb = fp8 ? (n + 127) / 128 : (n + 63) / 64;   // 128-byte rows per K block
   p.tc_n16 = align_up(k, 16);
   p.tc_ncols = 32;
   while (p.tc_ncols < p.tc_n16) p.tc_ncols <<= 1;
@@ -75,7 +78,7 @@ static bm_status make_plan_tc(int n, int k, long long s, Plan* out, int cap, int
     // widest staged block first, then a three-slot ring if it still fits
     for (int f : {64, 32, 16, 8, 4}) {
       for (int r : {3, 2}) {
-        smem = chunk_tc_smem(p.npad, k, R, p.tc_n16, f, r, planes);
+        smem = chunk_tc_smem(p.npad, k, R, p.tc_n16, f, r, p.tc_planes);
         if (smem + 2048 <= kSmemLimit) { fb = f; ns = r; break; }   // + static smem
       }
       if (fb) break;
@@ -108,14 +111,15 @@ static bm_status make_plan_simt(int n, int k, long long s, Plan* out, int cap);
 // Kernel family for (n, k, s): the row-in-register path for n <= 32; for
 // wider rows the tensor-core path when asked for (tc) or when the FP32
 // tables do not fit in shared memory, else the tiled FP32 path.  planes: the
-// tensor-core path's screening arithmetic (1: BF16, 2: split BF16).
+// tensor-core path's screening arithmetic (1: BF16, 2: split BF16); fp8:
+// E4M3 screening instead.
 // cap > 0 limits the CTAs of a chunk launch (the job then leaves the other
 // SMs to concurrent jobs); it gives way where shared memory needs more CTAs.
 static bm_status make_plan(int n, int k, long long s, Plan* out, bool tc = false, int cap = 0,
-                           int planes = 2) {
-  if (n > kNpMax && tc) return make_plan_tc(n, k, s, out, cap, planes);
+                           int planes = 2, bool fp8 = false) {
+  if (n > kNpMax && tc) return make_plan_tc(n, k, s, out, cap, planes, fp8);
   const bm_status st = make_plan_simt(n, k, s, out, cap);
-  if (st == BM_EUNSUPPORTED && n > kNpMax) return make_plan_tc(n, k, s, out, cap, planes);
+  if (st == BM_EUNSUPPORTED && n > kNpMax) return make_plan_tc(n, k, s, out, cap, planes, fp8);
   return st;
 }
 
@@ -297,7 +301,7 @@ static ChunkArgs chunk_args(const Workspace& w, const Plan& p, const float* X,
   a.part_sum = w.part_sum; a.part_cnt = w.part_cnt; a.part_f = w.part_f;
   a.blk_cnt = w.blk_cnt; a.ctl = w.ctl; a.stats = w.stats; a.kx = w.kx;
   a.tc_kb = p.tc_kb; a.tc_n16 = p.tc_n16; a.tc_ncols = p.tc_ncols; a.tc_fb = p.tc_fb;
-  a.tc_tpc = p.tc_tpc; a.tc_ns = p.tc_ns; a.tc_planes = p.tc_planes;
+  a.tc_tpc = p.tc_tpc; a.tc_ns = p.tc_ns; a.tc_planes = p.tc_planes; a.tc_fp8 = p.tc_fp8;
   a.Cb = w.Cb; a.sqs = w.sqs; a.Pb = w.Pb;
   return a;
 }
@@ -406,9 +410,13 @@ static bool wants_tc(const bm_config* cfg) {
          cfg->precision == BM_FP8_RESCORE;
 }
 
-// BF16 planes of the tensor-core chunk kernel's screening for a precision
-// form: one for BF16, two (split BF16) for the others, E4M3 included.
-static int chunk_planes(int precision) { return precision == BM_BF16_RESCORE ? 1 : 2; }
+// Screening arithmetic of the tensor-core chunk kernel for a precision
+// form: BF16 products (one plane), E4M3 products, or split BF16 (two planes)
+// for the others.
+static int chunk_planes(int precision) {
+  return precision == BM_BF16_RESCORE || precision == BM_FP8_RESCORE ? 1 : 2;
+}
+static bool chunk_fp8(int precision) { return precision == BM_FP8_RESCORE; }
 
 // Screening arithmetic of the tensor-core final assignment for a precision
 // form.
@@ -428,7 +436,7 @@ bm_status ctx_create(const bm_config* cfg, const float* X_dev, cudaStream_t stre
   c->X = X_dev;
   c->stream = stream;
   st = make_plan(cfg->n, cfg->k, cfg->s, &c->plan, wants_tc(cfg), cfg->max_ctas,
-                 chunk_planes(cfg->precision));
+                 chunk_planes(cfg->precision), chunk_fp8(cfg->precision));
   if (st != BM_OK) { delete c; return st; }
   c->ws.pool = pool;
   c->ws.pool_stream = stream;
@@ -446,7 +454,7 @@ bm_status ctx_footprint(const bm_config* cfg, size_t* bytes) {
   if (st != BM_OK) return st;
   Plan p;
   st = make_plan(cfg->n, cfg->k, cfg->s, &p, wants_tc(cfg), cfg->max_ctas,
-                 chunk_planes(cfg->precision));
+                 chunk_planes(cfg->precision), chunk_fp8(cfg->precision));
   if (st != BM_OK) return st;
   Workspace w;
   w.dry = true;

@@ -29,10 +29,21 @@
 //
 // K-means++ uses the same pieces: D^2 is the assignment's distance, and the
 // candidates' distances come from the staged sweep.
+//
+// Screening arithmetic (tc_planes, tc_fp8): BF16 products (one plane), split
+// BF16 (two planes), or E4M3 products with FP32 accumulation in K blocks of
+// 128 features.  In the E4M3 form each own row is scaled by the power of two
+// that brings its largest magnitude into [128, 256), and every centroid of
+// the chunk by one power of two cs chosen the same way from M, the largest
+// magnitude over the sample rows and the live incumbent centroids (every
+// centroid the chunk produces is a sample row or a mean of sample rows, so
+// |c_f| <= M up to rounding and nothing saturates).  The scales are exact,
+// so the epilogue scales the accumulator back with one factor per row.
 #include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include "bm_chunk_common.cuh"
@@ -50,13 +61,13 @@ constexpr int kTccWarps = kTccThreads / 32;
 struct TccLayout {
   int ring_a, ring_b, ring_slot, stage_c, sstride;
   int region, cmask, lab, dmin, part4, dc, order, cnt, start, cur, wc, cand, live, lidx, cc,
-      xx, xm, mlist, red, bars, holder, total;
+      xx, rsc, xm, mlist, red, bars, holder, total;
 };
 
 // Shared-memory layout.  The region at offset 0 holds either the ns-slot
-// MMA ring (A block: 128 rows x 64 BF16 x `planes` planes; B block: n16 rows
-// x 64 BF16 x `planes` planes) or the staged feature block of the exact passes (R rows
-// and k centroid rows of fb floats, row stride fb + 4).
+// MMA ring (A block: 128 rows x 128 bytes x `planes` planes; B block: n16
+// rows x 128 bytes x `planes` planes) or the staged feature block of the
+// exact passes (R rows and k centroid rows of fb floats, row stride fb + 4).
 __host__ __device__ inline TccLayout tcc_layout(int npad, int k, int R, int n16, int fb,
                                                 int ns, int planes) {
   TccLayout L;
@@ -83,6 +94,7 @@ __host__ __device__ inline TccLayout tcc_layout(int npad, int k, int R, int n16,
   L.lidx = o;   o += align_up((k + 1) * 4, 16);
   L.cc = o;     o += align_up(n16 * 4, 16);
   L.xx = o;     o += align_up(R * 4, 16);                // ||x||^2 of own rows
+  L.rsc = o;    o += align_up(R * 4, 16);                // E4M3: 1 / scale of own rows
   L.xm = o;     o += 2 * kTccM * 4;                      // column-half minima
   L.mlist = o;  o += align_up((R + 1) * 4, 16);          // multi-candidate rows
   L.red = o;    o += 80 * 8;
@@ -112,6 +124,7 @@ struct TccS {
   int* lidx;
   float* cc;          // [n16] ||c_j||^2, +inf if not live
   float* xx;          // [R] ||x||^2 of own rows
+  float* rsc;         // [R] E4M3 form: 1 / scale of own rows (a power of two)
   float* xm;          // [2][128]
   int* mlist;         // [R + 1], count at [R]
   double* red;
@@ -129,7 +142,7 @@ struct TccPipe {
 };
 
 struct TccBound {
-  float b0, b1;       // 2 eps max ||c||, (n + 2) 2^-22 max ||c||^2
+  float b0, b1;       // 2 eps max ||c|| (+ the E4M3 underflow term), (n + 2) 2^-22 max ||c||^2
 };
 
 __device__ __forceinline__ void fence_proxy_async_global() {
@@ -137,12 +150,29 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 }
 
 // ---------------------------------------------------------------- centroids
-// Writes centroid value v of (j, f) into the BF16 planes.
-__device__ __forceinline__ void put_cb(unsigned char* Cb, int n16, int j, int f, float v) {
+// E4M3 form: the chunk's centroid scale cs, 1 / cs and M (the largest
+// magnitude it was chosen from), the same in every CTA.
+__device__ __forceinline__ float* fp8_cscale() {
+  __shared__ float v[3];
+  return v;
+}
+
+// Writes centroid value v of (j, f) into the global centroid operand: the
+// BF16 planes (hi, lo), or the E4M3 byte of v cs.
+__device__ __forceinline__ void put_cb(const ChunkArgs& a, int j, int f, float v) {
+  const int n16 = a.tc_n16;
+  if (a.tc_fp8) {
+    const int w = f & 127;
+    const int off = (f >> 7) * (n16 * 128) + (j >> 3) * 1024 + (j & 7) * 128 +
+                    (((w >> 4) ^ (j & 7)) << 4) + (w & 15);
+    a.Cb[off] = (unsigned char)__nv_cvt_float_to_fp8(v * fp8_cscale()[0], __NV_SATFINITE,
+                                                     __NV_E4M3);
+    return;
+  }
   const int off = (f >> 6) * (2 * n16 * 128) + sw128_offset(j, f & 63);
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  *reinterpret_cast<__nv_bfloat16*>(Cb + off) = h;
-  *reinterpret_cast<__nv_bfloat16*>(Cb + off + n16 * 128) =
+  *reinterpret_cast<__nv_bfloat16*>(a.Cb + off) = h;
+  *reinterpret_cast<__nv_bfloat16*>(a.Cb + off + n16 * 128) =
       __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
@@ -157,7 +187,7 @@ __device__ __forceinline__ void publish32(const ChunkArgs& a, int j, int q, floa
   const bool on = f < a.n;
   if (on) {
     if (write_c) a.C[(size_t)j * a.npad + f] = v;
-    put_cb(a.Cb, a.tc_n16, j, f, v);
+    put_cb(a, j, f, v);
   }
   float sq = on ? v * v : 0.f;
   sq += __shfl_xor_sync(0xffffffffu, sq, 1);
@@ -190,10 +220,20 @@ __device__ void load_norms(const ChunkArgs& a, const TccS& S, TccBound* bd) {
   for (int i = 0; i < kTccWarps; ++i) mx = fmaxf(mx, (float)S.red[i]);
   // one BF16 rounding per operand, or for split BF16 products the dropped
   // lo*lo term and the second roundings; plus FP32 accumulation over n
-  // products
-  const float eps = a.tc_planes == 1 ? 1.01f * 0x1.0p-7f + (float)(a.n + 16) * 0x1.0p-22f
-                                     : 3.1f * 0x1.0p-16f + (float)(3 * a.n + 16) * 0x1.0p-22f;
-  bd->b0 = 2.f * eps * sqrtf(mx) * 1.0001f;
+  // products.  E4M3: each scaled operand is within 2^-4 relative or 2^-10
+  // absolute (the subnormal spacing) of its value, so with row scale
+  // 2^(7 - e) (2^e <= max|x_f| <= ||x||) and centroid scale cs (M cs < 256)
+  //   |x~ c~ - x c| <= ||x|| ||c|| (2^-3 + 2^-8 + 1.07 2^-17 sqrt n)
+  //                  + ||x|| M (1.07 2^-17 sqrt n + n 2^-34),
+  // plus the accumulation over n products of at most 1.14 ||x|| ||c||.
+  const float rn = sqrtf((float)a.n);
+  const float eps =
+      a.tc_fp8 ? 0x1.0p-3f + 0x1.0p-8f + 1.07f * 0x1.0p-17f * rn +
+                     1.14f * (float)(a.n + 16) * 0x1.0p-22f
+      : a.tc_planes == 1 ? 1.01f * 0x1.0p-7f + (float)(a.n + 16) * 0x1.0p-22f
+                         : 3.1f * 0x1.0p-16f + (float)(3 * a.n + 16) * 0x1.0p-22f;
+  const float tau = a.tc_fp8 ? 1.01f * (1.07f * 0x1.0p-17f * rn + (float)a.n * 0x1.0p-34f) : 0.f;
+  bd->b0 = 2.f * (eps * sqrtf(mx) + (a.tc_fp8 ? tau * fp8_cscale()[2] : 0.f)) * 1.0001f;
   bd->b1 = (float)(a.n + 2) * 0x1.0p-22f * mx;
   __syncthreads();
 }
@@ -204,6 +244,80 @@ __device__ void load_norms(const ChunkArgs& a, const TccS& S, TccBound* bd) {
 // contiguous block of 16 KB per plane (the hi plane, then for split BF16 the
 // lo plane) in the 128-byte-swizzled K-major layout of the MMA; ||x||^2 of
 // every own row -> S.xx.
+// E4M3 form: own rows -> E4M3 tiles (K blocks of 128 features), a warp per
+// row: lane l holds the 8-feature units l and l + 32 (npad <= 512), so the
+// row's largest magnitude and its norm are warp reductions.  Row i is scaled
+// by 1 / rsc[i], the power of two that brings that magnitude into
+// [128, 256).  Returns the largest magnitude over own rows (every thread).
+__device__ float tcc_convert_own_fp8(const ChunkArgs& a, const TccS& S, int r0, int nrows) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, kb = a.tc_kb, npad = a.npad;
+  constexpr int blk = kTccM * 128;
+  unsigned char* base = a.Pb + (size_t)blockIdx.x * a.tc_tpc * kb * blk;
+  float cmax = 0.f;
+  for (int t0 = 0; t0 < nrows; t0 += kTccM) {
+    const int rows = min(kTccM, nrows - t0);
+    unsigned char* dst = base + (size_t)(t0 / kTccM) * kb * blk;
+    for (int r = w; r < kTccM; r += kTccWarps) {   // every row of the tile: padding rows are zero
+      float v[2][8];
+      float mx = 0.f, q = 0.f;
+#pragma unroll
+      for (int uu = 0; uu < 2; ++uu) {
+        const int f0 = (l + 32 * uu) * 8;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[uu][u] = 0.f;
+        if (r < rows && f0 < npad) {
+          const float4* p = reinterpret_cast<const float4*>(a.P + (size_t)(r0 + t0 + r) * npad + f0);
+          const float4 x0 = __ldcg(p);
+          v[uu][0] = x0.x; v[uu][1] = x0.y; v[uu][2] = x0.z; v[uu][3] = x0.w;
+          if (f0 + 4 < npad) {
+            const float4 x1 = __ldcg(p + 1);
+            v[uu][4] = x1.x; v[uu][5] = x1.y; v[uu][6] = x1.z; v[uu][7] = x1.w;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          mx = fmaxf(mx, fabsf(v[uu][u]));
+          q = fmaf(v[uu][u], v[uu][u], q);
+        }
+      }
+      mx = warp_max_f32(mx);
+      q = warp_sum_f32(q);
+      const int e2 = (mx > 0.f && mx <= 3.0e38f) ? max(ilogbf(mx), -119) : 7;
+      const float inv = ldexpf(1.f, e2 - 7);
+      if (l == 0 && r < rows) {
+        S.xx[t0 + r] = q;
+        S.rsc[t0 + r] = inv;
+      }
+      cmax = fmaxf(cmax, mx);
+#pragma unroll
+      for (int uu = 0; uu < 2; ++uu) {
+        const int f0 = (l + 32 * uu) * 8;
+        if (f0 >= kb * 128) continue;
+        uint32_t wd[2] = {0u, 0u};
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const uint32_t byte =
+              (uint32_t)__nv_cvt_float_to_fp8(v[uu][u] / inv, __NV_SATFINITE, __NV_E4M3);
+          wd[u >> 2] |= byte << (8 * (u & 3));
+        }
+        const int wi = f0 & 127;
+        const int off = (f0 >> 7) * blk + (r >> 3) * 1024 + (r & 7) * 128 +
+                        (((wi >> 4) ^ (r & 7)) << 4) + (wi & 8);
+        *reinterpret_cast<uint2*>(dst + off) = make_uint2(wd[0], wd[1]);
+      }
+    }
+  }
+  fence_proxy_async_global();   // the tiles are read back by bulk copies
+  __syncthreads();
+  const float m = warp_max_f32(cmax);
+  if (l == 0) S.red[w] = m;
+  __syncthreads();
+  float all = 0.f;
+  for (int i = 0; i < kTccWarps; ++i) all = fmaxf(all, (float)S.red[i]);
+  __syncthreads();
+  return all;
+}
+
 __device__ void tcc_convert_own(const ChunkArgs& a, const TccS& S, int r0, int nrows) {
   const int tid = threadIdx.x, kb = a.tc_kb, npad = a.npad;
   const int blk = a.tc_planes * kTccM * 128;
@@ -278,11 +392,13 @@ __device__ bool tcc_pass_a(const ChunkArgs& a, const TccS& S, int r0, int nrows,
                            const TccBound& bd, uint32_t tmem, TccPipe& pp) {
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int kb = a.tc_kb, N = a.tc_n16, ns = S.ns;
-  const uint32_t idesc = idesc_bf16_f32(kTccM, N);
+  const bool fp8 = a.tc_fp8 != 0;
+  const uint32_t idesc = fp8 ? idesc_e4m3_f32(kTccM, N) : idesc_bf16_f32(kTccM, N);
   const float e_d = (float)(a.n + 4) * 0x1.0p-22f;
   const int planes = a.tc_planes;
   const uint32_t abytes = planes * kTccM * 128, bbytes = planes * N * 128;
-  const size_t cb_stride = 2 * (size_t)N * 128;   // the global centroid planes keep both
+  // the global BF16 centroid planes keep both (hi, lo); E4M3 has one
+  const size_t cb_stride = (fp8 ? 1 : 2) * (size_t)N * 128;
   const unsigned char* pbase = a.Pb + (size_t)blockIdx.x * a.tc_tpc * kb * abytes;
   const int ntl = (nrows + kTccM - 1) / kTccM;
   const uint32_t first = pp.ring, total = (uint32_t)(ntl * kb);
@@ -319,8 +435,12 @@ __device__ bool tcc_pass_a(const ChunkArgs& a, const TccS& S, int r0, int nrows,
         const uint64_t db = sdesc_sw128(smem_u32(sa + S.ring_a));
         const uint64_t alo = (uint64_t)((kTccM * 128) >> 4), blo = (uint64_t)((N * 128) >> 4);
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
+        for (int ks = 0; ks < 4; ++ks) {   // 32 bytes of K per step: 16 BF16 or 32 E4M3
           const uint64_t off = (uint64_t)((ks * 32) >> 4);
+          if (fp8) {
+            tc_mma_e4m3(tmem, da + off, db + off, idesc, (b > 0 || ks > 0) ? 1u : 0u);
+            continue;
+          }
           tc_mma_bf16(tmem, da + off, db + off, idesc, (b > 0 || ks > 0) ? 1u : 0u);
           if (planes == 2) {
             tc_mma_bf16(tmem, da + off, db + blo + off, idesc, 1u);
@@ -342,13 +462,16 @@ __device__ bool tcc_pass_a(const ChunkArgs& a, const TccS& S, int r0, int nrows,
     const int r = qd * 32 + lane;
     const bool valid = r < rows;
     const uint32_t lane_base = tmem + ((uint32_t)(qd * 32) << 16);
+    // -2 x.c from the accumulator: E4M3 scales it back by 1 / (row scale x
+    // cs), exact powers of two
+    const float g = fp8 && valid ? -2.f * S.rsc[t0 + r] * fp8_cscale()[1] : -2.f;
     float m1 = INFINITY;
     for (int c0 = hf * 32; c0 < N; c0 += 64) {
       float acc[32];
       tmem_ld32(lane_base + (uint32_t)c0, acc);
 #pragma unroll
       for (int u = 0; u < 32; ++u)
-        if (c0 + u < N) m1 = fminf(m1, fmaf(-2.f, acc[u], S.cc[c0 + u]));
+        if (c0 + u < N) m1 = fminf(m1, fmaf(g, acc[u], S.cc[c0 + u]));
     }
     S.xm[hf * kTccM + r] = m1;
     __syncthreads();
@@ -363,7 +486,7 @@ __device__ bool tcc_pass_a(const ChunkArgs& a, const TccS& S, int r0, int nrows,
       uint32_t bits = 0u;
 #pragma unroll
       for (int u = 0; u < 32; ++u)
-        if (c0 + u < N && S.cc[c0 + u] < INFINITY && fmaf(-2.f, acc[u], S.cc[c0 + u]) <= thr)
+        if (c0 + u < N && S.cc[c0 + u] < INFINITY && fmaf(g, acc[u], S.cc[c0 + u]) <= thr)
           bits |= 1u << u;
       if (valid) S.cmask[i * 4 + (c0 >> 5)] = bits;
     }
@@ -588,20 +711,28 @@ __device__ void tcc_sweep(const ChunkArgs& a, const TccS& S, int r0, int nrows, 
       else p4[i] = acc;
     }
     if (update) {
-      // fw threads per group, one feature each; groups take centroids in turn
-      const int ng = kTccThreads / fw;
-      const int g = threadIdx.x / fw, ff = threadIdx.x - g * fw, f = f0 + ff;
+      // fw / 4 threads per group, four consecutive features each (one
+      // float4); groups take centroids in turn.  Each feature's sum runs
+      // over the members in ascending order.  Padding features sum to zero.
+      const int q4 = fw >> 2, ng = kTccThreads / q4;
+      const int g = threadIdx.x / q4, c4 = threadIdx.x - g * q4, f = f0 + 4 * c4;
       if (g < ng && f < n) {
         const int nl = S.lidx[k];
         for (int q = g; q < nl; q += ng) {
           const int j = S.lidx[q];
-          const float c = S.sC[j * ss + ff];
-          float sum = 0.f;
+          const float4 c = *reinterpret_cast<const float4*>(S.sC + j * ss + 4 * c4);
+          float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
           const int e1 = S.start[j + 1];
 #pragma unroll 4
-          for (int e = S.start[j]; e < e1; ++e) sum += S.sP[S.order[e] * ss + ff] - c;
+          for (int e = S.start[j]; e < e1; ++e) {
+            const float4 v = *reinterpret_cast<const float4*>(S.sP + S.order[e] * ss + 4 * c4);
+            sum.x += v.x - c.x;
+            sum.y += v.y - c.y;
+            sum.z += v.z - c.z;
+            sum.w += v.w - c.w;
+          }
           if (BM_GUARD(j >= 0 && j < k, &a.ctl->status))
-            a.part_sum[((size_t)b * k + j) * npad + f] = sum;
+            *reinterpret_cast<float4*>(a.part_sum + ((size_t)b * k + j) * npad + f) = sum;
         }
       }
     }
@@ -709,7 +840,7 @@ __device__ void tcc_reduce(const ChunkArgs& a, const TccS& S, bool stop) {
     if (on) {
       c = __ldcg(a.C + (size_t)j * npad + f) + mine / (float)cnt;
       a.C[(size_t)j * npad + f] = c;
-      put_cb(a.Cb, a.tc_n16, j, f, c);
+      put_cb(a, j, f, c);
     }
     float sq = on ? c * c : 0.f;
     sq += __shfl_xor_sync(0xffffffffu, sq, 1);
@@ -930,6 +1061,60 @@ __device__ void tcc_gather(const ChunkArgs& a, const TccS& S, int r0, int nrows)
   __syncthreads();
 }
 
+// ---------------------------------------------------------------- incumbent
+// The (centroid, 32-feature unit) pairs of C' <- C that CTA b publishes:
+// q = b * warps + w, then every gridDim.x * warps.
+__device__ void tcc_publish_incumbent(const ChunkArgs& a, const TccS& S, const float* src,
+                                      bool full) {
+  const int k = a.k, nch = (a.npad + 31) >> 5;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int q = blockIdx.x * kTccWarps + w; q < k * nch; q += gridDim.x * kTccWarps) {
+    const int j = q / nch, ch = q - j * nch, f = ch * 32 + l;
+    const float v = f < a.npad ? __ldcg(src + (size_t)j * a.npad + f) : 0.f;
+    publish32(a, j, ch, v, full);
+  }
+  if (full && blockIdx.x == 0)
+    for (int j = threadIdx.x; j < k; j += blockDim.x) a.mask[j] = S.live[j];
+  fence_proxy_async_global();
+}
+
+// Largest magnitude over the live incumbent values of those same pairs
+// (every thread gets it).
+__device__ float tcc_incumbent_max(const ChunkArgs& a, const TccS& S, const float* src) {
+  const int k = a.k, nch = (a.npad + 31) >> 5;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  float m = 0.f;
+  for (int q = blockIdx.x * kTccWarps + w; q < k * nch; q += gridDim.x * kTccWarps) {
+    const int j = q / nch, f = (q - j * nch) * 32 + l;
+    if (S.live[j] && f < a.n) m = fmaxf(m, fabsf(__ldcg(src + (size_t)j * a.npad + f)));
+  }
+  m = warp_max_f32(m);
+  __syncthreads();
+  if (l == 0) S.red[w] = m;
+  __syncthreads();
+  float all = 0.f;
+  for (int i = 0; i < kTccWarps; ++i) all = fmaxf(all, (float)S.red[i]);
+  __syncthreads();
+  return all;
+}
+
+// E4M3 centroid scale of the chunk from the CTAs' shares of M (after the
+// grid barrier): cs = 2^(7 - floor(log2 M)), so M cs lies in [128, 256).
+__device__ void tcc_set_cscale(const double* mpart) {
+  if (threadIdx.x < 32) {
+    float m = 0.f;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) m = fmaxf(m, (float)__ldcg(mpart + i));
+    m = warp_max_f32(m);
+    if (threadIdx.x == 0) {
+      const int e2 = (m > 0.f && m <= 3.0e38f) ? max(ilogbf(m), -119) : 7;
+      fp8_cscale()[0] = ldexpf(1.f, 7 - e2);
+      fp8_cscale()[1] = ldexpf(1.f, e2 - 7);
+      fp8_cscale()[2] = m;
+    }
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------- kernel
 __global__ void __launch_bounds__(kTccThreads, 1) chunk_tc_kernel(ChunkArgs a) {
   extern __shared__ __align__(1024) unsigned char tcc_raw[];
@@ -955,6 +1140,7 @@ __global__ void __launch_bounds__(kTccThreads, 1) chunk_tc_kernel(ChunkArgs a) {
   S.lidx = reinterpret_cast<int*>(base + L.lidx);
   S.cc = reinterpret_cast<float*>(base + L.cc);
   S.xx = reinterpret_cast<float*>(base + L.xx);
+  S.rsc = reinterpret_cast<float*>(base + L.rsc);
   S.xm = reinterpret_cast<float*>(base + L.xm);
   S.mlist = reinterpret_cast<int*>(base + L.mlist);
   S.red = reinterpret_cast<double*>(base + L.red);
@@ -993,30 +1179,36 @@ __global__ void __launch_bounds__(kTccThreads, 1) chunk_tc_kernel(ChunkArgs a) {
 
   const bool full = (a.phases & kPhaseKeep) != 0;
   const bool work = (a.phases & (kPhaseKpp | kPhaseLloyd)) != 0;
+  const float* csrc = full ? a.Cinc : a.C;
   if (work) {
     // C' <- C (Alg. 1): the working copy starts from the incumbent; its
-    // planes and slice norms are rebuilt by all CTAs together
-    const float* src = full ? a.Cinc : a.C;
+    // planes and slice norms are rebuilt by all CTAs together (E4M3: once
+    // the chunk's centroid scale is known, below)
     const uint8_t* msrc = full ? a.mask_inc : a.mask;
     for (int j = threadIdx.x; j < k; j += blockDim.x)
       S.live[j] = __ldcg(reinterpret_cast<const unsigned char*>(msrc) + j) != 0;
     build_live_list(S.live, S.lidx, k);
-    const int nch = (a.npad + 31) >> 5;
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (int q = blockIdx.x * kTccWarps + w; q < k * nch; q += gridDim.x * kTccWarps) {
-      const int j = q / nch, ch = q - j * nch, f = ch * 32 + l;
-      const float v = f < a.npad ? __ldcg(src + (size_t)j * a.npad + f) : 0.f;
-      publish32(a, j, ch, v, full);
-    }
-    if (full && blockIdx.x == 0)
-      for (int j = threadIdx.x; j < k; j += blockDim.x) a.mask[j] = S.live[j];
-    fence_proxy_async_global();
+    if (!a.tc_fp8) tcc_publish_incumbent(a, S, csrc, full);
   }
   phase_tick(a, 0, &tclk);
   if (a.phases & kPhaseGather) tcc_gather(a, S, r0, nrows);
-  if (work) tcc_convert_own(a, S, r0, nrows);
-  if (work) {
+  if (work && a.tc_fp8) {
+    // M = the largest magnitude over the sample rows and the live incumbent
+    // centroids: each CTA's share (own rows, the incumbent values it
+    // publishes), exchanged through one grid barrier
+    double* MPART = a.part_f + (size_t)(kMaxTrials + 1) * gridDim.x;
+    const float mine = fmaxf(tcc_convert_own_fp8(a, S, r0, nrows), tcc_incumbent_max(a, S, csrc));
+    if (threadIdx.x == 0) MPART[blockIdx.x] = (double)mine;
     ok = gb.sync();
+    if (ok) {
+      tcc_set_cscale(MPART);
+      tcc_publish_incumbent(a, S, csrc, full);
+    }
+  } else if (work) {
+    tcc_convert_own(a, S, r0, nrows);
+  }
+  if (work) {
+    ok = ok && gb.sync();
     if (ok) load_norms(a, S, &bd);
   }
   phase_tick(a, 1, &tclk);

@@ -96,17 +96,20 @@ struct ChunkArgs {
   // [1 + 2G, 1 + 2G + kMaxTrials) the candidate rows' tags
   unsigned long long* kx;
   // tensor-core chunk kernel (rows wider than 32 features)
-  int tc_kb;              // 64-feature K blocks
+  int tc_kb;              // K blocks of 128-byte rows: 64 BF16 or 128 E4M3 features
   int tc_n16;             // MMA N: k rounded up to 16
   int tc_ncols;           // TMEM columns
   int tc_fb;              // features per staged block of the exact passes
   int tc_tpc;             // 128-row tiles per CTA: ceil(rows_per_cta / 128)
   int tc_ns;              // MMA ring slots (2 or 3)
-  int tc_planes;          // BF16 planes of the screening products: 1 (BF16) or
+  int tc_planes;          // planes of the screening products: 1 (BF16 or E4M3) or
                           // 2 (split BF16: hi*hi + hi*lo + lo*hi)
-  unsigned char* Cb;      // [tc_kb][2][tc_n16][128 B] centroid BF16 planes (hi, lo), swizzled
+  int tc_fp8;             // 1: E4M3 screening (rows scaled per row, centroids by
+                          // one power of two per chunk), tc_planes = 1
+  unsigned char* Cb;      // BF16: [tc_kb][2][tc_n16][128 B] centroid planes (hi, lo);
+                          // E4M3: [tc_kb][tc_n16][128 B]; swizzled
   float* sqs;             // [k][ceil(npad / 8)] squared norms of 8-feature slices of C
-  unsigned char* Pb;      // [G][tc_tpc][tc_kb][tc_planes][128][128 B] own-row BF16 planes, swizzled
+  unsigned char* Pb;      // [G][tc_tpc][tc_kb][tc_planes][128][128 B] own-row planes, swizzled
 };
 
 struct AssignArgs {

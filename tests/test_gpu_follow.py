@@ -5,9 +5,13 @@ draws of the benchmark workloads:
   * m = 20,000, n = 2, k = 10, s = 2,000, seed 0, all 20 chunks;
   * m = 1e6, n = 28, k = 25, s = 50,000, seed 0, all 100 chunks (FP32);
   * m = 1e7, n = 128, k = 50, s = 50,000, seed 0: all 100 chunks of the
-    timed job in its timed form (split BF16 + exact rescoring; fewer with
+    timed job in its timed form (BF16 + exact rescoring; fewer with
     BM_FOLLOW_C3_CHUNKS), then the final assignment of all 1e7 rows against
-    the oracle's over every row.
+    the oracle's over every row;
+  * m = 2e6, n = 384, k = 100, s = 50,000, seed 0 (per-feature scales
+    log-uniform in [0.1, 10]) in the E4M3 form: the first 10 chunks (more or
+    fewer with BM_FOLLOW_FP8_CHUNKS), then the final assignment of all 2e6
+    rows.
 
 The GPU runs alone: each chunk is one bm_fit_chunk call, and only its
 outcome is read.  After every chunk the oracle must reproduce that outcome,
@@ -30,6 +34,7 @@ from gpu_helpers import OBJ_REL, dev, host, labels_match, rel, require_gpu, torc
 pytestmark = pytest.mark.gpu
 
 C3_CHUNKS = int(os.environ.get("BM_FOLLOW_C3_CHUNKS", "100"))
+FP8_CHUNKS = int(os.environ.get("BM_FOLLOW_FP8_CHUNKS", "10"))
 
 
 @pytest.fixture(scope="module")
@@ -107,21 +112,20 @@ def test_c2_hepmass_like_seed0_all_chunks_free_running(bm):
     assert len(followed) <= 10
 
 
-def test_c3_chunks_and_full_final_assignment(bm):
-    m, n, k, s, seed = 10_000_000, 128, 50, 50_000, 0
-    T = C3_CHUNKS
-    Xd = bi.mixtures.gas_sensor_like_device(seed, m=m, n=n, device="cuda:0")
+def _follow_device_workload(bm, Xd, m, n, k, s, T, seed, prec, name, max_followed):
+    """Free-running chunks of a device-generated workload against the
+    oracle (which reads only the chunk rows: a compact copy with remapped
+    draws), then the final assignment of all m rows from the oracle's
+    incumbent (equal to the GPU's within the parity tolerance) against the
+    oracle's over every row."""
     draws = [bi.chunk_draws(seed, t, m, s, k) for t in range(T)]
-    # the oracle reads the chunk rows only: a compact copy with remapped draws
     allidx = np.concatenate([np.asarray(d[0], np.int64) for d in draws])
     Xs = Xd[torch.from_numpy(allidx).to("cuda:0")].cpu().numpy()
     cdraws = [(np.arange(q * s, (q + 1) * s), d[1], d[2]) for q, d in enumerate(draws)]
-    ctx, st, recs, followed, bad = _follow(bm, None, Xd, m, n, k, s, T, seed, prec=3,
+    ctx, st, recs, followed, bad = _follow(bm, None, Xd, m, n, k, s, T, seed, prec=prec,
                                            Xo=Xs, draws=cdraws)
     try:
         assert bad is None, "chunk %r: no admissible oracle outcome matches" % bad
-        # final assignment of all rows from the oracle's incumbent (equal to
-        # the GPU's within the parity tolerance), in the timed form
         bm.bm_set_state(ctx, st.C.astype(np.float32), st.live.astype(np.uint8), st.f_opt, T)
         labels = torch.empty(m, dtype=torch.int32, device="cuda:0")
         sse = bm.bm_assign(ctx, labels)
@@ -138,7 +142,21 @@ def test_c3_chunks_and_full_final_assignment(bm):
     sse_ref = float(d1.sum())
     nbad, nties = labels_match(lab_gpu, A, d1, d2)
     assert nbad == 0 and rel(sse, sse_ref) <= OBJ_REL
-    _report("c3_gas_sensor_like_seed0", chunks=T, followed=[list(f) for f in followed],
+    _report(name, chunks=T, followed=[list(f) for f in followed],
             accepted=sum(r.accepted for r in recs), lloyd_iters=sum(r.iters for r in recs),
             final_rows=m, final_tie_rows=nties, sse_rel=rel(sse, sse_ref))
-    assert len(followed) <= 4
+    assert len(followed) <= max_followed
+
+
+def test_c3_chunks_and_full_final_assignment(bm):
+    m, n, k, s, seed = 10_000_000, 128, 50, 50_000, 0
+    Xd = bi.mixtures.gas_sensor_like_device(seed, m=m, n=n, device="cuda:0")
+    _follow_device_workload(bm, Xd, m, n, k, s, C3_CHUNKS, seed, 1,
+                            "c3_gas_sensor_like_seed0", 4)
+
+
+def test_c3_fp8_variant_chunks_and_full_final_assignment(bm):
+    m, n, k, s, seed = 2_000_000, 384, 100, 50_000, 0
+    Xd = bi.mixtures.scaled_384_device(seed, m=m, device="cuda:0")
+    _follow_device_workload(bm, Xd, m, n, k, s, FP8_CHUNKS, seed, 2,
+                            "c3_fp8_scaled_384_seed0", 6)

@@ -1,8 +1,9 @@
 """GPU parity of the tensor-core chunk kernel (rows wider than 32 features).
 
-A context created with a BF16 precision form runs every Lloyd and K-means++
-assignment of a chunk on the tensor cores with exact FP32 rescoring; an FP32
-context whose shared-memory tables do not fit takes the same kernel.  Cases
+A context created with a BF16, split-BF16 or E4M3 precision form runs every
+Lloyd and K-means++ assignment of a chunk on the tensor cores with exact
+FP32 rescoring; an FP32 context whose shared-memory tables do not fit takes
+the same kernel.  Cases
 are decisive in the sense of test_gpu_parity (asserted from the oracle's own
 record), so the GPU must reach the oracle's decisions: labels, degenerate
 sets, Lloyd iteration counts, keep-the-best outcomes, and objectives and
@@ -18,7 +19,7 @@ from gpu_helpers import (CEN_REL, OBJ_REL, centroids_close, dev, host, labels_ma
 from test_gpu_parity import _assert_decisive
 
 pytestmark = pytest.mark.gpu
-BF16, BF16X3 = 1, 3
+BF16, FP8, BF16X3 = 1, 2, 3
 
 
 @pytest.fixture(scope="module")
@@ -57,6 +58,14 @@ def _run(bm, X, cfg, T):
     (1000, 33, 7, 999, 0, 2, BF16),
     (3000, 384, 100, 1500, 0, 2, BF16),
     (1200, 40, 1, 400, 0, 3, BF16),
+    # E4M3 screening (K blocks of 128 features, per-row and per-chunk scales)
+    (3000, 384, 100, 1500, 0, 2, FP8),      # three K blocks, n16 = 112
+    (4000, 128, 50, 2000, 1, 3, FP8),
+    (2500, 200, 17, 1300, 0, 3, FP8),       # n = 200: second K block padded
+    (1000, 33, 7, 999, 0, 2, FP8),
+    (5000, 68, 100, 2500, 0, 2, FP8),
+    (3000, 64, 33, 1000, 0, 3, FP8),
+    (1200, 40, 1, 400, 0, 3, FP8),
 ])
 def test_tc_chunks_match_oracle(bm, m, n, k, s, seed, T, prec):
     X, _ = bi.mixtures.isotropic_blobs(m, n, max(k, 2), seed, box=8.0)
@@ -78,7 +87,8 @@ def test_tc_chunks_match_oracle(bm, m, n, k, s, seed, T, prec):
 
 
 @pytest.mark.parametrize("seed,chunks,prec", [(2, (1, 2, 3, 4, 5), BF16X3),
-                                              (2, (1, 2, 3, 4, 5), BF16)])
+                                              (2, (1, 2, 3, 4, 5), BF16),
+                                              (2, (1, 2, 3, 4, 5), FP8)])
 def test_tc_full_size_chunks_teacher_forced(bm, seed, chunks, prec):
     """m = 200,000, n = 128, k = 50, s = 50,000 (a 100-component mixture with
     Dirichlet(0.5) weights): every chunk starts from the oracle's incumbent
@@ -117,7 +127,7 @@ def test_tc_and_fp32_kernels_agree(bm):
     m, n, k, s, T, seed = 3000, 64, 33, 1000, 3, 0
     X, _ = bi.mixtures.isotropic_blobs(m, n, k, seed, box=8.0)
     out = []
-    for prec in (0, BF16X3, BF16):
+    for prec in (0, BF16X3, BF16, FP8):
         cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=seed, precision=prec)
         out.append(_run(bm, X, cfg, T))
     r0, C0, m0, f0, l0, s0 = out[0]
@@ -128,10 +138,11 @@ def test_tc_and_fp32_kernels_agree(bm):
         assert centroids_close(C1, C0.astype(np.float64), m0) <= CEN_REL
 
 
-def test_tc_runs_are_bitwise_deterministic(bm):
+@pytest.mark.parametrize("prec", [BF16X3, FP8])
+def test_tc_runs_are_bitwise_deterministic(bm, prec):
     m, n, k, s, T, seed = 20_000, 96, 40, 6000, 4, 5
     X, _ = bi.mixtures.isotropic_blobs(m, n, 60, seed)
-    cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=seed, precision=BF16X3)
+    cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=seed, precision=prec)
     a = _run(bm, X, cfg, T)
     b = _run(bm, X, cfg, T)
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
@@ -154,3 +165,41 @@ def test_tc_op_level_lloyd_for_wide_tables(bm):
     assert np.array_equal(host(md).astype(bool), res.live)
     assert rel(f, res.f) <= OBJ_REL
     assert centroids_close(host(Cd), res.C, res.live) <= CEN_REL
+
+
+@pytest.mark.parametrize("prec", [FP8, BF16])
+def test_tc_far_incumbent_centroid(bm, prec):
+    """A chunk whose incumbent holds a centroid 40 times farther out than the
+    largest data value (the E4M3 centroid scale of the chunk then comes from
+    that centroid, so the other centroids sit far down the E4M3 range): the
+    far centroid loses every member and becomes degenerate, and the chunk
+    (accepted: the incumbent objective is +inf) must end at the oracle's
+    outcome."""
+    m, n, k, s, seed = 6000, 128, 20, 3000, 3
+    X, _ = bi.mixtures.isotropic_blobs(m, n, 30, seed, box=8.0)
+    st = o.BigMeansState(k, n)
+    idx, uf, u = bi.chunk_draws(seed, 0, m, s, k)
+    o.big_means_chunk(X, st, idx, uf, u, t=0)
+    st.C[3] = 40.0 * np.abs(X).max() * np.where(np.arange(n) % 2 == 1, 1.0, -1.0)
+    st.f_opt = np.inf
+    before = st.copy()
+    idx, uf, u = bi.chunk_draws(seed, 1, m, s, k)
+    rec = o.big_means_chunk(X, st, idx, uf, u, t=1)
+    _assert_decisive([rec])
+    assert rec.accepted and not st.live[3]
+    cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=seed, precision=prec)
+    ctx = bm.bm_create(cfg, dev(X))
+    try:
+        bm.bm_set_state(ctx, before.C.astype(np.float32), before.live.astype(np.uint8),
+                        before.f_opt, 1)
+        rep = bm.bm_fit_chunk(ctx, 1)
+        C = np.zeros((k, n), np.float32)
+        mask = np.zeros(k, np.uint8)
+        f_opt, tc = bm.bm_get_state(ctx, C, mask)
+    finally:
+        bm.bm_destroy(ctx)
+    assert tc == 2
+    assert rep["accepted"] == 1 and rep["lloyd_iters"] == rec.iters
+    assert np.array_equal(mask.astype(bool), st.live)
+    assert rel(f_opt, st.f_opt) <= OBJ_REL
+    assert centroids_close(C, st.C, st.live) <= CEN_REL
