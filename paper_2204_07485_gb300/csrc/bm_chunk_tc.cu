@@ -15,7 +15,7 @@
 //       approximate distance (see the tensor-core assignment) and records
 //       the candidate centroids of each row;
 //   A'. decides the rows with more than one candidate from exact FP32
-//       distances (one warp per row, coalesced loads);
+//       distances (a half-warp per row, coalesced loads);
 //   BC. sweeps its rows again in feature blocks staged in shared memory:
 //       the exact FP32 distance of every single-candidate
 //       row to its centroid (four partial sums over f mod 4, ascending f --
@@ -244,72 +244,86 @@ __device__ void load_norms(const ChunkArgs& a, const TccS& S, TccBound* bd) {
 // contiguous block of 16 KB per plane (the hi plane, then for split BF16 the
 // lo plane) in the 128-byte-swizzled K-major layout of the MMA; ||x||^2 of
 // every own row -> S.xx.
-// E4M3 form: own rows -> E4M3 tiles (K blocks of 128 features), a warp per
-// row: lane l holds the 8-feature units l and l + 32 (npad <= 512), so the
-// row's largest magnitude and its norm are warp reductions.  Row i is scaled
-// by 1 / rsc[i], the power of two that brings that magnitude into
-// [128, 256).  Returns the largest magnitude over own rows (every thread).
+// E4M3 form: own rows -> E4M3 tiles (K blocks of 128 features).  A first
+// pass gives each row its largest magnitude and norm (8 threads per row,
+// every float4 of the row in flight at once); row i is scaled by
+// 1 / rsc[i], the power of two that brings that magnitude into [128, 256).
+// A second pass converts 16-feature chunks (4 per thread in flight) into
+// the 128-byte-swizzled K-major tiles; padding rows and features are zero.
+// Returns the largest magnitude over own rows (every thread).
 __device__ float tcc_convert_own_fp8(const ChunkArgs& a, const TccS& S, int r0, int nrows) {
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, kb = a.tc_kb, npad = a.npad;
+  const int tid = threadIdx.x, kb = a.tc_kb, npad = a.npad, np4 = npad >> 2;
   constexpr int blk = kTccM * 128;
-  unsigned char* base = a.Pb + (size_t)blockIdx.x * a.tc_tpc * kb * blk;
+  const float4* P4 = reinterpret_cast<const float4*>(a.P) + (size_t)r0 * np4;
   float cmax = 0.f;
+  for (int i0 = 0; i0 < nrows; i0 += kTccThreads / 8) {
+    const int i = i0 + (tid >> 3), c = tid & 7;
+    float4 v[16];   // np4 <= 128
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int q = c + 8 * u;
+      v[u] = (i < nrows && q < np4) ? __ldcg(P4 + (size_t)i * np4 + q)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float mx = 0.f, nq = 0.f;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[u].x), fabsf(v[u].y)), fmaxf(fabsf(v[u].z), fabsf(v[u].w))));
+      nq = fmaf(v[u].x, v[u].x, nq);
+      nq = fmaf(v[u].y, v[u].y, nq);
+      nq = fmaf(v[u].z, v[u].z, nq);
+      nq = fmaf(v[u].w, v[u].w, nq);
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {   // the 8 threads of a row are consecutive lanes
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      nq += __shfl_xor_sync(0xffffffffu, nq, o);
+    }
+    if (c == 0 && i < nrows) {
+      const int e2 = (mx > 0.f && mx <= 3.0e38f) ? max(ilogbf(mx), -119) : 7;
+      S.xx[i] = nq;
+      S.rsc[i] = ldexpf(1.f, e2 - 7);
+    }
+    cmax = fmaxf(cmax, mx);
+  }
+  __syncthreads();
+  unsigned char* base = a.Pb + (size_t)blockIdx.x * a.tc_tpc * kb * blk;
   for (int t0 = 0; t0 < nrows; t0 += kTccM) {
     const int rows = min(kTccM, nrows - t0);
-    unsigned char* dst = base + (size_t)(t0 / kTccM) * kb * blk;
-    for (int r = w; r < kTccM; r += kTccWarps) {   // every row of the tile: padding rows are zero
-      float v[2][8];
-      float mx = 0.f, q = 0.f;
+    for (int b = 0; b < kb; ++b) {
+      unsigned char* dst = base + (size_t)((t0 / kTccM) * kb + b) * blk;
+      float4 v[4][4];
 #pragma unroll
-      for (int uu = 0; uu < 2; ++uu) {
-        const int f0 = (l + 32 * uu) * 8;
+      for (int u = 0; u < 4; ++u) {
+        const int q = tid + u * kTccThreads, r = q >> 3, f0 = b * 128 + (q & 7) * 16;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[uu][u] = 0.f;
-        if (r < rows && f0 < npad) {
-          const float4* p = reinterpret_cast<const float4*>(a.P + (size_t)(r0 + t0 + r) * npad + f0);
-          const float4 x0 = __ldcg(p);
-          v[uu][0] = x0.x; v[uu][1] = x0.y; v[uu][2] = x0.z; v[uu][3] = x0.w;
-          if (f0 + 4 < npad) {
-            const float4 x1 = __ldcg(p + 1);
-            v[uu][4] = x1.x; v[uu][5] = x1.y; v[uu][6] = x1.z; v[uu][7] = x1.w;
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          mx = fmaxf(mx, fabsf(v[uu][u]));
-          q = fmaf(v[uu][u], v[uu][u], q);
-        }
+        for (int e = 0; e < 4; ++e)
+          v[u][e] = (r < rows && f0 + 4 * e < npad)
+              ? __ldcg(P4 + (size_t)(t0 + r) * np4 + (f0 >> 2) + e)
+              : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      mx = warp_max_f32(mx);
-      q = warp_sum_f32(q);
-      const int e2 = (mx > 0.f && mx <= 3.0e38f) ? max(ilogbf(mx), -119) : 7;
-      const float inv = ldexpf(1.f, e2 - 7);
-      if (l == 0 && r < rows) {
-        S.xx[t0 + r] = q;
-        S.rsc[t0 + r] = inv;
-      }
-      cmax = fmaxf(cmax, mx);
 #pragma unroll
-      for (int uu = 0; uu < 2; ++uu) {
-        const int f0 = (l + 32 * uu) * 8;
-        if (f0 >= kb * 128) continue;
-        uint32_t wd[2] = {0u, 0u};
+      for (int u = 0; u < 4; ++u) {
+        const int q = tid + u * kTccThreads, r = q >> 3, ch = q & 7;
+        const float inv = r < rows ? S.rsc[t0 + r] : 1.f;
+        uint32_t wd[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const uint32_t byte =
-              (uint32_t)__nv_cvt_float_to_fp8(v[uu][u] / inv, __NV_SATFINITE, __NV_E4M3);
-          wd[u >> 2] |= byte << (8 * (u & 3));
+        for (int e = 0; e < 4; ++e) {
+          const float4 x = v[u][e];
+          wd[e] = (uint32_t)__nv_cvt_float_to_fp8(x.x / inv, __NV_SATFINITE, __NV_E4M3) |
+                  ((uint32_t)__nv_cvt_float_to_fp8(x.y / inv, __NV_SATFINITE, __NV_E4M3) << 8) |
+                  ((uint32_t)__nv_cvt_float_to_fp8(x.z / inv, __NV_SATFINITE, __NV_E4M3) << 16) |
+                  ((uint32_t)__nv_cvt_float_to_fp8(x.w / inv, __NV_SATFINITE, __NV_E4M3) << 24);
         }
-        const int wi = f0 & 127;
-        const int off = (f0 >> 7) * blk + (r >> 3) * 1024 + (r & 7) * 128 +
-                        (((wi >> 4) ^ (r & 7)) << 4) + (wi & 8);
-        *reinterpret_cast<uint2*>(dst + off) = make_uint2(wd[0], wd[1]);
+        const int off = (r >> 3) * 1024 + (r & 7) * 128 + ((ch ^ (r & 7)) << 4);
+        *reinterpret_cast<uint4*>(dst + off) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
       }
     }
   }
   fence_proxy_async_global();   // the tiles are read back by bulk copies
-  __syncthreads();
+  const int w = tid >> 5, l = tid & 31;
   const float m = warp_max_f32(cmax);
+  __syncthreads();
   if (l == 0) S.red[w] = m;
   __syncthreads();
   float all = 0.f;
@@ -512,8 +526,8 @@ __device__ bool tcc_pass_a(const ChunkArgs& a, const TccS& S, int r0, int nrows,
 }
 
 // ---------------------------------------------------------------- pass A'
-// Rows with several candidates: exact FP32 distances to each candidate, one
-// warp per row (lane l holds features 4 l + 128 u), lowest index on ties.
+// Rows with several candidates: exact FP32 distances to each candidate, a
+// half-warp per row, lowest index on ties.
 __device__ void tcc_pass_multi(const ChunkArgs& a, const TccS& S, int r0, int nrows) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, npad = a.npad;
   if (threadIdx.x == 0) S.mlist[a.rows_per_cta] = 0;
@@ -529,49 +543,53 @@ __device__ void tcc_pass_multi(const ChunkArgs& a, const TccS& S, int r0, int nr
   }
   __syncthreads();
   const int nm = S.mlist[a.rows_per_cta];
-  const int nq = (npad + 127) >> 7;   // float4 per lane
-  for (int e = w; e < nm; e += kTccWarps) {
-    const int i = S.mlist[e];
-    float4 x[4];
+  // a half-warp per row, so two rows (and their candidates' centroid rows)
+  // are in flight per warp: lane h of half hw holds features 4 h + 64 u
+  // (u < 8: npad <= 512)
+  const int h = l & 15, hw = l >> 4, nu = (npad + 63) >> 6;
+  for (int e0 = 2 * w; e0 < nm; e0 += 2 * kTccWarps) {
+    const int e = e0 + hw;
+    const bool on = e < nm;
+    const int i = on ? S.mlist[e] : 0;
+    float4 x[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int f = 4 * l + 128 * u;
-      x[u] = (u < nq && f < npad)
+    for (int u = 0; u < 8; ++u) {
+      const int f = 4 * h + 64 * u;
+      x[u] = (on && u < nu && f < npad)
           ? __ldcg(reinterpret_cast<const float4*>(a.P + (size_t)(r0 + i) * npad + f))
           : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    float best = INFINITY;
-    int bj = INT_MAX;
     uint32_t mw[4];
 #pragma unroll
-    for (int wd = 0; wd < 4; ++wd) mw[wd] = S.cmask[i * 4 + wd];
-    int wd = 0;
+    for (int wd = 0; wd < 4; ++wd) mw[wd] = on ? S.cmask[i * 4 + wd] : 0u;
+    float best = INFINITY;
+    int bj = INT_MAX, wd = 0;
     while (true) {
-      // the next (up to) four candidates in ascending order; their centroid
-      // rows are loaded together
-      int js[4], nj = 0;
-      while (nj < 4 && wd < 4) {
+      // the next (up to) two candidates of this half's row, ascending; the
+      // warp runs while either half has some left (the sums shuffle across it)
+      int js[2] = {0, 0}, nj = 0;
+      while (nj < 2 && wd < 4) {
         if (mw[wd] == 0u) { ++wd; continue; }
         js[nj++] = wd * 32 + __ffs(mw[wd]) - 1;
         mw[wd] &= mw[wd] - 1u;
       }
-      if (nj == 0) break;
-      float4 cv[4][4];
+      if ((nj | __shfl_xor_sync(0xffffffffu, nj, 16)) == 0) break;
+      float4 cv[2][8];
 #pragma unroll
-      for (int t = 0; t < 4; ++t)
+      for (int t = 0; t < 2; ++t)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int f = 4 * l + 128 * u;
-          cv[t][u] = (t < nj && u < nq && f < npad)
+        for (int u = 0; u < 8; ++u) {
+          const int f = 4 * h + 64 * u;
+          cv[t][u] = (t < nj && u < nu && f < npad)
               ? __ldcg(reinterpret_cast<const float4*>(a.C + (size_t)js[t] * npad + f))
               : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        if (t >= nj) break;
+      for (int t = 0; t < 2; ++t) {
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 8; ++u) {
+          if (u >= nu) break;
           const float e0 = x[u].x - cv[t][u].x, e1 = x[u].y - cv[t][u].y;
           const float e2 = x[u].z - cv[t][u].z, e3 = x[u].w - cv[t][u].w;
           s0 = fmaf(e0, e0, s0);
@@ -579,15 +597,18 @@ __device__ void tcc_pass_multi(const ChunkArgs& a, const TccS& S, int r0, int nr
           s2 = fmaf(e2, e2, s2);
           s3 = fmaf(e3, e3, s3);
         }
-        s0 = warp_sum_f32(s0);
-        s1 = warp_sum_f32(s1);
-        s2 = warp_sum_f32(s2);
-        s3 = warp_sum_f32(s3);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {   // within the half-warp
+          s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+          s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+          s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+          s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+        }
         const float d = (s0 + s1) + (s2 + s3);
-        if (bj == INT_MAX || d < best) { best = d; bj = js[t]; }
+        if (t < nj && (bj == INT_MAX || d < best)) { best = d; bj = js[t]; }
       }
     }
-    if (l == 0) {
+    if (on && h == 0) {
       S.lab[i] = bj;
       S.dmin[i] = best;
     }
