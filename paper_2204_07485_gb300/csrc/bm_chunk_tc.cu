@@ -815,59 +815,113 @@ __device__ bool tcc_assign(const ChunkArgs& a, const TccS& S, int r0, int nrows,
 // ---------------------------------------------------------------- reduce
 // New centroids from the partials, one warp per (centroid, 8-feature slice):
 // the member count over CTAs and the slice's sums over CTAs (lane l sums the
-// CTAs u = l, l + 32, ... -- all loads in flight at once -- then a fixed
-// xor butterfly), c <- c + sum / count, the slice's planes and squared norm.
-// Centroids without members become degenerate (Sec. 3.3) unless the launch
-// keeps them in place.
-__device__ void tcc_reduce(const ChunkArgs& a, const TccS& S, bool stop) {
-  const int k = a.k, npad = a.npad, n = a.n, G = gridDim.x;
+// CTAs u = l, l + 32, ... in that order, then a fixed xor butterfly),
+// c <- c + sum / count, the slice's planes and squared norm.  Centroids
+// without members become degenerate (Sec. 3.3) unless the launch keeps them
+// in place.
+//
+// A task's loads (the CTAs' partials, the old centroid value) land in
+// registers first and are summed later, so a warp issues the loads of its
+// first task before the objective's round trip and those of its next task
+// before finishing the current one.
+constexpr int kRedSlots = 5;   // CTAs u = l + 32 i, i < kRedSlots, held in registers
+
+struct RedTask {
+  int q;                       // (centroid, slice) index, or -1
+  int cnt[kRedSlots];
+  float4 x0[kRedSlots], x1[kRedSlots];
+  float c;                     // lane l < 8: the old value of feature 8 sl + l
+};
+
+__device__ __forceinline__ RedTask tcc_reduce_load(const ChunkArgs& a, const TccS& S, int q) {
+  const int k = a.k, npad = a.npad, G = gridDim.x, l = threadIdx.x & 31;
   const int nsl = (npad + 7) >> 3;
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const int gw = blockIdx.x * kTccWarps + w, nw = G * kTccWarps;
-  for (int q = gw; q < k * nsl; q += nw) {
-    const int j = q / nsl, sl = q - j * nsl;
-    if (!S.live[j]) continue;
-    const bool two = sl * 8 + 4 < npad;   // the slice's second float4 exists
-    int cnt = 0;
-    float v[8];
+  RedTask t;
+  t.q = -1;
+  t.c = 0.f;
+  if (q >= k * nsl) return t;
+  const int j = q / nsl, sl = q - j * nsl;
+  if (!S.live[j]) return t;
+  t.q = q;
+  const bool two = sl * 8 + 4 < npad;   // the slice's second float4 exists
 #pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = 0.f;
-#pragma unroll 5
-    for (int u = l; u < G; u += 32) {
-      cnt += __ldcg(a.part_cnt + (size_t)u * k + j);
-      const float4* ps =
-          reinterpret_cast<const float4*>(a.part_sum + ((size_t)u * k + j) * npad + sl * 8);
-      const float4 x0 = __ldcg(ps);
-      const float4 x1 = two ? __ldcg(ps + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-      v[0] += x0.x; v[1] += x0.y; v[2] += x0.z; v[3] += x0.w;
-      v[4] += x1.x; v[5] += x1.y; v[6] += x1.z; v[7] += x1.w;
-    }
-    cnt = warp_sum_i32(cnt);
-    if (cnt == 0) {   // degenerate, or kept in place (planes and norm unchanged)
-      if (!a.empty_keep && sl == 0 && l == 0) a.mask[j] = 0;
-      continue;
-    }
-    if (stop) continue;
+  for (int i = 0; i < kRedSlots; ++i) {
+    const int u = l + 32 * i;
+    const bool on = u < G;
+    t.cnt[i] = on ? __ldcg(a.part_cnt + (size_t)u * k + j) : 0;
+    const float4* ps =
+        reinterpret_cast<const float4*>(a.part_sum + ((size_t)u * k + j) * npad + sl * 8);
+    t.x0[i] = on ? __ldcg(ps) : make_float4(0.f, 0.f, 0.f, 0.f);
+    t.x1[i] = on && two ? __ldcg(ps + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  const int f = sl * 8 + l;
+  if (l < 8 && f < a.n) t.c = __ldcg(a.C + (size_t)j * npad + f);
+  return t;
+}
+
+__device__ __forceinline__ void tcc_reduce_finish(const ChunkArgs& a, const RedTask& t,
+                                                  bool stop) {
+  const int k = a.k, npad = a.npad, n = a.n, G = gridDim.x, l = threadIdx.x & 31;
+  const int nsl = (npad + 7) >> 3;
+  const int j = t.q / nsl, sl = t.q - j * nsl;
+  const bool two = sl * 8 + 4 < npad;
+  int cnt = 0;
+  float v[8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
+  for (int e = 0; e < 8; ++e) v[e] = 0.f;
 #pragma unroll
-      for (int e = 0; e < 8; ++e) v[e] += __shfl_xor_sync(0xffffffffu, v[e], o);
-    float mine = 0.f;
+  for (int i = 0; i < kRedSlots; ++i) {
+    cnt += t.cnt[i];
+    v[0] += t.x0[i].x; v[1] += t.x0[i].y; v[2] += t.x0[i].z; v[3] += t.x0[i].w;
+    v[4] += t.x1[i].x; v[5] += t.x1[i].y; v[6] += t.x1[i].z; v[7] += t.x1[i].w;
+  }
+  for (int u = l + 32 * kRedSlots; u < G; u += 32) {   // grids beyond 32 kRedSlots CTAs
+    cnt += __ldcg(a.part_cnt + (size_t)u * k + j);
+    const float4* ps =
+        reinterpret_cast<const float4*>(a.part_sum + ((size_t)u * k + j) * npad + sl * 8);
+    const float4 x0 = __ldcg(ps);
+    const float4 x1 = two ? __ldcg(ps + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+    v[0] += x0.x; v[1] += x0.y; v[2] += x0.z; v[3] += x0.w;
+    v[4] += x1.x; v[5] += x1.y; v[6] += x1.z; v[7] += x1.w;
+  }
+  cnt = warp_sum_i32(cnt);
+  if (cnt == 0) {   // degenerate, or kept in place (planes and norm unchanged)
+    if (!a.empty_keep && sl == 0 && l == 0) a.mask[j] = 0;
+    return;
+  }
+  if (stop) return;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) if ((l & 7) == e) mine = v[e];
-    const int f = sl * 8 + l;
-    const bool on = l < 8 && f < n;
-    float c = 0.f;
-    if (on) {
-      c = __ldcg(a.C + (size_t)j * npad + f) + mine / (float)cnt;
-      a.C[(size_t)j * npad + f] = c;
-      put_cb(a, j, f, c);
-    }
-    float sq = on ? c * c : 0.f;
-    sq += __shfl_xor_sync(0xffffffffu, sq, 1);
-    sq += __shfl_xor_sync(0xffffffffu, sq, 2);
-    sq += __shfl_xor_sync(0xffffffffu, sq, 4);
-    if (l == 0) a.sqs[(size_t)j * nsl + sl] = sq;
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] += __shfl_xor_sync(0xffffffffu, v[e], o);
+  float mine = 0.f;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) if ((l & 7) == e) mine = v[e];
+  const int f = sl * 8 + l;
+  const bool on = l < 8 && f < n;
+  float c = 0.f;
+  if (on) {
+    c = t.c + mine / (float)cnt;
+    a.C[(size_t)j * npad + f] = c;
+    put_cb(a, j, f, c);
+  }
+  float sq = on ? c * c : 0.f;
+  sq += __shfl_xor_sync(0xffffffffu, sq, 1);
+  sq += __shfl_xor_sync(0xffffffffu, sq, 2);
+  sq += __shfl_xor_sync(0xffffffffu, sq, 4);
+  if (l == 0) a.sqs[(size_t)j * nsl + sl] = sq;
+}
+
+// Every task of this warp, the first one's loads already issued (`first`).
+__device__ void tcc_reduce(const ChunkArgs& a, const TccS& S, bool stop, const RedTask& first) {
+  const int nsl = (a.npad + 7) >> 3, tasks = a.k * nsl;
+  const int w = threadIdx.x >> 5;
+  const int gw = blockIdx.x * kTccWarps + w, nw = gridDim.x * kTccWarps;
+  RedTask cur = first;
+  for (int q = gw; q < tasks; q += nw) {
+    const RedTask nxt = tcc_reduce_load(a, S, q + nw);
+    if (cur.q >= 0) tcc_reduce_finish(a, cur, stop);
+    cur = nxt;
   }
   fence_proxy_async_global();   // the planes are read by bulk copies after the barrier
 }
@@ -996,6 +1050,7 @@ __device__ bool tcc_lloyd(const ChunkArgs& a, const TccS& S, GridBarrier& gb, in
     phase_tick(a, 3, tclk);
     if (!ok || !gb.sync()) { ok = false; break; }
     phase_tick(a, 4, tclk);
+    const RedTask first = tcc_reduce_load(a, S, b * kTccWarps + w);
     if (w == 0) {
       const double t = warp_sum_array_f64(FPART, G);
       if (l == 0) s_f = t;
@@ -1004,7 +1059,7 @@ __device__ bool tcc_lloyd(const ChunkArgs& a, const TccS& S, GridBarrier& gb, in
     f = s_f;
     const bool stop = (f == 0.0) || (it > 0 && f_prev - f <= a.tol * f_prev) ||
                       (it == a.max_iter);
-    tcc_reduce(a, S, stop);
+    tcc_reduce(a, S, stop, first);
     phase_tick(a, 5, tclk);
     if (!gb.sync()) { ok = false; break; }
     for (int j = threadIdx.x; j < k; j += blockDim.x)
