@@ -31,6 +31,25 @@ __device__ __forceinline__ bool guard_ok(bool in_bounds, int* status) {
 #define BM_GUARD(cond, status) (true)
 #endif
 
+// Checking builds (BM_DEBUG_GUARDS) also fill a kernel's dynamic shared
+// memory with 0xFF bytes before it starts -- a NaN in FP32, BF16 and E4M3,
+// -1 as an integer -- so that a read of a location the kernel never wrote
+// changes its results instead of picking up an earlier kernel's leftovers.
+// Called by every thread at the top of the kernel; release builds compile
+// it to nothing.
+#ifdef BM_DEBUG_GUARDS
+__device__ __forceinline__ void poison_dynamic_smem() {
+  extern __shared__ __align__(16) uint32_t bm_poison_base[];
+  uint32_t bytes;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(bytes));
+  for (uint32_t i = threadIdx.x; i < bytes / 4; i += blockDim.x) bm_poison_base[i] = 0xFFFFFFFFu;
+  __syncthreads();
+}
+#define BM_POISON_SMEM() (::bm::poison_dynamic_smem())
+#else
+#define BM_POISON_SMEM() ((void)0)
+#endif
+
 // Bounds of every device-side spin: the wait gives up after this many polls
 // or this much wall time (read from %globaltimer), whichever comes first.
 constexpr uint32_t kSpinLimit = 1u << 26;

@@ -258,6 +258,7 @@ __device__ void group_assign_segments(const GroupArgs& a) {
 
 __global__ void __launch_bounds__(kGroupThreads)
 group_assign_kernel(GroupArgs a) {
+  BM_POISON_SMEM();
   group_assign_segments(a);
 }
 
@@ -335,6 +336,7 @@ group_update_kernel(GroupArgs a) {
 // One Lloyd step of every unfinished problem in one cooperative launch.
 __global__ void __launch_bounds__(kGroupThreads)
 group_step_kernel(GroupArgs a) {
+  BM_POISON_SMEM();
   group_assign_segments(a);
   GridBarrier gb{a.bar + a.bar_sel, a.status, 0u};
   if (!gb.sync()) return;

@@ -818,6 +818,7 @@ template <int NP, bool GENERIC>
 __global__ void __launch_bounds__(GENERIC ? 256 : 384)
 chunk_kernel(ChunkArgs a) {
   extern __shared__ __align__(16) char smem_raw[];
+  BM_POISON_SMEM();
   const int G = gridDim.x;
   const ChunkSmem L = chunk_smem(a.npad, a.k, a.kpad, a.rows_per_cta, GENERIC);
   const Smem S = carve(smem_raw, L);
@@ -921,6 +922,7 @@ template <int NP>
 __global__ void __launch_bounds__(kThreads)
 assign_np_kernel(AssignArgs a) {
   extern __shared__ __align__(16) char smem_raw[];
+  BM_POISON_SMEM();
   float* cen = reinterpret_cast<float*>(smem_raw);
   int o = align_up(a.k * NP * 4, 16);
   int* live = reinterpret_cast<int*>(smem_raw + o);
@@ -962,6 +964,7 @@ assign_np_kernel(AssignArgs a) {
 __global__ void __launch_bounds__(kThreads)
 assign_generic_kernel(AssignArgs a) {
   extern __shared__ __align__(16) char smem_raw[];
+  BM_POISON_SMEM();
   float* cenT = reinterpret_cast<float*>(smem_raw);
   int o = align_up(a.npad * a.kpad * 4, 16);
   int* live = reinterpret_cast<int*>(smem_raw + o);

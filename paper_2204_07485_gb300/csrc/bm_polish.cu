@@ -21,6 +21,7 @@ constexpr int kPolishFpl = 8;    // features per lane: blocks of at most 256 fea
 // partials.  Warps >= wu only help with the set-up and the combination.
 __global__ void __launch_bounds__(kPolishThreads) polish_accum_kernel(PolishArgs a) {
   extern __shared__ __align__(16) float psm[];
+  BM_POISON_SMEM();
   const int k = a.k, npad = a.npad, wu = a.wu, f0 = a.f0, fw = a.fw;
   const int n = min(a.n - f0, fw);                   // features of this block
   float* cen = psm;                                  // [k][fw] current centroids

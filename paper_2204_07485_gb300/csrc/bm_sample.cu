@@ -59,6 +59,7 @@ __device__ __forceinline__ uint32_t sample_bits(uint32_t raw, long long w, long 
 
 __global__ void __launch_bounds__(kDrawThreads) draw_kernel(DrawArgs a) {
   extern __shared__ __align__(16) uint32_t sbits[];   // the chunk's bitmap, when it fits
+  BM_POISON_SMEM();
   __shared__ int red[32];
   __shared__ int scan[32];
   const long long W = (a.m + 31) / 32;

@@ -120,6 +120,7 @@ template <bool FP8>
 __global__ void __launch_bounds__(kTcThreads, 4)
 assign_tc_kernel(AssignTcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw_tc[];
+  BM_POISON_SMEM();
   // the swizzled tiles need a 1024-byte aligned base (the launch adds slack)
   unsigned char* smem_tc =
       smem_raw_tc + ((1024u - (smem_u32(smem_raw_tc) & 1023u)) & 1023u);
@@ -438,7 +439,9 @@ assign_tc_kernel(AssignTcArgs a) {
     const int r = tid;
     const bool valid = r < rows;
     const float* xrow = S == 2 ? tile + (size_t)r * n : xf ? xF + r * xs : src + (size_t)r * n;
-    const float xq = (cslots > 32 ? __fadd_rn(xx[r], xx[kTcRows + r]) : xx[r]) * 1.00002f;
+    // (the E4M3 conversion keeps a row's whole norm in xx[r]: a warp per row)
+    const float xq =
+        (!FP8 && cslots > 32 ? __fadd_rn(xx[r], xx[kTcRows + r]) : xx[r]) * 1.00002f;
     const float E1 = fmaf(sqrtf(xq), s_bound[0], s_bound[1]);
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     // approximate distance minus ||x||^2 from accumulator column j (the E4M3

@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(tcs_threads(W), 1)
 assign_tcs_kernel(const __grid_constant__ CUtensorMap xmap, TcsArgs a) {
   constexpr int kThreads = tcs_threads(W);
   extern __shared__ __align__(1024) unsigned char tcs_raw[];
+  BM_POISON_SMEM();
   unsigned char* sm = tcs_raw + ((1024u - (smem_u32(tcs_raw) & 1023u)) & 1023u);
   constexpr int NF = NB * 32;                // features held per row (zero padded)
   constexpr int KB = (NF + 63) / 64;         // K blocks of 64 BF16

@@ -70,6 +70,7 @@ __device__ __forceinline__ void tb_arrive(uint64_t* mbar) {
 
 __global__ void __launch_bounds__(kTbThreads, 1) tile_bench_kernel(TbArgs a) {
   extern __shared__ __align__(1024) unsigned char tb_raw[];
+  BM_POISON_SMEM();
   unsigned char* sm = tb_raw + ((1024u - (smem_u32(tb_raw) & 1023u)) & 1023u);
   const int n = a.n, k = a.k, N = a.N, P = a.planes, T = a.tiles, kb = n / 64;
   const TbLayout L = tb_layout(n, N, P, T);
