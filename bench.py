@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-grouped", action="store_true")
     ap.add_argument("--profile", choices=["chunk_np", "chunk_tc", "assign_tc", "assign_fp8",
-                                          "grouped"],
+                                          "draw_m1e7", "grouped"],
                     default=None,
                     help="run one short job of a kernel family (for ncu captures) and exit")
     ap.add_argument("--chunks", type=int, default=C3_WORKLOAD["chunks"])
@@ -884,6 +884,7 @@ PROFILE_CASES = {
     "chunk_tc": (1_000_000, 128, 50, 50_000, 1, 3),    # chunk_tc_kernel, BF16 screening
     "assign_tc": (2_000_000, 128, 50, 50_000, 1, 1),   # assign_tcs_kernel, BF16 (final assignment)
     "assign_fp8": (2_000_000, 384, 100, 50_000, 2, 1),  # assign_tc_kernel<true> (E4M3)
+    "draw_m1e7": (10_000_000, 4, 5, 50_000, 0, 64),     # draw_kernel, bitmaps in global memory
 }
 
 

@@ -161,9 +161,11 @@ bm_status bm_fit_chunk(bm_ctx* ctx, int32_t chunks, bm_fit_report* out);
  * accumulated in float64.  With a tensor-core precision form (BM_BF16_RESCORE,
  * BM_BF16X3_RESCORE, BM_FP8_RESCORE) the distances run on the tensor cores in
  * that arithmetic with exact FP32 rescoring (see bm_assign_rows_prec); the
- * chunks of a BM_BF16_RESCORE context screen with BF16 products, those of
- * the other tensor-core forms with split BF16 products (labels and distances
- * are those of FP32 either way).  Blocks until done. */
+ * chunks of a context (rows wider than 32 features) screen with BF16
+ * products in BM_BF16_RESCORE, E4M3 products in BM_FP8_RESCORE (rows scaled
+ * per row, centroids by one power of two per chunk) and split BF16 products
+ * otherwise (labels and distances are those of FP32 either way).  Blocks
+ * until done. */
 bm_status bm_assign(bm_ctx* ctx, int32_t* labels_dev, double* sse_out);
 
 /* Streaming (stream processing of newly arriving data portions, Sec. 1 and
