@@ -28,6 +28,19 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+// Slots a warp reads per page of a per-CTA exchange: lane l holds slots
+// l, l + 32, ... (kKxLanes of them), so one page costs one round trip.
+constexpr int kKxLanes = 8;
+constexpr int kKxPage = 32 * kKxLanes;
 
 // Launch generation: read by every CTA at the start of a launch (the previous
 // launch on the workspace has completed), advanced by CTA 0 at its end.
@@ -74,6 +87,29 @@ static __device__ __noinline__ bool kx_wait(const ChunkArgs& a, const unsigned l
     __nanosleep(32);
   }
   return true;
+}
+
+// The calling warp acquires tags[0, count) == want: a page's tags are read
+// with relaxed loads, all in flight together; a tag that is not yet current
+// is waited for (kx_wait); then one acquire fence orders every later read
+// after all the tags.  Every lane gets true when all arrived.
+__device__ __forceinline__ bool kx_wait_warp(const ChunkArgs& a, const unsigned long long* tags,
+                                             int count, unsigned long long want) {
+  const int l = threadIdx.x & 31;
+  bool ok = true;
+  for (int p0 = 0; p0 < count; p0 += kKxPage) {
+    unsigned long long v[kKxLanes];
+#pragma unroll
+    for (int i = 0; i < kKxLanes; ++i) {
+      const int x = p0 + l + 32 * i;
+      v[i] = x < count ? ld_relaxed_u64(tags + x) : want;
+    }
+#pragma unroll
+    for (int i = 0; i < kKxLanes; ++i)
+      if (v[i] != want) ok = kx_wait(a, tags + p0 + l + 32 * i, want) && ok;
+  }
+  fence_acq_rel_gpu();
+  return __all_sync(0xffffffffu, ok);
 }
 
 // Thread 0 publishes this CTA's D^2 block sum for slot j.
@@ -129,14 +165,27 @@ __device__ __forceinline__ bool kpp_locate(const ChunkArgs& a, const float* dmin
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (w == 0) {
     // every block sum's tag first: afterwards the sums are read as published
-    bool ok = true;
-    for (int x = l; x < G; x += 32) ok = kx_wait(a, kx_dsum(a) + x, tag) && ok;
-    ok = __all_sync(0xffffffffu, ok);
+    const bool ok = kx_wait_warp(a, kx_dsum(a), G, tag);
     if (l == 0) s_ok = ok;
+    // the sums of a page in registers (lane l: CTAs p0 + l + 32 i), all
+    // loads in flight; the first page is kept for the prefix pass
+    double first[kKxLanes];
+    auto load_page = [&](int p0, double* dv) {
+#pragma unroll
+      for (int i = 0; i < kKxLanes; ++i) {
+        const int x = p0 + l + 32 * i;
+        dv[i] = x < G ? __ldcg(DSUM + x) : 0.0;
+      }
+    };
     double carry = 0.0;
-    for (int base = 0; base < G; base += 32) {
-      const double v = (base + l < G) ? __ldcg(DSUM + base + l) : 0.0;
-      carry += warp_sum_f64(v);
+    for (int p0 = 0; p0 < G; p0 += kKxPage) {
+      double dv[kKxLanes];
+      load_page(p0, dv);
+#pragma unroll
+      for (int i = 0; i < kKxLanes; ++i) {
+        if (p0 == 0) first[i] = dv[i];
+        if (p0 + 32 * i < G) carry += warp_sum_f64(dv[i]);
+      }
     }
     const double total = carry;
     double tgt[kMaxTrials];
@@ -155,33 +204,45 @@ __device__ __forceinline__ bool kpp_locate(const ChunkArgs& a, const float* dmin
       double run = 0.0;
       int last_pos = -1;
       double last_excl = 0.0;
-      for (int base = 0; base < G; base += 32) {
-        const double v = (base + l < G) ? __ldcg(DSUM + base + l) : 0.0;
-        double x = v;
+      for (int p0 = 0; p0 < G; p0 += kKxPage) {
+        double dv[kKxLanes];
+        if (p0 == 0) {
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const double y = __shfl_up_sync(0xffffffffu, x, o);
-          if (l >= o) x += y;
+          for (int i = 0; i < kKxLanes; ++i) dv[i] = first[i];
+        } else {
+          load_page(p0, dv);
         }
-        const double incl = run + x;
 #pragma unroll
-        for (int t = 0; t < kMaxTrials; ++t) {
-          if (t < a.trials && found[t] < 0) {
-            const unsigned hit = __ballot_sync(0xffffffffu, base + l < G && incl > tgt[t]);
-            if (hit) {
-              const int ll = __ffs(hit) - 1;
-              found[t] = base + ll;
-              excl[t] = __shfl_sync(0xffffffffu, incl - v, ll);
+        for (int i = 0; i < kKxLanes; ++i) {
+          const int base = p0 + 32 * i;
+          if (base >= G) break;
+          const double v = dv[i];
+          double x = v;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const double y = __shfl_up_sync(0xffffffffu, x, o);
+            if (l >= o) x += y;
+          }
+          const double incl = run + x;
+#pragma unroll
+          for (int t = 0; t < kMaxTrials; ++t) {
+            if (t < a.trials && found[t] < 0) {
+              const unsigned hit = __ballot_sync(0xffffffffu, base + l < G && incl > tgt[t]);
+              if (hit) {
+                const int ll = __ffs(hit) - 1;
+                found[t] = base + ll;
+                excl[t] = __shfl_sync(0xffffffffu, incl - v, ll);
+              }
             }
           }
+          const unsigned pos = __ballot_sync(0xffffffffu, base + l < G && v > 0.0);
+          if (pos) {
+            const int ll = 31 - __clz(pos);
+            last_pos = base + ll;
+            last_excl = __shfl_sync(0xffffffffu, incl - v, ll);
+          }
+          run = __shfl_sync(0xffffffffu, incl, 31);
         }
-        const unsigned pos = __ballot_sync(0xffffffffu, base + l < G && v > 0.0);
-        if (pos) {
-          const int ll = 31 - __clz(pos);
-          last_pos = base + ll;
-          last_excl = __shfl_sync(0xffffffffu, incl - v, ll);
-        }
-        run = __shfl_sync(0xffffffffu, incl, 31);
       }
 #pragma unroll
       for (int t = 0; t < kMaxTrials; ++t)
@@ -240,16 +301,27 @@ __device__ __forceinline__ int kpp_best(const ChunkArgs& a, unsigned long long t
   const int G = gridDim.x;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (w == 0) {
-    bool ok = true;
-    for (int u = l; u < G; u += 32) ok = kx_wait(a, kx_pot(a) + u, tag) && ok;
-    ok = __all_sync(0xffffffffu, ok);
+    const bool ok = kx_wait_warp(a, kx_pot(a), G, tag);
     double v[kMaxTrials];
 #pragma unroll
     for (int t = 0; t < kMaxTrials; ++t) v[t] = 0.0;
-    for (int u = l; u < G; u += 32)
+    // a page's potentials in registers first (all loads in flight), then
+    // added per trial over u = l, l + 32, ... in order
+    for (int p0 = 0; p0 < G; p0 += kKxPage) {
+      double pv[kKxLanes][kMaxTrials];
 #pragma unroll
-      for (int t = 0; t < kMaxTrials; ++t)
-        if (t < a.trials) v[t] += __ldcg(a.part_f + (size_t)t * G + u);
+      for (int i = 0; i < kKxLanes; ++i) {
+        const int u = p0 + l + 32 * i;
+#pragma unroll
+        for (int t = 0; t < kMaxTrials; ++t)
+          pv[i][t] = (u < G && t < a.trials) ? __ldcg(a.part_f + (size_t)t * G + u) : 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < kKxLanes; ++i)
+#pragma unroll
+        for (int t = 0; t < kMaxTrials; ++t)
+          if (p0 + l + 32 * i < G && t < a.trials) v[t] += pv[i][t];
+    }
     int best = 0;
     double bestv = 0.0;
 #pragma unroll
