@@ -115,9 +115,10 @@ typedef struct bm_fit_report {
   int64_t chunk_counter; /* index t of the next chunk                          */
   double f_opt;          /* incumbent sample objective after the call          */
   double seconds;        /* host wall time of the call                         */
-  int64_t host_gathers;  /* CTA gathers of this call that read the sample rows
-                            from host memory (bm_fit_host while the copy of X
-                            to the device is still in flight); 0 otherwise     */
+  int64_t host_gathers;  /* CTA gathers of this call that read some of their
+                            sample rows from host memory (bm_fit_host while
+                            those rows of X have not reached the device yet);
+                            0 otherwise                                       */
 } bm_fit_report;
 
 typedef struct bm_ctx bm_ctx;
@@ -246,12 +247,13 @@ bm_status bm_trace(bm_ctx* ctx, double* ns_out, int32_t count);
  * stream; its device memory comes from a stream-ordered pool per device that
  * the library keeps (with the freed blocks, for the next call) until the
  * process exits.  When X_host is pinned or registered host memory (readable
- * by the GPU in place), the copy runs on a second stream while the chunks
- * start at once: a CTA gathers its sample rows from host memory until the
- * copy has landed and from the device copy afterwards (the same bytes, so
- * the results are those of the copied path); the final assignment waits for
- * the copy.  report->host_gathers counts the CTA gathers served from host
- * memory.  X_host must stay unchanged during the call. */
+ * by the GPU in place), the copy runs on a second stream, in pieces of
+ * consecutive rows, while the chunks start at once: a CTA gathers each
+ * sample row from the device copy when the row's piece has landed and from
+ * host memory otherwise (the same bytes, so the results are those of the
+ * copied path); the final assignment waits for the copy.
+ * report->host_gathers counts the CTA gathers that read host memory.
+ * X_host must stay unchanged during the call. */
 bm_status bm_fit_host(const bm_config* cfg, const float* X_host,
                       int32_t chunks, float* C_out_host,
                       uint8_t* mask_out_host, int32_t* labels_out_host,

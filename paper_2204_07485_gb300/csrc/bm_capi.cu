@@ -1204,6 +1204,10 @@ bm_status bm_set_state(bm_ctx* c, const float* C_host, const uint8_t* mask_host,
 // Device memory of bm_fit_host: a stream-ordered pool per device that keeps
 // freed blocks for the next call (held until the process exits), so repeated
 // calls neither pay for cudaMalloc nor synchronise the device in cudaFree.
+// Pieces of the host-to-device copy of X in bm_fit_host (the landed-row
+// count the gathers read advances once per piece).
+static constexpr long long kHostCopyPieces = 32;
+
 static cudaMemPool_t fit_host_pool(int dev) {
   static std::mutex mu;
   static std::map<int, cudaMemPool_t> pools;
@@ -1279,10 +1283,24 @@ bm_status bm_fit_host(const bm_config* cfg, const float* X_host, int32_t chunks,
         cudaEventCreateWithFlags(&e_alloc, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&e_copied, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventRecord(e_alloc, st) != cudaSuccess ||
-        cudaStreamWaitEvent(cs, e_alloc, 0) != cudaSuccess ||
-        cudaMemcpyAsync(X, X_host, xbytes, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
-        launch_x_ready(ready, cs) != cudaSuccess ||
-        cudaEventRecord(e_copied, cs) != cudaSuccess) {
+        cudaStreamWaitEvent(cs, e_alloc, 0) != cudaSuccess) {
+      rc = BM_ECUDA;
+      goto done;
+    }
+    // the copy in pieces of consecutive rows, each followed by the count of
+    // rows landed so far, so that the chunks' gathers move to the device
+    // copy row range by row range
+    const long long piece = std::max<long long>(1, (cfg->m + kHostCopyPieces - 1) / kHostCopyPieces);
+    for (long long r = 0; r < cfg->m && rc == BM_OK; r += piece) {
+      const long long r1 = std::min<long long>(cfg->m, r + piece);
+      const size_t off = (size_t)r * cfg->n * 4, len = (size_t)(r1 - r) * cfg->n * 4;
+      if (cudaMemcpyAsync(reinterpret_cast<char*>(X) + off,
+                          reinterpret_cast<const char*>(X_host) + off, len,
+                          cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+          launch_x_ready(ready, (uint32_t)r1, cs) != cudaSuccess)
+        rc = BM_ECUDA;
+    }
+    if (rc != BM_OK || cudaEventRecord(e_copied, cs) != cudaSuccess) {
       rc = BM_ECUDA;
       goto done;
     }

@@ -31,20 +31,33 @@ __device__ __forceinline__ void phase_tick(const ChunkArgs& a, int i, uint64_t* 
 }
 
 // Where a CTA gathers its sample rows from: X, or -- while X is still being
-// filled by a copy from host memory (*x_ready == 0) -- the host copy itself,
-// read over the CPU-GPU link.  Both hold the same bytes, so the results do
-// not depend on the choice; each CTA takes one source for its whole gather.
-// Called by all threads.
-__device__ __forceinline__ const float* gather_source(const ChunkArgs& a) {
-  if (!a.Xh) return a.X;
-  __shared__ int s_dev;
+// filled by a copy from host memory, piece by piece in row order -- the host
+// copy for the rows that have not landed yet (row >= *x_ready), read over
+// the CPU-GPU link.  Both hold the same bytes, so the results do not depend
+// on the choice.  gather_rows_ready returns the landed-row count for the
+// whole gather (m without a host copy); called by all threads.
+__device__ __forceinline__ long long gather_rows_ready(const ChunkArgs& a, int r0, int nrows) {
+  if (!a.Xh) return a.m;
+  __shared__ long long s_ready;
   __syncthreads();
   if (threadIdx.x == 0) {
-    s_dev = ld_acquire(a.x_ready) != 0u;
-    if (!s_dev) atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats->host_gathers), 1ull);
+    const long long ready = (long long)ld_acquire(a.x_ready);
+    s_ready = ready;
+    // a gather that reads any row from host memory (the rows are ascending)
+    if (nrows > 0 && (long long)__ldcg(a.idx + r0 + nrows - 1) >= ready)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats->host_gathers), 1ull);
   }
   __syncthreads();
-  return s_dev ? a.X : a.Xh;
+  return s_ready;
+}
+__device__ __forceinline__ const float* gather_row_source(const ChunkArgs& a, long long row,
+                                                          long long ready) {
+  return row < ready ? a.X : a.Xh;
+}
+// Both sources allow 16-byte loads of rows whose length is a multiple of 4.
+__device__ __forceinline__ bool gather_sources_aligned16(const ChunkArgs& a) {
+  return (reinterpret_cast<uintptr_t>(a.X) & 15) == 0 &&
+         (!a.Xh || (reinterpret_cast<uintptr_t>(a.Xh) & 15) == 0);
 }
 
 // lidx[0..c) <- indices of the live centroids in ascending order, lidx[k] = c.

@@ -1085,10 +1085,9 @@ __device__ void tcc_gather(const ChunkArgs& a, const TccS& S, int r0, int nrows)
   const int n = a.n, npad = a.npad, w = threadIdx.x >> 5, l = threadIdx.x & 31;
   for (int i = threadIdx.x; i < nrows; i += blockDim.x) S.order[i] = __ldcg(a.idx + r0 + i);
   __syncthreads();
-  const float* X = gather_source(a);
-  if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+  const long long ready = gather_rows_ready(a, r0, nrows);
+  if ((n & 3) == 0 && gather_sources_aligned16(a)) {
     const int q4 = npad >> 2, units = nrows * q4;
-    const float4* X4 = reinterpret_cast<const float4*>(X);
     float4* P4 = reinterpret_cast<float4*>(a.P) + (size_t)r0 * q4;
     for (int u0 = threadIdx.x; u0 < units; u0 += 8 * kTccThreads) {
       float4 v[8];
@@ -1099,7 +1098,8 @@ __device__ void tcc_gather(const ChunkArgs& a, const TccS& S, int r0, int nrows)
           const int i = u / q4, c = u - i * q4;
           int row = S.order[i];
           if (!BM_GUARD(row >= 0 && row < a.m, &a.ctl->status)) row = 0;
-          v[q] = __ldg(X4 + (size_t)row * q4 + c);
+          v[q] = __ldg(reinterpret_cast<const float4*>(gather_row_source(a, row, ready)) +
+                       (size_t)row * q4 + c);
         }
       }
 #pragma unroll
@@ -1121,7 +1121,7 @@ __device__ void tcc_gather(const ChunkArgs& a, const TccS& S, int r0, int nrows)
           const int i = u / nch, f = (u - i * nch) * 32 + l;
           const int row = S.order[i];
           if (f < n && BM_GUARD(row >= 0 && row < a.m, &a.ctl->status))
-            v[q] = __ldg(X + (size_t)row * n + f);
+            v[q] = __ldg(gather_row_source(a, row, ready) + (size_t)row * n + f);
         }
       }
 #pragma unroll

@@ -59,9 +59,10 @@ struct Stats {
 
 struct ChunkArgs {
   const float* X;      // m x n (row stride n)
-  // Optional second copy of X in device-accessible host memory: the gathers
-  // read it while *x_ready is 0 (X still being filled by a host-to-device
-  // copy) and X afterwards.  Both hold the same bytes.  Null: X only.
+  // Optional second copy of X in device-accessible host memory: while X is
+  // being filled by a host-to-device copy (in pieces of consecutive rows),
+  // *x_ready counts the rows that have landed; a gather reads rows below it
+  // from X and the others from Xh.  Both hold the same bytes.  Null: X only.
   const float* Xh;
   const uint32_t* x_ready;
   long long m;
@@ -280,7 +281,7 @@ inline cudaError_t launch_cooperative(Kernel fn, int grid, int threads, size_t s
 cudaError_t launch_draw(const DrawArgs& a, int chunks, cudaStream_t st);
 // *flag <- 1 once every earlier operation of the stream has completed (the
 // host-to-device copy of X that chunk gathers wait for).
-cudaError_t launch_x_ready(uint32_t* flag, cudaStream_t st);
+cudaError_t launch_x_ready(uint32_t* rows_ready, uint32_t rows, cudaStream_t st);
 // Streaming tensor-core final assignment (n <= 128, n % 4 == 0, k <= 128):
 // shared memory of its plan, 0 when it does not take the shape.
 struct TcsPlan {

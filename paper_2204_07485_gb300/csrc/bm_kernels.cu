@@ -529,14 +529,14 @@ __device__ __forceinline__ int block_excl_scan(int v, int* buf, int* total) {
 template <int NP, bool GENERIC>
 __device__ void phase_gather(const ChunkArgs& a, const Smem& S, int r0, int nrows) {
   const int npad = a.npad, n = a.n;
-  const float* X = gather_source(a);
+  const long long ready = gather_rows_ready(a, r0, nrows);
   if constexpr (!GENERIC) {
-    const bool vec4 = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    const bool vec4 = (n % 4 == 0) && gather_sources_aligned16(a);
     for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
       long long row = __ldcg(a.idx + r0 + i);
       if (!BM_GUARD(row >= 0 && row < a.m, &a.ctl->status)) row = 0;
       float p[NP];
-      load_row_np<NP>(p, X + (size_t)row * n, n, vec4, false);
+      load_row_np<NP>(p, gather_row_source(a, row, ready) + (size_t)row * n, n, vec4, false);
       float4* dst = reinterpret_cast<float4*>(a.P + (size_t)(r0 + i) * NP);
       float4* res = reinterpret_cast<float4*>(S.prow + i * NP);
 #pragma unroll
@@ -558,7 +558,7 @@ __device__ void phase_gather(const ChunkArgs& a, const Smem& S, int r0, int nrow
           const int i = e / npad, f = e - i * npad;
           const long long row = __ldcg(a.idx + r0 + i);
           if (f < n && BM_GUARD(row >= 0 && row < a.m, &a.ctl->status))
-            v[u] = __ldg(X + (size_t)row * n + f);
+            v[u] = __ldg(gather_row_source(a, row, ready) + (size_t)row * n + f);
         }
       }
 #pragma unroll
@@ -996,11 +996,12 @@ assign_generic_kernel(AssignArgs a) {
   assign_finish(a, acc, red);
 }
 
-// Publishes the end of the host-to-device copy of X that precedes it on its
-// stream: chunk gathers switch from the host copy to X once they see 1.
-__global__ void x_ready_kernel(uint32_t* flag) {
+// Publishes that the rows [0, rows) of X have landed: the host-to-device
+// copies of those rows precede it on its stream.  Chunk gathers read rows
+// below the count from X, the others from the host copy.
+__global__ void x_ready_kernel(uint32_t* rows_ready, uint32_t rows) {
   __threadfence();
-  atomicExch(flag, 1u);
+  atomicMax(rows_ready, rows);
 }
 
 // ------------------------------------------------------------ launch glue
@@ -1078,8 +1079,8 @@ int assign_max_grid(bool generic, int np, size_t smem) {
   }
 }
 
-cudaError_t launch_x_ready(uint32_t* flag, cudaStream_t st) {
-  x_ready_kernel<<<1, 1, 0, st>>>(flag);
+cudaError_t launch_x_ready(uint32_t* rows_ready, uint32_t rows, cudaStream_t st) {
+  x_ready_kernel<<<1, 1, 0, st>>>(rows_ready, rows);
   return cudaGetLastError();
 }
 
