@@ -474,7 +474,7 @@ typedef struct bm_server_config {
                              once; 0 = half the device memory free at creation  */
   int32_t max_queue;      /* admitted jobs waiting for a worker (>= 1)          */
   int32_t job_ctas;       /* CTA cap of a job whose cfg.max_ctas is 0 (>= 0;
-                             0 = ceil(SMs / 4)).  It does not depend on
+                             0 = ceil(SMs / 2)).  It does not depend on
                              `workers`, so a job's results are those of the
                              same configuration with max_ctas = this cap run
                              alone, whatever the server's size               */

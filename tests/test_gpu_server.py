@@ -75,7 +75,7 @@ def test_mix_results_equal_jobs_run_alone(bm):
 
 def test_results_do_not_depend_on_the_worker_count(bm):
     # a job without its own CTA cap runs with the server's job_ctas (default
-    # ceil(SMs / 4)) whatever the number of workers: the same bits under
+    # ceil(SMs / 2)) whatever the number of workers: the same bits under
     # servers of 1 and 6 workers, and those of the job alone with that cap
     m, n, k, s, T = 60_000, 28, 12, 8_000, 3
     X = dev(bi.mixtures.isotropic_blobs(m, n, 20, 5)[0])
@@ -94,7 +94,7 @@ def test_results_do_not_depend_on_the_worker_count(bm):
         out.append((r["sse"], r["f_opt"], C, mask, host(lab)))
     assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
     assert np.array_equal(out[0][2], out[1][2]) and np.array_equal(out[0][4], out[1][4])
-    cap = -(-torch.cuda.get_device_properties(0).multi_processor_count // 4)
+    cap = -(-torch.cuda.get_device_properties(0).multi_processor_count // 2)
     alone_cfg = bm.bm_config_default(m=m, n=n, k=k, s=s, seed=5, precision=1, max_ctas=cap)
     sse, f_opt, _, C1, mask1, lab1 = _alone(bm, X, alone_cfg, T)
     assert out[0][0] == sse and out[0][1] == f_opt and np.array_equal(out[0][2], C1)
