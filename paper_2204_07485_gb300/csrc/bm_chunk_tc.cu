@@ -1195,6 +1195,7 @@ __device__ void tcc_set_cscale(const double* mpart) {
 __global__ void __launch_bounds__(kTccThreads, 1) chunk_tc_kernel(ChunkArgs a) {
   extern __shared__ __align__(1024) unsigned char tcc_raw[];
   BM_POISON_SMEM();
+  BM_START_SKEW();
   unsigned char* base = tcc_raw + ((1024u - (smem_u32(tcc_raw) & 1023u)) & 1023u);
   const int R = a.rows_per_cta, k = a.k;
   const TccLayout L = tcc_layout(a.npad, k, R, a.tc_n16, a.tc_fb, a.tc_ns, a.tc_planes);

@@ -106,6 +106,29 @@ __device__ __forceinline__ int ld_volatile(const int* p) {
   return *reinterpret_cast<const volatile int*>(p);
 }
 
+// Checking builds (BM_DEBUG_GUARDS) also spread the starts of the CTAs of a
+// cooperative launch: CTA b first spins (b mod 32) x 1,500 SM cycles (about
+// 0.8 us per step at the boost clock, at most about 25 us; far inside the
+// grid barrier's timeout).  A CTA's start then falls at many points of the
+// first microseconds of CTA 0's work, so anything one CTA writes to global
+// memory before the launch's first grid barrier while another reads it at
+// its start shows up as a changed result, not as a rare wrong one.  Release
+// builds compile it to nothing.
+#ifdef BM_DEBUG_GUARDS
+__device__ __forceinline__ void start_skew() {
+  if (threadIdx.x == 0) {
+    const long long wait = 1500ll * (long long)(blockIdx.x % 32u);
+    const long long c0 = clock64();
+    while (clock64() - c0 < wait) {
+    }
+  }
+  __syncthreads();
+}
+#define BM_START_SKEW() (::bm::start_skew())
+#else
+#define BM_START_SKEW() ((void)0)
+#endif
+
 // ------------------------------------------------------------ grid barrier
 // Monotone-counter barrier for a cooperative launch (all CTAs co-resident).
 // Barrier number e completes when the counter reaches e * gridDim.x.  On

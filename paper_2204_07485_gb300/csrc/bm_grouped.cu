@@ -337,6 +337,7 @@ group_update_kernel(GroupArgs a) {
 __global__ void __launch_bounds__(kGroupThreads)
 group_step_kernel(GroupArgs a) {
   BM_POISON_SMEM();
+  BM_START_SKEW();
   group_assign_segments(a);
   GridBarrier gb{a.bar + a.bar_sel, a.status, 0u};
   if (!gb.sync()) return;

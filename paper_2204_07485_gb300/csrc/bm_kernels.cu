@@ -585,7 +585,30 @@ __device__ __forceinline__ void load_cand_row(const ChunkArgs& a, const Smem& S,
     S.cand[c * a.npad + f] = __ldcg(a.P + (size_t)row * a.npad + f);
 }
 
+// Forgy's row for slot j: floor(u_j * s), u_j the slot's first K-means++
+// uniform.
+__device__ __forceinline__ int forgy_row(const ChunkArgs& a, int j) {
+  const double u = unit_double(philox_word(a.seed, (uint64_t)a.t, 2, 0,
+                                           (uint64_t)(j * a.trials)));
+  return min(a.s - 1, (int)floor(u * (double)a.s));
+}
+
+// CTA 0: sample row `row` -> slot j of the global working C (the same
+// L2-coherent loads that fill the candidate table, so the same bits).
+__device__ __forceinline__ void put_global_row(const ChunkArgs& a, int j, int row) {
+  for (int f = threadIdx.x; f < a.npad; f += blockDim.x)
+    a.C[(size_t)j * a.npad + f] = __ldcg(a.P + (size_t)row * a.npad + f);
+}
+
 // K-means++ reseed of every degenerate slot, ascending (Sec. 3.3, Sec. 5).
+//
+// Without the incumbent copy (step-level calls) every CTA reads the starting
+// centroids and mask from the global working C at its start.  Slots filled
+// before the launch's first grid barrier -- the uniform first pick, Forgy's
+// picks -- therefore reach the global C and mask only after that barrier:
+// a CTA that started late would otherwise find a slot live in the mask while
+// its row is still (partly) unwritten, and compute its D^2 against the wrong
+// point.
 template <int NP, bool GENERIC>
 __device__ bool phase_kpp(const ChunkArgs& a, const Smem& S, GridBarrier& gb,
                           int r0, int nrows, long long* nd_out, unsigned long long gen) {
@@ -593,29 +616,32 @@ __device__ bool phase_kpp(const ChunkArgs& a, const Smem& S, GridBarrier& gb,
   const int nlive = S.lidx[k];
   if (nlive == k) return true;
   if (a.init == kInitForgy) {
-    // Forgy: slot j <- sample row floor(u_j * s), u_j its first K-means++
-    // uniform; no distances, every CTA applies the same picks
+    // Forgy: slot j <- sample row floor(u_j * s); no distances, every CTA
+    // applies the same picks
     for (int j = 0; j < k; ++j) {
       if (S.live[j]) continue;
-      const double u = unit_double(philox_word(a.seed, (uint64_t)a.t, 2, 0,
-                                               (uint64_t)(j * a.trials)));
-      const int row = min(a.s - 1, (int)floor(u * (double)a.s));
-      load_cand_row(a, S, 0, row);
+      load_cand_row(a, S, 0, forgy_row(a, j));
       __syncthreads();
       set_centroid_row<GENERIC>(S, S.cand, j, a.npad, a.kpad);
       if (threadIdx.x == 0) S.live[j] = 1;
-      if (b == 0) {
-        for (int f = threadIdx.x; f < a.npad; f += blockDim.x)
-          a.C[(size_t)j * a.npad + f] = S.cand[f];
-        if (threadIdx.x == 0) a.mask[j] = 1;
-      }
       __syncthreads();
     }
     build_live_list(S.live, S.lidx, k);
-    return gb.sync();
+    if (!gb.sync()) return false;
+    if (b == 0) {
+      // the global mask still holds the starting live set: only CTA 0
+      // writes it, and only below, after every row is in place
+      for (int j = 0; j < k; ++j)
+        if (__ldcg(reinterpret_cast<const unsigned char*>(a.mask) + j) == 0)
+          put_global_row(a, j, forgy_row(a, j));
+      __syncthreads();
+      for (int j = threadIdx.x; j < k; j += blockDim.x) a.mask[j] = 1;
+    }
+    return true;
   }
   long long nd = 0;
   double* DSUM = a.part_f + (size_t)kMaxTrials * G;   // D^2 block sums region
+  int first_row = -1;   // the uniform first pick, until CTA 0 has published it
   if (nlive > 0) {
     assign_own_rows<NP, GENERIC>(a, S, r0, nrows);
     nd += (long long)a.s * nlive;
@@ -626,15 +652,21 @@ __device__ bool phase_kpp(const ChunkArgs& a, const Smem& S, GridBarrier& gb,
     __syncthreads();
     set_centroid_row<GENERIC>(S, S.cand, 0, a.npad, a.kpad);
     if (threadIdx.x == 0) S.live[0] = 1;
-    if (b == 0) {
-      for (int f = threadIdx.x; f < a.npad; f += blockDim.x) a.C[f] = S.cand[f];
-      if (threadIdx.x == 0) a.mask[0] = 1;
-    }
+    first_row = i0;
     own_rows_to_cands<NP, GENERIC>(a, S, r0, nrows, 1);
     for (int i = threadIdx.x; i < nrows; i += blockDim.x) S.dmin[i] = S.dc[i];
     __syncthreads();
     nd += a.s;
   }
+  // after a grid barrier: slot 0 <- the first pick in the global C and mask
+  auto publish_first = [&]() {
+    if (first_row < 0) return;
+    if (b == 0) {
+      put_global_row(a, 0, first_row);
+      if (threadIdx.x == 0) a.mask[0] = 1;
+    }
+    first_row = -1;
+  };
   const int R = a.rows_per_cta;
   __shared__ int s_rows[kMaxTrials];
   for (int j = 0; j < k; ++j) {
@@ -644,6 +676,7 @@ __device__ bool phase_kpp(const ChunkArgs& a, const Smem& S, GridBarrier& gb,
     const double mine = own_dmin_sum(S, nrows);
     kpp_put_dsum(a, DSUM, mine, tag);
     if (!gb.sync()) return false;
+    publish_first();
     // (B) targets, the blocks that hold them and the rows inside those blocks
     if (!kpp_locate(a, S.dmin, r0, nrows, DSUM, j, tag)) return false;
     if (!gb.sync()) return false;
@@ -678,7 +711,10 @@ __device__ bool phase_kpp(const ChunkArgs& a, const Smem& S, GridBarrier& gb,
   }
   build_live_list(S.live, S.lidx, k);
   // make the reseeded rows of the global working C visible before Lloyd
+  // (Lloyd reads it back only after its own barriers, so the first pick of a
+  // launch that reseeded no other slot may follow this one)
   if (!gb.sync()) return false;
+  publish_first();
   *nd_out += nd;
   return true;
 }
@@ -819,6 +855,7 @@ __global__ void __launch_bounds__(GENERIC ? 256 : 384)
 chunk_kernel(ChunkArgs a) {
   extern __shared__ __align__(16) char smem_raw[];
   BM_POISON_SMEM();
+  BM_START_SKEW();
   const int G = gridDim.x;
   const ChunkSmem L = chunk_smem(a.npad, a.k, a.kpad, a.rows_per_cta, GENERIC);
   const Smem S = carve(smem_raw, L);

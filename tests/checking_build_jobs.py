@@ -84,6 +84,17 @@ def gpu_jobs(bm):
     bm.bm_kpp_reseed(P, 4_000, 128, 50, C0, m0, 5, 0, 3)
     f, it = bm.bm_lloyd(P, 4_000, 128, 50, C0, m0)
     out["ops"] = {"lloyd_f": f, "iters": it, "C": float(C0.double().sum().item())}
+    # every slot degenerate on the tiled FP32 kernel (12 CTAs): CTA 0 fills
+    # slot 0 before the launch's first grid barrier while the others read
+    # the starting centroids; the checking build's start skew exposes any
+    # overlap of the two
+    Xs, _ = bi.mixtures.isotropic_blobs(6_000, 128, 50, 2)
+    idx_s, _, _ = bi.chunk_draws(2, 0, 6_000, 3_000, 50)
+    Ps = torch.from_numpy(Xs[idx_s]).to(dev)
+    Cs = torch.zeros((50, 128), dtype=torch.float32, device=dev)
+    ms = torch.zeros(50, dtype=torch.uint8, device=dev)
+    bm.bm_kpp_reseed(Ps, 3_000, 128, 50, Cs, ms, 2, 0, 3)
+    out["kpp_all_degenerate"] = [float(v) for v in Cs.double().sum(dim=1).cpu().numpy()]
     out["assign_rows"] = bm.bm_assign_rows(P, 4_000, 128, C0, m0, 50)
     X28d = torch.from_numpy(X28[:50_000]).to(dev)
     C28 = torch.from_numpy(X28[:25].copy()).to(dev)
