@@ -330,13 +330,12 @@ bm_status bm_assign_rows_prec(const float* X_dev, int64_t m, int32_t n,
  * float64 partial per CTA, the last-CTA ticket and the result, 16,640 bytes)
  * is a fixed array inside the library that every GPU loading the library
  * holds until the process exits.  The first call on each device looks up that
- * array's device address (cudaGetSymbolAddress, with the device current);
- * make that first call before any stream capture begins.  All calls share the
- * one array, and calls that overlapped on the GPU would race on it: so every
- * call holds a lock inside the library from its first use of the array until
- * its result has been read back (the call blocks until its work is done),
- * and calls from several host threads of the process, on one stream or on
- * several, run one after another.  A launch that would need more than 2048
+ * array's device address (cudaGetSymbolAddress, with the device current).
+ * All calls share the one array, and calls that overlapped on the GPU would
+ * race on it: so every call holds a lock inside the library from its first
+ * use of the array until its result has been read back (the call blocks
+ * until its work is done), and calls from several host threads of the
+ * process, on one stream or on several, run one after another.  A launch that would need more than 2048
  * CTAs, k > 128, or a centroid table beyond shared memory (where
  * bm_assign_rows would switch to the tensor-core kernel, whose scratch grows
  * with m) returns BM_EUNSUPPORTED. */
