@@ -1137,6 +1137,103 @@ __device__ void tcc_gather(const ChunkArgs& a, const TccS& S, int r0, int nrows)
   __syncthreads();
 }
 
+// Whether the gather can build the BF16 row tiles itself (tcc_gather_convert):
+// rows of 16-byte units from 16-byte aligned sources, whole 8-feature chunks,
+// and at most 16 K blocks (the norm partials' scratch).
+__device__ __forceinline__ bool tcc_fused_gather_ok(const ChunkArgs& a) {
+  return !a.tc_fp8 && (a.n & 3) == 0 && (a.npad & 7) == 0 && a.tc_kb <= 16 &&
+         gather_sources_aligned16(a);
+}
+
+// tcc_gather and tcc_convert_own in one pass: every 8-feature chunk of an
+// own row goes from X to registers once and from there to P (FP32), to the
+// row tiles (BF16 planes, the same bits as tcc_convert_own) and to the
+// chunk's share of the row norm.  Units are (tile row, 8-feature chunk) over
+// whole tiles and K blocks, so the eight lanes of a (row, K block) are
+// consecutive and the padding rows and features of the tiles are written as
+// zeros, as tcc_convert_own writes them.  Each thread keeps kGcUnits units
+// (16 float4 loads) in flight.  The norm of row i adds its K blocks' sums in
+// block order into 0, as tcc_convert_own does, through per-(row, block)
+// partials in the part4 scratch.
+constexpr int kGcUnits = 8;
+__device__ void tcc_gather_convert(const ChunkArgs& a, const TccS& S, int r0, int nrows) {
+  const int tid = threadIdx.x, kb = a.tc_kb, npad = a.npad;
+  const int cpr = kb * 8;                                  // 8-feature chunks per tile row
+  const int ntl = (nrows + kTccM - 1) / kTccM;
+  const int units = ntl * kTccM * cpr;
+  const int blk = a.tc_planes * kTccM * 128;
+  float* nqs = reinterpret_cast<float*>(S.part4);          // [nrows][kb] norm partials
+  for (int i = tid; i < nrows; i += blockDim.x) S.order[i] = __ldcg(a.idx + r0 + i);
+  __syncthreads();
+  const long long ready = gather_rows_ready(a, r0, nrows);
+  unsigned char* base = a.Pb + (size_t)blockIdx.x * a.tc_tpc * kb * blk;
+  // the trip count depends on the units only, so every lane reaches the
+  // shuffles below
+  for (int u0 = 0; u0 < units; u0 += kGcUnits * kTccThreads) {
+    float4 v[kGcUnits][2];
+#pragma unroll
+    for (int q = 0; q < kGcUnits; ++q) {
+      const int u = u0 + q * kTccThreads + tid;
+      const int i = u / cpr, f0 = (u - i * cpr) * 8;
+      v[q][0] = v[q][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (u < units && i < nrows && f0 < npad) {
+        int row = S.order[i];
+        if (!BM_GUARD(row >= 0 && row < a.m, &a.ctl->status)) row = 0;
+        const float4* src = reinterpret_cast<const float4*>(
+            gather_row_source(a, row, ready) + (size_t)row * a.n + f0);
+        v[q][0] = __ldg(src);
+        v[q][1] = __ldg(src + 1);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kGcUnits; ++q) {
+      const int u = u0 + q * kTccThreads + tid;
+      const int i = u / cpr, c8 = u - i * cpr, f0 = c8 * 8;
+      const bool real = u < units && i < nrows && f0 < npad;
+      if (real) {
+        float4* dstp = reinterpret_cast<float4*>(a.P + (size_t)(r0 + i) * npad + f0);
+        dstp[0] = v[q][0];
+        dstp[1] = v[q][1];
+      }
+      const float x[8] = {v[q][0].x, v[q][0].y, v[q][0].z, v[q][0].w,
+                          v[q][1].x, v[q][1].y, v[q][1].z, v[q][1].w};
+      float nq = 0.f;
+      uint32_t h[4], lo[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        nq = fmaf(x[2 * e], x[2 * e], nq);
+        nq = fmaf(x[2 * e + 1], x[2 * e + 1], nq);
+        const __nv_bfloat162 hh = __floats2bfloat162_rn(x[2 * e], x[2 * e + 1]);
+        const float2 hf = __bfloat1622float2(hh);
+        const __nv_bfloat162 ll = __floats2bfloat162_rn(x[2 * e] - hf.x, x[2 * e + 1] - hf.y);
+        h[e] = *reinterpret_cast<const uint32_t*>(&hh);
+        lo[e] = *reinterpret_cast<const uint32_t*>(&ll);
+      }
+      if (u < units) {
+        const int b = c8 >> 3, ch = c8 & 7, tl = i / kTccM, r = i - tl * kTccM;
+        unsigned char* dst = base + (size_t)(tl * kb + b) * blk;
+        const int off = sw128_offset(r, ch * 8);
+        *reinterpret_cast<uint4*>(dst + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        if (a.tc_planes == 2)
+          *reinterpret_cast<uint4*>(dst + kTccM * 128 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+      // the eight lanes of a (row, K block) are consecutive
+      nq += __shfl_xor_sync(0xffffffffu, nq, 1);
+      nq += __shfl_xor_sync(0xffffffffu, nq, 2);
+      nq += __shfl_xor_sync(0xffffffffu, nq, 4);
+      if ((c8 & 7) == 0 && u < units && i < nrows) nqs[i * kb + (c8 >> 3)] = nq;
+    }
+  }
+  fence_proxy_async_global();   // the tiles are read back by bulk copies
+  __syncthreads();
+  for (int i = tid; i < nrows; i += blockDim.x) {
+    float xx = 0.f;
+    for (int b = 0; b < kb; ++b) xx += nqs[i * kb + b];
+    S.xx[i] = xx;
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------- incumbent
 // The (centroid, 32-feature unit) pairs of C' <- C that CTA b publishes:
 // q = b * warps + w, then every gridDim.x * warps.
@@ -1269,7 +1366,10 @@ __global__ void __launch_bounds__(kTccThreads, 1) chunk_tc_kernel(ChunkArgs a) {
     if (!a.tc_fp8) tcc_publish_incumbent(a, S, csrc, full);
   }
   phase_tick(a, 0, &tclk);
-  if (a.phases & kPhaseGather) tcc_gather(a, S, r0, nrows);
+  // BF16 forms: the gather builds the row tiles as it goes
+  const bool fused = work && (a.phases & kPhaseGather) && tcc_fused_gather_ok(a);
+  if (fused) tcc_gather_convert(a, S, r0, nrows);
+  else if (a.phases & kPhaseGather) tcc_gather(a, S, r0, nrows);
   if (work && a.tc_fp8) {
     // M = the largest magnitude over the sample rows and the live incumbent
     // centroids: each CTA's share (own rows, the incumbent values it
@@ -1282,7 +1382,7 @@ __global__ void __launch_bounds__(kTccThreads, 1) chunk_tc_kernel(ChunkArgs a) {
       tcc_set_cscale(MPART);
       tcc_publish_incumbent(a, S, csrc, full);
     }
-  } else if (work) {
+  } else if (work && !fused) {
     tcc_convert_own(a, S, r0, nrows);
   }
   if (work) {
