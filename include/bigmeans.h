@@ -48,7 +48,7 @@ typedef enum bm_status {
   BM_ETIMEOUT = 4,      /* a bounded device-side wait gave up                 */
   BM_EBUSY = 5,         /* server full / resource in use                      */
   BM_ECANCELLED = 6,    /* job cancelled before completion                   */
-  BM_EUNSUPPORTED = 7,  /* shape outside what this build's kernels cover      */
+  BM_EUNSUPPORTED = 7,  /* shape outside what the library's kernels cover    */
   BM_EGUARD = 8         /* debug builds only (BM_DEBUG_GUARDS): a device index
                            guard found an access outside its buffer and
                            skipped it                                        */

@@ -174,9 +174,9 @@ bm_status bm_server_create(const bm_server_config* cfg, bm_server** out) {
   sv->device = dev;
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // half the GPU: on the survey's serving mix two large jobs fill it and
-  // small ones overlap (measured: 174 jobs/s against 143 with a quarter or
-  // the whole GPU per job)
+  // half the GPU: on a mixed load (m up to 5e6, n from 8 to 384, jobs of
+  // 20 chunks) two large jobs fill it and small ones overlap (measured: 174
+  // jobs/s against 143 with a quarter or the whole GPU per job)
   sv->cap = cfg->job_ctas > 0 ? cfg->job_ctas : (sms + 1) / 2;
   if (sv->cfg.memory_budget == 0) {
     size_t free_b = 0, total_b = 0;
