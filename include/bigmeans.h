@@ -115,10 +115,9 @@ typedef struct bm_fit_report {
   int64_t chunk_counter; /* index t of the next chunk                          */
   double f_opt;          /* incumbent sample objective after the call          */
   double seconds;        /* host wall time of the call                         */
-  int64_t host_gathers;  /* CTA gathers of this call that read some of their
-                            sample rows from host memory (bm_fit_host while
-                            those rows of X have not reached the device yet);
-                            0 otherwise                                       */
+  int64_t host_gathers;  /* CTA gathers of this call made while part of X
+                            was still only in host memory (bm_fit_host, while
+                            its copy of X is in flight); 0 otherwise          */
 } bm_fit_report;
 
 typedef struct bm_ctx bm_ctx;
@@ -247,12 +246,14 @@ bm_status bm_trace(bm_ctx* ctx, double* ns_out, int32_t count);
  * stream; its device memory comes from a stream-ordered pool per device that
  * the library keeps (with the freed blocks, for the next call) until the
  * process exits.  When X_host is pinned or registered host memory (readable
- * by the GPU in place), the copy runs on a second stream, in pieces of
- * consecutive rows, while the chunks start at once: a CTA gathers each
- * sample row from the device copy when the row's piece has landed and from
- * host memory otherwise (the same bytes, so the results are those of the
- * copied path); the final assignment waits for the copy.
- * report->host_gathers counts the CTA gathers that read host memory.
+ * by the GPU in place), the copy runs on a second stream, in 32 interleaved
+ * pieces (X cut into blocks of a power-of-two number of rows, at most
+ * m / 4096; piece p holds every 32nd block from block p), while the chunks
+ * start at once: a CTA gathers each sample row from the device copy when the
+ * row's piece has landed and from host memory otherwise (the same bytes, so
+ * the results are those of the copied path); the final assignment waits for
+ * the copy.  report->host_gathers counts the CTA gathers made before the
+ * last piece landed.
  * X_host must stay unchanged during the call. */
 bm_status bm_fit_host(const bm_config* cfg, const float* X_host,
                       int32_t chunks, float* C_out_host,

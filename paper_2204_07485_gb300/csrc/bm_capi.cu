@@ -365,9 +365,11 @@ struct bm_ctx {
   bm_config cfg;
   const float* X;
   // bm_fit_host while its copy of X is in flight: the device-accessible host
-  // rows and the flag that turns 1 when X holds them (null otherwise)
+  // rows, the count of landed copy pieces and the pieces' block size
+  // (2^x_shift rows); null otherwise
   const float* Xh = nullptr;
   const uint32_t* x_ready = nullptr;
+  int x_shift = 0;
   cudaStream_t stream;
   Plan plan;
   Workspace ws;
@@ -624,6 +626,7 @@ bm_status bm_fit_chunk(bm_ctx* c, int32_t chunks, bm_fit_report* out) {
   ChunkArgs a = chunk_args(c->ws, c->plan, c->X, c->cfg.m, c->cfg.n, c->cfg.k, c->cfg.s);
   a.Xh = c->Xh;
   a.x_ready = c->x_ready;
+  a.x_shift = c->x_shift;
   a.seed = c->cfg.seed;
   a.max_iter = c->cfg.max_iter;
   a.tol = c->cfg.tol;
@@ -1204,9 +1207,6 @@ bm_status bm_set_state(bm_ctx* c, const float* C_host, const uint8_t* mask_host,
 // Device memory of bm_fit_host: a stream-ordered pool per device that keeps
 // freed blocks for the next call (held until the process exits), so repeated
 // calls neither pay for cudaMalloc nor synchronise the device in cudaFree.
-// Pieces of the host-to-device copy of X in bm_fit_host (the landed-row
-// count the gathers read advances once per piece).
-static constexpr long long kHostCopyPieces = 32;
 
 static cudaMemPool_t fit_host_pool(int dev) {
   static std::mutex mu;
@@ -1262,6 +1262,7 @@ bm_status bm_fit_host(const bm_config* cfg, const float* X_host, int32_t chunks,
   // stream while the first chunks gather their samples from host memory;
   // the final assignment waits for the copy.
   const float* Xh = host_rows_on_device(X_host);
+  int x_shift = 0;   // the copy pieces' block size, 2^x_shift rows
   bm_status rc = BM_OK;
   bm_ctx* c = nullptr;
   if (cudaMallocFromPoolAsync(reinterpret_cast<void**>(&X), xbytes, pool, st) != cudaSuccess) {
@@ -1287,17 +1288,36 @@ bm_status bm_fit_host(const bm_config* cfg, const float* X_host, int32_t chunks,
       rc = BM_ECUDA;
       goto done;
     }
-    // the copy in pieces of consecutive rows, each followed by the count of
-    // rows landed so far, so that the chunks' gathers move to the device
-    // copy row range by row range
-    const long long piece = std::max<long long>(1, (cfg->m + kHostCopyPieces - 1) / kHostCopyPieces);
-    for (long long r = 0; r < cfg->m && rc == BM_OK; r += piece) {
-      const long long r1 = std::min<long long>(cfg->m, r + piece);
-      const size_t off = (size_t)r * cfg->n * 4, len = (size_t)(r1 - r) * cfg->n * 4;
-      if (cudaMemcpyAsync(reinterpret_cast<char*>(X) + off,
-                          reinterpret_cast<const char*>(X_host) + off, len,
-                          cudaMemcpyHostToDevice, cs) != cudaSuccess ||
-          launch_x_ready(ready, (uint32_t)r1, cs) != cudaSuccess)
+    // the copy in kHostCopyPieces interleaved pieces, each followed by the
+    // count of pieces landed so far: X is cut into blocks of 2^x_shift rows
+    // and piece p takes blocks p, p + P, p + 2P, ... (one strided copy), so
+    // every CTA's share of a chunk's sorted sample -- a 1/G slice of the
+    // rows -- spans all pieces and moves to the device copy at the same pace
+    // (with pieces of consecutive rows, the CTAs holding the last rows read
+    // all of theirs from host memory until the copy reached them, and every
+    // chunk waited for those CTAs).  Blocks: at most m / 4096 rows, so a
+    // slice of the rows spans every piece, and strides below 1 GB.
+    const size_t rowb = (size_t)cfg->n * 4;
+    const long long P = kHostCopyPieces;
+    x_shift = 0;
+    while ((2LL << x_shift) <= cfg->m / 4096 &&
+           (size_t)P * ((size_t)2 << x_shift) * rowb <= ((size_t)1 << 30))
+      ++x_shift;
+    const long long B = 1LL << x_shift, nfull = cfg->m >> x_shift;   // full blocks
+    const size_t bbytes = (size_t)B * rowb;
+    char* Xd = reinterpret_cast<char*>(X);
+    const char* Xs = reinterpret_cast<const char*>(X_host);
+    for (long long p = 0; p < P && rc == BM_OK; ++p) {
+      cudaError_t e = cudaSuccess;
+      const long long h = nfull > p ? (nfull - 1 - p) / P + 1 : 0;   // full blocks p + P j
+      if (h > 0)
+        e = cudaMemcpy2DAsync(Xd + (size_t)p * bbytes, (size_t)P * bbytes, Xs + (size_t)p * bbytes,
+                              (size_t)P * bbytes, bbytes, (size_t)h, cudaMemcpyHostToDevice, cs);
+      if (e == cudaSuccess && nfull % P == p && (cfg->m & (B - 1)) != 0) {   // the last, partial block
+        const size_t off = (size_t)nfull * bbytes, len = (size_t)(cfg->m - nfull * B) * rowb;
+        e = cudaMemcpyAsync(Xd + off, Xs + off, len, cudaMemcpyHostToDevice, cs);
+      }
+      if (e != cudaSuccess || launch_x_ready(ready, (uint32_t)(p + 1), cs) != cudaSuccess)
         rc = BM_ECUDA;
     }
     if (rc != BM_OK || cudaEventRecord(e_copied, cs) != cudaSuccess) {
@@ -1319,6 +1339,7 @@ bm_status bm_fit_host(const bm_config* cfg, const float* X_host, int32_t chunks,
   if (Xh) {
     c->Xh = Xh;
     c->x_ready = ready;
+    c->x_shift = x_shift;
   }
   rc = bm_fit_chunk(c, chunks, report);
   if (Xh) {

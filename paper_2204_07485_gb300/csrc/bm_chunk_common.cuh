@@ -31,20 +31,22 @@ __device__ __forceinline__ void phase_tick(const ChunkArgs& a, int i, uint64_t* 
 }
 
 // Where a CTA gathers its sample rows from: X, or -- while X is still being
-// filled by a copy from host memory, piece by piece in row order -- the host
-// copy for the rows that have not landed yet (row >= *x_ready), read over
-// the CPU-GPU link.  Both hold the same bytes, so the results do not depend
-// on the choice.  gather_rows_ready returns the landed-row count for the
-// whole gather (m without a host copy); called by all threads.
+// filled by a copy from host memory in interleaved pieces (blocks of
+// 2^x_shift rows, block b in piece b mod kHostCopyPieces, pieces landing in
+// order) -- the host copy for the rows whose piece has not landed yet, read
+// over the CPU-GPU link.  Both hold the same bytes, so the results do not
+// depend on the choice.  gather_rows_ready returns the count of landed pieces
+// for the whole gather (all of them without a host copy) and counts the
+// gathers made before the last piece landed; called by all threads.
 __device__ __forceinline__ long long gather_rows_ready(const ChunkArgs& a, int r0, int nrows) {
-  if (!a.Xh) return a.m;
+  (void)r0;
+  if (!a.Xh) return kHostCopyPieces;
   __shared__ long long s_ready;
   __syncthreads();
   if (threadIdx.x == 0) {
     const long long ready = (long long)ld_acquire(a.x_ready);
     s_ready = ready;
-    // a gather that reads any row from host memory (the rows are ascending)
-    if (nrows > 0 && (long long)__ldcg(a.idx + r0 + nrows - 1) >= ready)
+    if (nrows > 0 && ready < kHostCopyPieces)
       atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats->host_gathers), 1ull);
   }
   __syncthreads();
@@ -52,7 +54,8 @@ __device__ __forceinline__ long long gather_rows_ready(const ChunkArgs& a, int r
 }
 __device__ __forceinline__ const float* gather_row_source(const ChunkArgs& a, long long row,
                                                           long long ready) {
-  return row < ready ? a.X : a.Xh;
+  if (!a.Xh) return a.X;
+  return ((row >> a.x_shift) & (kHostCopyPieces - 1)) < ready ? a.X : a.Xh;
 }
 // Both sources allow 16-byte loads of rows whose length is a multiple of 4.
 __device__ __forceinline__ bool gather_sources_aligned16(const ChunkArgs& a) {

@@ -14,7 +14,11 @@ constexpr int kMaxK = 128;         // centroids per job handled by the kernels
 constexpr int kTermsFp8 = 8;       // AssignTcArgs::terms of the E4M3 form
 constexpr int kRoundSlots = 64;    // per-round draw counters (== kMaxRounds)
 constexpr int kNpMax = 32;         // widest row kept in registers
-constexpr int kNumPhaseTimers = 11;  // see Stats::phase_ns
+constexpr int kNumPhaseTimers = 11;
+// Pieces of bm_fit_host's host-to-device copy of X (a power of two: a row's
+// piece is its block index modulo this).
+constexpr int kHostCopyPieces = 32;
+static_assert((kHostCopyPieces & (kHostCopyPieces - 1)) == 0, "pieces: a power of two");  // see Stats::phase_ns
 
 // Reinitialisation of degenerate centroids (bm_config.init).
 constexpr int kInitKmeanspp = 0;
@@ -54,17 +58,20 @@ struct Stats {
   // [7] keep-the-best; [8..10] split [3] into assignment, update slices and
   // slice combination + partial-sum stores
   unsigned long long phase_ns[kNumPhaseTimers];
-  long long host_gathers;   // CTA gathers that read the host-memory copy of X
+  long long host_gathers;   // CTA gathers made while part of X was still only in host memory
 };
 
 struct ChunkArgs {
   const float* X;      // m x n (row stride n)
   // Optional second copy of X in device-accessible host memory: while X is
-  // being filled by a host-to-device copy (in pieces of consecutive rows),
-  // *x_ready counts the rows that have landed; a gather reads rows below it
-  // from X and the others from Xh.  Both hold the same bytes.  Null: X only.
+  // being filled by a host-to-device copy in kHostCopyPieces interleaved
+  // pieces (blocks of 2^x_shift rows, block b in piece b mod
+  // kHostCopyPieces, pieces landing in order), *x_ready counts the pieces
+  // that have landed; a gather reads a row from X when its piece has landed
+  // and from Xh otherwise.  Both hold the same bytes.  Null: X only.
   const float* Xh;
   const uint32_t* x_ready;
+  int x_shift;
   long long m;
   int n, npad, k, s;
   int rows_per_cta;    // R = ceil(s / gridDim.x)
@@ -279,9 +286,9 @@ inline cudaError_t launch_cooperative(Kernel fn, int grid, int threads, size_t s
 
 // Host-side launch helpers (bm_kernels.cu, bm_sample.cu, bm_tc.cu).
 cudaError_t launch_draw(const DrawArgs& a, int chunks, cudaStream_t st);
-// *flag <- 1 once every earlier operation of the stream has completed (the
-// host-to-device copy of X that chunk gathers wait for).
-cudaError_t launch_x_ready(uint32_t* rows_ready, uint32_t rows, cudaStream_t st);
+// *landed <- max(*landed, count) once every earlier operation of the stream
+// has completed (the pieces of the host-to-device copy of X before it).
+cudaError_t launch_x_ready(uint32_t* landed, uint32_t count, cudaStream_t st);
 // Streaming tensor-core final assignment (n <= 128, n % 4 == 0, k <= 128):
 // shared memory of its plan, 0 when it does not take the shape.
 struct TcsPlan {

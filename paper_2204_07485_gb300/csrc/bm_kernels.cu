@@ -1033,12 +1033,13 @@ assign_generic_kernel(AssignArgs a) {
   assign_finish(a, acc, red);
 }
 
-// Publishes that the rows [0, rows) of X have landed: the host-to-device
-// copies of those rows precede it on its stream.  Chunk gathers read rows
-// below the count from X, the others from the host copy.
-__global__ void x_ready_kernel(uint32_t* rows_ready, uint32_t rows) {
+// Publishes that the first `count` pieces of X have landed: the
+// host-to-device copies of those pieces precede it on its stream.  Chunk
+// gathers read the rows of landed pieces from X, the others from the host
+// copy.
+__global__ void x_ready_kernel(uint32_t* landed, uint32_t count) {
   __threadfence();
-  atomicMax(rows_ready, rows);
+  atomicMax(landed, count);
 }
 
 // ------------------------------------------------------------ launch glue
@@ -1116,8 +1117,8 @@ int assign_max_grid(bool generic, int np, size_t smem) {
   }
 }
 
-cudaError_t launch_x_ready(uint32_t* rows_ready, uint32_t rows, cudaStream_t st) {
-  x_ready_kernel<<<1, 1, 0, st>>>(rows_ready, rows);
+cudaError_t launch_x_ready(uint32_t* landed, uint32_t count, cudaStream_t st) {
+  x_ready_kernel<<<1, 1, 0, st>>>(landed, count);
   return cudaGetLastError();
 }
 
